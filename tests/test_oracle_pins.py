@@ -1,0 +1,362 @@
+"""Pins of the FP64 CPU oracle against mathematics that does not come from the
+oracle itself: closed forms, invariants, symmetries, special cases that reduce
+to library routines (dense eigenvalues, QR, linear solves, least squares) and
+brute-force dense constructions on tiny lattices.
+
+The paper (arXiv:1601.03184) prints no worked numerical example for any
+operator (its Sec. 6 gives only speed-up ratios), so every pin here is
+mathematical.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1601_03184_gb300 import inputs
+from lattice_helpers import (aggregate_of_sites, colour_rotate, coords, dense_coarse, dense_D,
+                             dense_P, gamma5_fine, gauge_transform, vol)
+
+C1 = dict(dims=(4, 4, 4, 4), agg=(2, 2, 2, 2), ntv=8, eps=0.3, m0=-0.2, csw=1.0, gseed=1001, tvseed=2001)
+
+
+def c1_field():
+    U = inputs.gauge_field(C1["dims"], C1["eps"], C1["gseed"])
+    A = oracle.clover(C1["dims"], U, C1["m0"], C1["csw"])
+    return U, A
+
+
+# ---------------------------------------------------------------- inputs ----
+def test_gauge_field_is_su3():
+    U = inputs.gauge_field((4, 4, 4, 4), 0.6, 7)
+    Ud = np.conj(np.swapaxes(U, -1, -2))
+    assert np.abs(Ud @ U - np.eye(3)).max() < 1e-14
+    assert np.abs(np.linalg.det(U) - 1).max() < 1e-14
+    # eps -> 0 gives the unit field
+    U0 = inputs.gauge_field((2, 2, 2, 2), 1e-13, 7)
+    assert np.abs(U0 - np.eye(3)).max() < 1e-12
+
+
+def test_gell_mann_algebra():
+    lam = inputs.gell_mann()
+    for a in range(8):
+        assert np.allclose(lam[a], lam[a].conj().T)
+        assert abs(np.trace(lam[a])) < 1e-15
+        for b in range(8):
+            assert abs(np.trace(lam[a] @ lam[b]) - 2 * (a == b)) < 1e-14
+
+
+# ---------------------------------------------------------------- gammas ----
+def test_gamma_clifford_and_chiral_basis():
+    G = oracle.gammas()
+    for mu in range(4):
+        assert np.allclose(G[mu], G[mu].conj().T)
+        for nu in range(4):
+            assert np.allclose(G[mu] @ G[nu] + G[nu] @ G[mu], 2 * np.eye(4) * (mu == nu), atol=1e-15)
+    assert np.allclose(G[4], np.diag([1, 1, -1, -1]))
+    for mu in range(4):
+        for nu in range(4):
+            sig = 0.5j * (G[mu] @ G[nu] - G[nu] @ G[mu])
+            assert np.allclose(sig @ G[4], G[4] @ sig)  # chirality block diagonal
+
+
+# ---------------------------------------------------------------- clover ----
+def test_clover_unit_field():
+    dims = (4, 4, 4, 4)
+    A = oracle.clover(dims, inputs.unit_gauge_field(dims), -0.3, 1.7)
+    assert np.abs(A - 3.7 * np.eye(12)).max() < 1e-15
+
+
+@pytest.mark.parametrize("plane", [(0, 1), (0, 3), (1, 2), (2, 3)])
+def test_clover_constant_abelian_field(plane):
+    """U_nu(x) = diag(e^{i phi x_mu}, e^{-i phi x_mu}, 1), other links 1, with
+    phi L_mu = 2 pi: every plaquette of the mu-nu plane equals
+    diag(e^{i phi}, e^{-i phi}, 1), so Fhat = i sin(phi) diag(1,-1,0) and
+    A = (4+m0) + (csw/2) i sigma_{mu nu} (x) Fhat in closed form."""
+    mu, nu = plane
+    dims = (4, 4, 4, 4)
+    V = vol(dims)
+    U = inputs.unit_gauge_field(dims)
+    phi = 2 * np.pi / dims[mu]
+    xm = coords(dims)[:, mu]
+    U[:, nu, 0, 0] = np.exp(1j * phi * xm)
+    U[:, nu, 1, 1] = np.exp(-1j * phi * xm)
+    m0, csw = -0.4, 1.3
+    A = oracle.clover(dims, U, m0, csw)
+    G = oracle.gammas()
+    sig = 0.5j * (G[mu] @ G[nu] - G[nu] @ G[mu])
+    F = 1j * np.sin(phi) * np.diag([1, -1, 0])
+    ref = (4 + m0) * np.eye(12) + 0.5 * csw * 1j * np.kron(sig, F)
+    assert np.abs(A - ref[None]).max() < 1e-14
+    assert V == A.shape[0]
+
+
+def test_clover_hermitian_chiral_and_covariant():
+    dims = (4, 4, 4, 4)
+    U = inputs.gauge_field(dims, 0.6, 11)
+    A = oracle.clover(dims, U, -0.2, 1.5)
+    assert np.abs(A - np.conj(np.swapaxes(A, 1, 2))).max() < 1e-14
+    assert np.abs(A[:, :6, 6:]).max() < 1e-15 and np.abs(A[:, 6:, :6]).max() < 1e-15
+    Om = inputs.random_su3(vol(dims), 12)
+    At = oracle.clover(dims, gauge_transform(dims, U, Om), -0.2, 1.5)
+    O12 = np.einsum("ij,sab->siajb", np.eye(4), Om).reshape(-1, 12, 12)
+    ref = O12 @ A @ np.conj(np.swapaxes(O12, 1, 2))
+    assert np.abs(At - ref).max() < 1e-13
+
+
+# ---------------------------------------------------------- Dirac operator --
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (4, 4, 4, 4)])
+def test_free_field_spectrum(dims):
+    """Unit gauge field: eigenvalues m0 + sum(1-cos p) +/- i sqrt(sum sin^2 p),
+    6-fold each, p_k = 2 pi n/L_k (x,y,z), p_t = (2n+1) pi/L_t."""
+    from scipy.optimize import linear_sum_assignment
+
+    m0 = -0.2
+    U = inputs.unit_gauge_field(dims)
+    A = oracle.clover(dims, U, m0, 1.0)
+    ev = np.linalg.eigvals(dense_D(dims, U, A))
+    moms = [2 * np.pi * np.arange(dims[k]) / dims[k] for k in range(3)]
+    moms.append((2 * np.arange(dims[3]) + 1) * np.pi / dims[3])
+    ref = []
+    for p in itertools.product(*moms):
+        p = np.array(p)
+        a = m0 + np.sum(1 - np.cos(p))
+        b = np.sqrt(np.sum(np.sin(p) ** 2))
+        ref += [a + 1j * b] * 6 + [a - 1j * b] * 6
+    ref = np.array(ref)
+    cost = np.abs(ev[:, None] - ref[None, :])
+    r, c = linear_sum_assignment(cost)
+    assert cost[r, c].max() < 1e-11
+
+
+def test_plane_wave_fixes_sign_convention():
+    """D e^{ipx} u = e^{ipx} (m0 + sum(1-cos p) + i sum gamma_mu sin p_mu) u"""
+    dims = (4, 4, 4, 4)
+    m0 = -0.2
+    U = inputs.unit_gauge_field(dims)
+    A = oracle.clover(dims, U, m0, 1.0)
+    G = oracle.gammas()
+    x = coords(dims)
+    rng = np.random.default_rng(3)
+    for n in [(1, 0, 0, 0), (0, 2, 1, 0), (3, 1, 2, 1)]:
+        p = np.array([2 * np.pi * n[k] / dims[k] for k in range(3)] + [(2 * n[3] + 1) * np.pi / dims[3]])
+        u = rng.standard_normal(12) + 1j * rng.standard_normal(12)
+        ph = np.exp(1j * x @ p)
+        Dp = (m0 + np.sum(1 - np.cos(p))) * np.eye(4) + 1j * sum(G[m] * np.sin(p[m]) for m in range(4))
+        ref = ph[:, None] * (np.kron(Dp, np.eye(3)) @ u)[None, :]
+        y = oracle.apply_D(dims, U, A, ph[:, None] * u[None, :])
+        assert np.abs(y - ref).max() < 1e-13
+
+
+def test_gamma5_hermiticity():
+    U, A = c1_field()
+    dims = C1["dims"]
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal((vol(dims), 12)) + 1j * rng.standard_normal((vol(dims), 12))
+    y = rng.standard_normal((vol(dims), 12)) + 1j * rng.standard_normal((vol(dims), 12))
+    g5 = np.array([1] * 6 + [-1] * 6)
+    lhs = np.vdot(x, g5 * oracle.apply_D(dims, U, A, g5 * y))
+    rhs = np.vdot(oracle.apply_D(dims, U, A, x), y)
+    assert abs(lhs - rhs) < 1e-13 * abs(rhs) * 100
+
+
+def test_gauge_covariance_of_D():
+    U, _ = c1_field()
+    dims = C1["dims"]
+    A = oracle.clover(dims, U, -0.2, 1.0)
+    Om = inputs.random_su3(vol(dims), 21)
+    Ut = gauge_transform(dims, U, Om)
+    At = oracle.clover(dims, Ut, -0.2, 1.0)
+    psi = inputs.gaussian_field((vol(dims), 12), 22)
+    lhs = oracle.apply_D(dims, Ut, At, colour_rotate(Om, psi))
+    rhs = colour_rotate(Om, oracle.apply_D(dims, U, A, psi))
+    assert np.abs(lhs - rhs).max() < 1e-13
+
+
+def test_block_D_is_D_with_cut_links():
+    """D_B equals the full D on a field whose links crossing aggregate
+    boundaries are set to zero (clover kept from the original field)."""
+    U, A = c1_field()
+    dims, agg = C1["dims"], C1["agg"]
+    Ag = aggregate_of_sites(dims, agg)
+    Ucut = U.copy()
+    c = coords(dims)
+    for mu in range(4):
+        cp = c.copy()
+        cp[:, mu] = (cp[:, mu] + 1) % dims[mu]
+        xp = cp[:, 0] + dims[0] * (cp[:, 1] + dims[1] * (cp[:, 2] + dims[2] * cp[:, 3]))
+        Ucut[Ag != Ag[xp], mu] = 0
+    psi = inputs.gaussian_field((vol(dims), 12), 31)
+    y1 = oracle.apply_D_block(dims, agg, U, A, psi)
+    y2 = oracle.apply_D(dims, Ucut, A, psi)
+    assert np.abs(y1 - y2).max() < 1e-14
+
+
+# -------------------------------------------------------------------- SAP ----
+def test_sap_many_mr_steps_is_block_gauss_seidel():
+    """With many MR steps the block solves are exact, so one sweep is the
+    multiplicative Schwarz step: x0 <- x0 + D_00^-1 (b - D x)_0, then colour 1."""
+    U, A = c1_field()
+    dims, agg = C1["dims"], C1["agg"]
+    V = vol(dims)
+    D = dense_D(dims, U, A)
+    Ag = aggregate_of_sites(dims, agg)
+    nb = [d // a for d, a in zip(dims, agg)]
+    bc = np.stack(np.unravel_index(Ag, nb[::-1]), axis=1)[:, ::-1]
+    colour = bc.sum(axis=1) % 2
+    b = inputs.gaussian_field((V, 12), 41)
+    x0 = inputs.gaussian_field((V, 12), 42) * 0.1
+    x = x0.reshape(-1).copy()
+    bb = b.reshape(-1)
+    for col in (0, 1):
+        r = bb - D @ x
+        for Bk in np.unique(Ag[colour == col]):
+            idx = np.concatenate([np.arange(s * 12, s * 12 + 12) for s in np.where(Ag == Bk)[0]])
+            x[idx] += np.linalg.solve(D[np.ix_(idx, idx)], r[idx])
+    xo = oracle.sap(dims, agg, U, A, b[None], x0[None], 1, 400)[0]
+    assert np.abs(xo.reshape(-1) - x).max() / np.abs(x).max() < 1e-11
+
+
+def test_sap_reduces_residual_and_is_gauge_covariant():
+    U, A = c1_field()
+    dims, agg = C1["dims"], C1["agg"]
+    V = vol(dims)
+    b = inputs.gaussian_field((1, V, 12), 43)
+    res = [1.0]
+    for ns in (1, 2, 4):
+        x = oracle.sap(dims, agg, U, A, b, np.zeros_like(b), ns, 4)
+        res.append(oracle.relres(dims, U, A, b[0], x[0]))
+    assert all(res[i + 1] < res[i] for i in range(len(res) - 1))
+    Om = inputs.random_su3(V, 44)
+    Ut = gauge_transform(dims, U, Om)
+    At = oracle.clover(dims, Ut, C1["m0"], C1["csw"])
+    xt = oracle.sap(dims, agg, Ut, At, colour_rotate(Om, b), np.zeros_like(b), 2, 3)
+    x = oracle.sap(dims, agg, U, A, b, np.zeros_like(b), 2, 3)
+    assert np.abs(xt - colour_rotate(Om, x)).max() < 1e-12
+
+
+# ------------------------------------------------------------ Gram-Schmidt --
+def test_gram_schmidt_is_unique_thin_qr():
+    dims, agg, ntv = C1["dims"], C1["agg"], C1["ntv"]
+    tv = inputs.test_vectors(ntv, dims, 51)
+    P = oracle.gram_schmidt(dims, agg, tv)
+    Ag = aggregate_of_sites(dims, agg)
+    for Ak in range(16):
+        sites = np.where(Ag == Ak)[0]
+        for h in range(2):
+            Vm = tv[:, sites, 6 * h:6 * h + 6].reshape(ntv, -1).T
+            Pm = P[:, sites, 6 * h:6 * h + 6].reshape(ntv, -1).T
+            assert np.abs(Pm.conj().T @ Pm - np.eye(ntv)).max() < 1e-14
+            Q, R = np.linalg.qr(Vm)  # Householder (LAPACK)
+            ph = np.diag(R) / np.abs(np.diag(R))
+            assert np.abs(Pm - Q * ph[None, :]).max() < 1e-13
+    # columns outside the chirality are untouched: P restricted to (A, h) only
+    assert P.shape == tv.shape
+
+
+# ----------------------------------------------------------- coarse operator --
+@pytest.mark.parametrize("case", ["c1", "tiny"])
+def test_coarse_operator_brute_force(case):
+    """Summed 9-point stencil == dense P^dag D P (P the dense prolongation)."""
+    if case == "c1":
+        dims, agg, ntv = C1["dims"], C1["agg"], C1["ntv"]
+        U, A = c1_field()
+    else:
+        dims, agg, ntv = (2, 2, 2, 2), (1, 1, 1, 1), 4
+        U = inputs.gauge_field(dims, 0.5, 61)
+        A = oracle.clover(dims, U, 0.1, 1.2)
+    tv = inputs.test_vectors(ntv, dims, 62)
+    P = oracle.gram_schmidt(dims, agg, tv)
+    Dc = oracle.coarse_op(dims, agg, U, A, P)
+    Pd = dense_P(dims, agg, P)
+    ref = Pd.conj().T @ dense_D(dims, U, A) @ Pd
+    got = dense_coarse(dims, agg, Dc)
+    assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
+    # coarse gamma_5 hermiticity: Gamma5 Dc Gamma5 = Dc^dag
+    nagg = Dc.shape[0]
+    g5c = np.kron(np.eye(nagg), np.diag([1.0] * ntv + [-1.0] * ntv))
+    assert np.abs(g5c @ got @ g5c - got.conj().T).max() < 1e-12 * np.abs(got).max()
+    # R P = 1 on the coarse space, apply_Dc = R D P
+    uc = inputs.gaussian_field((2, nagg, 2 * ntv), 63)
+    u = oracle.prolong(dims, agg, P, uc)
+    assert np.abs(oracle.restrict(dims, agg, P, u) - uc).max() < 1e-13
+    yc = oracle.apply_Dc(dims, agg, Dc, uc)
+    ref_yc = oracle.restrict(dims, agg, P, oracle.apply_D(dims, U, A, u))
+    assert np.abs(yc - ref_yc).max() < 1e-12 * np.abs(ref_yc).max()
+
+
+# ------------------------------------------------------------------ GMRES ----
+def test_coarse_gmres_iterate_is_krylov_minimiser():
+    dims, agg, ntv = C1["dims"], C1["agg"], C1["ntv"]
+    U, A = c1_field()
+    P = oracle.gram_schmidt(dims, agg, inputs.test_vectors(ntv, dims, 71))
+    Dc = oracle.coarse_op(dims, agg, U, A, P)
+    M = dense_coarse(dims, agg, Dc)
+    bc = inputs.gaussian_field((1, Dc.shape[0], 2 * ntv), 72)
+    b = bc.reshape(-1)
+    for k in (1, 3, 6):
+        xc, its = oracle.coarse_solve(dims, agg, Dc, bc, 0.0, 20, k)
+        assert its[0] == k
+        K = np.stack([np.linalg.matrix_power(M, i) @ b for i in range(k)], axis=1)
+        Q, _ = np.linalg.qr(K)
+        y, *_ = np.linalg.lstsq(M @ Q, b, rcond=None)
+        ref = Q @ y
+        assert np.abs(xc.reshape(-1) - ref).max() < 1e-10 * np.abs(ref).max()
+    # to tolerance: the true residual meets it
+    xc, its = oracle.coarse_solve(dims, agg, Dc, bc, 1e-9, 10, 1000)
+    assert np.linalg.norm(b - M @ xc.reshape(-1)) <= 1.01e-9 * np.linalg.norm(b)
+
+
+def test_setup_and_fgmres_c1():
+    """The C1 setup (3 SAP sweeps x 4 MR, 1 refinement) gives an orthonormal
+    P and a D_c equal to P^dag D P; two-level FGMRES then solves D x = b to
+    1e-10 and agrees with the dense solve."""
+    dims, agg, ntv = C1["dims"], C1["agg"], C1["ntv"]
+    U, A = c1_field()
+    tv0 = inputs.test_vectors(ntv, dims, C1["tvseed"])
+    prm = oracle.make_params(n_init_sweeps=3, n_init_mr=4, n_refine=1)
+    tv, P, Dc = oracle.setup_init(dims, agg, U, A, tv0, prm)
+    tv, P, Dc, its = oracle.setup_refine(dims, agg, U, A, tv, P, Dc, prm)
+    assert (its >= 1).all()
+    Pd = dense_P(dims, agg, P)
+    assert np.abs(Pd.conj().T @ Pd - np.eye(Pd.shape[1])).max() < 1e-13
+    D = dense_D(dims, U, A)
+    assert np.abs(dense_coarse(dims, agg, Dc) - Pd.conj().T @ D @ Pd).max() < 1e-12 * 10
+    b = inputs.gaussian_field((vol(dims), 12), 3001)
+    x, it, rr = oracle.fgmres(dims, agg, U, A, P, Dc, b, tol=1e-10)
+    assert rr <= 1e-10 and it < 100
+    xd = np.linalg.solve(D, b.reshape(-1))
+    assert np.abs(x.reshape(-1) - xd).max() < 1e-8 * np.abs(xd).max()
+
+
+def test_setup_gauge_invariance():
+    """U -> U^Om and tv -> Om tv leave D_c unchanged and map P -> Om P."""
+    dims, agg, ntv = C1["dims"], C1["agg"], 4
+    U, A = c1_field()
+    tv0 = inputs.test_vectors(ntv, dims, 81)
+    Om = inputs.random_su3(vol(dims), 82)
+    Ut = gauge_transform(dims, U, Om)
+    At = oracle.clover(dims, Ut, C1["m0"], C1["csw"])
+    prm = oracle.make_params(n_init_sweeps=2, n_init_mr=3, n_refine=1, n_smooth_sweeps=2, n_smooth_mr=3,
+                             coarse_tol=0.0, coarse_maxit=6)
+    tv, P, Dc = oracle.setup_init(dims, agg, U, A, tv0, prm)
+    tv, P, Dc, _ = oracle.setup_refine(dims, agg, U, A, tv, P, Dc, prm)
+    tvt, Pt, Dct = oracle.setup_init(dims, agg, Ut, At, colour_rotate(Om, tv0), prm)
+    tvt, Pt, Dct, _ = oracle.setup_refine(dims, agg, Ut, At, tvt, Pt, Dct, prm)
+    assert np.abs(Dct - Dc).max() < 1e-11 * np.abs(Dc).max()
+    assert np.abs(Pt - colour_rotate(Om, P)).max() < 1e-11
+
+
+def test_init_modes_agree_for_one_sweep():
+    dims, agg, ntv = C1["dims"], C1["agg"], 3
+    U, A = c1_field()
+    tv0 = inputs.test_vectors(ntv, dims, 91)
+    a = oracle.setup_init(dims, agg, U, A, tv0, oracle.make_params(init_mode=0, n_init_sweeps=1))
+    b = oracle.setup_init(dims, agg, U, A, tv0, oracle.make_params(init_mode=1, n_init_sweeps=1))
+    for u, v in zip(a, b):
+        assert np.array_equal(u, v)
+
+
+def test_gamma5_fine_helper_consistent():
+    g = gamma5_fine(2)
+    assert g.shape == (24, 24) and np.allclose(np.diag(g)[:12], [1] * 6 + [-1] * 6)
