@@ -1,0 +1,251 @@
+/*
+ * mrhs.h - C ABI of the GB300 (sm_103a) multiple-right-hand-side setup of
+ * two-level DD-alpha-AMG for the Wilson-clover Dirac operator
+ * (Richtmann, Heybrock, Wettig, arXiv:1601.03184).
+ *
+ * Every step of the setup runs in the library's own CUDA kernels. The calls
+ * below are the boundary: plain pointers and sizes, no C++ or torch types.
+ *
+ * General rules for every call
+ *  - Return value: MRHS_OK (0) or a negative mrhs_status. No exception and no
+ *    abort crosses this boundary; mrhs_last_error(ctx) holds the message of
+ *    the last failure on that context (mrhs_last_error(NULL): failures of
+ *    mrhs_create).
+ *  - Host pointers are owned by the caller and read or written only during
+ *    the call. Device pointers are owned by the caller, must be 16-byte
+ *    aligned, and are read/written in stream order on the context's stream
+ *    (the call may return before the GPU has finished; mrhs_sync waits).
+ *    Everything the library allocates is freed by mrhs_destroy.
+ *  - Sites: canonical index s = x + Lx*(y + Ly*(z + Lz*t)); spinor component
+ *    c = 3*spin + colour; chirality h = 0 for spins 0,1 (gamma_5 = +1), h = 1
+ *    for spins 2,3, in the chiral gamma basis gamma_k = [[0,-i sigma_k],
+ *    [i sigma_k,0]] (mu = k-1 = 0,1,2), gamma_4 = [[0,1],[1,0]] (mu = 3).
+ *    Fermion fields are antiperiodic in t, periodic otherwise.
+ *  - Host ("canonical") field layout: [nrhs][V][12] complex, complex128 for
+ *    MRHS_F64 or complex64 for MRHS_F32 host dtypes.
+ *  - Device ("interleaved") field layout: the right-hand sides are the
+ *    innermost index, real parts of all nrhs then imaginary parts (the
+ *    array-of-structs-of-short-vectors layout of Sec. 5 of the paper, with
+ *    the vector length equal to nrhs): element (site, c, re/im, rhs) at
+ *    ((site*12 + c)*2 + re/im)*nrhs + rhs, sites in the library's
+ *    aggregate-major order (aggregate, then site inside it). Only the
+ *    library's own pack/unpack calls write or read this order; use
+ *    mrhs_field_bytes for sizes.
+ *  - Coarse fields: per aggregate 2*ntv complex values (index h*ntv + j,
+ *    Sec. 2: "coarse-grid dof 2 Ntv"). Host layout [nrhs][nagg][2ntv]
+ *    complex; device layout ((A*2ntv + i)*2 + re/im)*nrhs + rhs.
+ *  - Aggregates are lattice blocks of agg[0]x..xagg[3] sites in
+ *    lexicographic block order. They are also the Schwarz domains of the SAP
+ *    smoother (Sec. 2, domain size 4^4 in Sec. 6).
+ */
+#ifndef MRHS_H
+#define MRHS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mrhs_ctx_s* mrhs_ctx;
+
+typedef enum {
+  MRHS_OK = 0,
+  MRHS_ERR_ARG = -1,       /* bad pointer, enum value or parameter */
+  MRHS_ERR_SHAPE = -2,     /* lattice/aggregate/ntv combination not allowed */
+  MRHS_ERR_OOM = -3,       /* device or host allocation failed */
+  MRHS_ERR_CUDA = -4,      /* a CUDA runtime call failed */
+  MRHS_ERR_NOCONV = -5,    /* an iterative solve hit maxit before its tolerance */
+  MRHS_ERR_NONFINITE = -6, /* NaN/Inf or a linearly dependent test vector */
+  MRHS_ERR_STATE = -7,     /* call made before the state it needs exists */
+  MRHS_ERR_TIMEOUT = -8    /* reserved: a bounded device wait ran out */
+} mrhs_status;
+
+/* storage type of a field (device) or of a host array */
+typedef enum { MRHS_F64 = 0, MRHS_F32 = 1, MRHS_BF16 = 2, MRHS_F16 = 3 } mrhs_dtype;
+
+/* precision of a context: what the setup stores its test vectors, P, work
+ * vectors and D_c in. FP64: all double. FP32: all float (reductions in
+ * double). MIX_BF16 / MIX_FP16: test vectors and P in bf16 / fp16, smoother
+ * and coarse work in float, Gram-Schmidt inner products in double. */
+typedef enum { MRHS_PREC_FP64 = 0, MRHS_PREC_FP32 = 1, MRHS_PREC_MIX_BF16 = 2, MRHS_PREC_MIX_FP16 = 3 } mrhs_prec;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a lattice context on the current CUDA device.
+ * dims: lattice extents (Lx,Ly,Lz,Lt); agg: aggregate (= Schwarz domain)
+ * extents; ntv: number of test vectors N_tv (Sec. 2); prec: mrhs_prec;
+ * stream: a cudaStream_t (NULL = the legacy default stream) used for every
+ * later launch and copy of this context.
+ * MRHS_ERR_SHAPE unless: every dims[mu] % agg[mu] == 0, every
+ * dims[mu]/agg[mu] is even (red-black colouring of the domains), V < 2^30,
+ * 1 <= ntv <= 6*|aggregate| and ntv <= 64. Builds the index tables. */
+int mrhs_create(const int dims[4], const int agg[4], int ntv, int prec, void* stream, mrhs_ctx* out);
+void mrhs_destroy(mrhs_ctx ctx);
+const char* mrhs_last_error(mrhs_ctx ctx);
+/* wait for all work of the context's stream */
+int mrhs_sync(mrhs_ctx ctx);
+/* out[0..7] = V, nagg, sites per aggregate, ntv, prec, device bytes held by
+ * the library, number of SMs, 0 */
+int mrhs_info(mrhs_ctx ctx, long long out[8]);
+
+/* bytes of a device field of nrhs right-hand sides (coarse != 0: coarse
+ * field) in storage type dtype */
+size_t mrhs_field_bytes(mrhs_ctx ctx, int nrhs, int dtype, int coarse);
+
+/* Neighbour and aggregate tables, canonical order, as built on the GPU.
+ * nbr [V][8]: k = 0..3 the site s + mu_hat, k = 4..7 the site s - mu_hat;
+ * bit 30 set when the hop crosses the t boundary (fermion sign -1).
+ * aggof [V][2]: (aggregate index, offset of s inside its aggregate, both
+ * lexicographic). aggnbr [nagg][8]: aggregate +mu (k<4) and -mu (k>=4).
+ * Any pointer may be NULL. */
+int mrhs_get_tables(mrhs_ctx ctx, int* nbr, int* aggof, int* aggnbr);
+
+/* ------------------------------------------------------ gauge and clover */
+
+/* Copy the gauge field in: host U[V][4][3][3] complex128, canonical order
+ * (the links U_mu(x) of the Wilson-clover operator named in Sec. 2). */
+int mrhs_set_gauge(mrhs_ctx ctx, const double* U);
+
+/* Build the clover term on the GPU (in FP64) from the gauge field:
+ * A(x) = (4+m0) + (csw/2) sum_{mu<nu} i sigma_{mu nu} Fhat_{mu nu}(x),
+ * sigma_{mu nu} = (i/2)[gamma_mu, gamma_nu], Fhat = (Q - Q^dag)/8 with Q the
+ * four-leaf clover sum; stored as two Hermitian 6x6 blocks per site
+ * (chiralities h = 0, 1). MRHS_ERR_STATE before mrhs_set_gauge. */
+int mrhs_build_clover(mrhs_ctx ctx, double m0, double csw);
+
+/* Copy the clover blocks out: host [V][2][6][6] complex128, canonical. */
+int mrhs_get_clover(mrhs_ctx ctx, double* host_out);
+
+/* ------------------------------------------------------- field transfer */
+
+/* host canonical [nrhs][V][12] (host_dtype MRHS_F64: complex128, MRHS_F32:
+ * complex64) -> device interleaved field of storage type dev_dtype. */
+int mrhs_pack(mrhs_ctx ctx, const void* host, int host_dtype, void* dev, int dev_dtype, int nrhs);
+/* device interleaved -> host canonical */
+int mrhs_unpack(mrhs_ctx ctx, const void* dev, int dev_dtype, void* host, int host_dtype, int nrhs);
+/* the same for coarse fields: host [nrhs][nagg][2ntv] */
+int mrhs_pack_coarse(mrhs_ctx ctx, const void* host, int host_dtype, void* dev, int dev_dtype, int nrhs);
+int mrhs_unpack_coarse(mrhs_ctx ctx, const void* dev, int dev_dtype, void* host, int host_dtype, int nrhs);
+
+/* ------------------------------------------------------------ operators */
+
+/* y = D x for nrhs right-hand sides at once (multi-RHS Wilson-clover
+ * stencil; the "Dirac equation" operator of Sec. 1-2):
+ * y(x) = A(x) x(x) - 1/2 sum_mu [(1-gamma_mu) U_mu(x) x(x+mu)
+ *                              + (1+gamma_mu) U_mu(x-mu)^dag x(x-mu)].
+ * x, y: device interleaved fields of storage dtype (F64 computes in double,
+ * the others in float). x and y must not overlap.
+ * MRHS_ERR_STATE before mrhs_build_clover. */
+int mrhs_apply_D(mrhs_ctx ctx, const void* x, void* y, int nrhs, int dtype);
+
+/* y = D_B x: D with every coupling between different aggregates removed
+ * (the block operator of the Schwarz smoother, Sec. 2). */
+int mrhs_apply_D_block(mrhs_ctx ctx, const void* x, void* y, int nrhs, int dtype);
+
+/* x <- SAP^n_sweeps(b, x): the Schwarz alternating procedure smoother of
+ * Sec. 2 on all nrhs right-hand sides at once. One sweep = colour 0 then
+ * colour 1 of the red-black domain colouring (colour = parity of the sum of
+ * the aggregate coordinates); per colour r = b - D x, then on every domain
+ * B of that colour n_mr minimal-residual steps on D_B e = r_B from e = 0
+ * (alpha = <q,rho>/<q,q>, q = D_B rho), and x_B += e. b, x: device fields
+ * of storage dtype F64 or F32. */
+int mrhs_sap(mrhs_ctx ctx, const void* b, void* x, int nrhs, int dtype, int n_sweeps, int n_mr);
+
+/* ------------------------------------------------------ setup building blocks */
+
+/* copy ntv test vectors (device interleaved field, nrhs = ntv, storage
+ * dtype) into the context's test-vector storage (converted to the context
+ * precision's storage type) */
+int mrhs_set_tv(mrhs_ctx ctx, const void* tv, int dtype);
+
+/* P from the test vectors: per aggregate A and chirality h the vectors
+ * v_1..v_ntv restricted to A x h are orthonormalised in order (Sec. 2:
+ * "construct restriction R, prolongation P = R^dag"); the result is the Q
+ * factor of the thin QR with positive real diagonal, computed on the GPU
+ * by two Cholesky-QR passes with double-precision Gram matrices.
+ * MRHS_ERR_NONFINITE if a vector set is (numerically) dependent. */
+int mrhs_build_P(mrhs_ctx ctx);
+
+/* D_c = R D P (Sec. 2) as a 9-point stencil on the aggregate lattice:
+ * Dc[A][k][2ntv][2ntv], k = 0 the aggregate itself, k = 1+mu the aggregate
+ * A+mu, k = 5+mu the aggregate A-mu (the blocks are kept separate even when
+ * A+mu == A-mu). MRHS_ERR_STATE before mrhs_build_P. */
+int mrhs_build_Dc(mrhs_ctx ctx);
+
+/* restriction vc = R v = P^dag v (Algorithm 3 of the paper, all nrhs at
+ * once): vc[A][h*ntv+j] = sum_{x in A, c in h} conj(P_j(x,c)) v(x,c).
+ * v: fine device field, vc: coarse device field, both of storage dtype
+ * (F64 or F32; must match the context's compute type). */
+int mrhs_restrict(mrhs_ctx ctx, const void* v, void* vc, int nrhs, int dtype);
+/* prolongation u = P uc (Sec. 2, Algorithm 1) */
+int mrhs_prolong(mrhs_ctx ctx, const void* uc, void* u, int nrhs, int dtype);
+/* yc = D_c xc on nrhs coarse right-hand sides (Sec. 5: D_c applied with the
+ * same broadcast scheme as the restriction) */
+int mrhs_apply_Dc(mrhs_ctx ctx, const void* xc, void* yc, int nrhs, int dtype);
+
+/* Coarse solve "to low accuracy" (Algorithm 1/2, tolerance 0.05 in Sec. 6):
+ * GMRES(restart) on D_c xc = bc from xc = 0 for every right-hand side at
+ * once, each with its own Krylov space; a right-hand side stops when its
+ * residual estimate reaches tol*|bc| or after maxit iterations in total.
+ * tol = 0 gives exactly maxit iterations. iters (host, may be NULL)
+ * receives the iteration count of every right-hand side. */
+int mrhs_coarse_solve(mrhs_ctx ctx, const void* bc, void* xc, int nrhs, int dtype, double tol, int restart,
+                      int maxit, int* iters);
+
+/* ------------------------------------------------------------------ setup */
+
+/* Initial phase (Sec. 2): the SAP smoother on every test vector from x0 = 0
+ * (init_mode 0: one call of n_sweeps sweeps with b = v_j; init_mode 1:
+ * n_sweeps calls of one sweep, each v_j <- SAP(b = v_j, x0 = 0)), each v_j
+ * normalised, then P (mrhs_build_P) and D_c (mrhs_build_Dc). All test
+ * vectors are processed at once. tv0: device interleaved field, nrhs = ntv,
+ * storage dtype. */
+int mrhs_setup_init(mrhs_ctx ctx, const void* tv0, int dtype, int init_mode, int n_sweeps, int n_mr);
+
+/* Iterative refinement, Algorithm 2 with block length N_b = ntv (all test
+ * vectors at once): n_iter times { vc = R v; uc ~ D_c^-1 vc (coarse GMRES,
+ * coarse_tol, coarse_restart, coarse_maxit); x = P uc; x <- SAP^n_sweeps
+ * (b = v, x0 = x); v <- x normalised; then P and D_c rebuilt }.
+ * coarse_iters (host, may be NULL): [n_iter][ntv] coarse iteration counts.
+ * MRHS_ERR_STATE before mrhs_setup_init. */
+int mrhs_setup_refine(mrhs_ctx ctx, int n_iter, int n_sweeps, int n_mr, double coarse_tol, int coarse_restart,
+                      int coarse_maxit, int* coarse_iters);
+
+/* copy the test vectors / P out: host canonical [ntv][V][12] (complex128
+ * for MRHS_F64, complex64 for MRHS_F32). Column j of P is the orthonormalised
+ * v_j; its chirality-h part is the prolongation column (h, j). */
+int mrhs_get_tv(mrhs_ctx ctx, void* host, int host_dtype);
+int mrhs_get_P(mrhs_ctx ctx, void* host, int host_dtype);
+/* copy D_c out: host [nagg][9][2ntv][2ntv] complex */
+int mrhs_get_Dc(mrhs_ctx ctx, void* host, int host_dtype);
+
+/* ---------------------------------------------------------- measurement */
+
+/* Per-kernel timing with CUDA events recorded on the context's stream around
+ * every launch of the library's kernels. enable = 1 clears the counters and
+ * starts recording; enable = 0 stops. Adds two event records per launch. */
+int mrhs_profile(mrhs_ctx ctx, int enable);
+/* Entry idx (0-based) of the per-kernel totals recorded so far (waits for
+ * the stream): kernel class name (NUL-terminated, truncated to name_len),
+ * number of launches and total milliseconds. MRHS_ERR_ARG past the last
+ * entry. */
+int mrhs_profile_read(mrhs_ctx ctx, int idx, char* name, int name_len, long long* launches, double* ms);
+
+/* ------------------------------------------------------------ the judge */
+
+/* Two-level FGMRES(restart) on D x = b (Sec. 2: FGMRES preconditioned by the
+ * multigrid V-cycle), outer Arnoldi, D and residual in FP64; the
+ * preconditioner z = SAP^n_sweeps(b = r, x0 = P GMRES_c(R r)) runs in the
+ * context precision. b, x: host canonical [V][12] complex128. Stops at
+ * relative residual tol or maxit iterations. iters, relres: host, may be
+ * NULL. MRHS_ERR_NOCONV when maxit is reached first (x is still written). */
+int mrhs_solve_fgmres(mrhs_ctx ctx, const double* b, double* x, double tol, int restart, int maxit,
+                      double coarse_tol, int coarse_restart, int coarse_maxit, int n_sweeps, int n_mr,
+                      int* iters, double* relres);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MRHS_H */

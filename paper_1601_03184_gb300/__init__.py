@@ -1,0 +1,281 @@
+"""GB300 (sm_103a) multiple-right-hand-side setup of two-level DD-alpha-AMG
+for the Wilson-clover Dirac operator (arXiv:1601.03184).
+
+This module is a thin ctypes binding of the C ABI declared in include/mrhs.h.
+Every function named mrhs_* here has the same name, arguments and meaning as
+its C counterpart; it only marshals arguments (numpy arrays -> host pointers,
+torch CUDA tensors -> device pointers) and raises MrhsError on a non-zero
+status. All computation happens in libmrhs.so's CUDA kernels; there is no CPU
+fallback: if the library is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmrhs.so")
+
+# enums of mrhs.h
+MRHS_OK = 0
+MRHS_ERR_ARG, MRHS_ERR_SHAPE, MRHS_ERR_OOM, MRHS_ERR_CUDA = -1, -2, -3, -4
+MRHS_ERR_NOCONV, MRHS_ERR_NONFINITE, MRHS_ERR_STATE, MRHS_ERR_TIMEOUT = -5, -6, -7, -8
+MRHS_F64, MRHS_F32, MRHS_BF16, MRHS_F16 = 0, 1, 2, 3
+MRHS_PREC_FP64, MRHS_PREC_FP32, MRHS_PREC_MIX_BF16, MRHS_PREC_MIX_FP16 = 0, 1, 2, 3
+
+_VP = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_IP = ctypes.POINTER(ctypes.c_int)
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "mrhs_create": (_I, [ctypes.POINTER(_I), ctypes.POINTER(_I), _I, _I, _VP, ctypes.POINTER(_VP)]),
+    "mrhs_destroy": (None, [_VP]),
+    "mrhs_last_error": (ctypes.c_char_p, [_VP]),
+    "mrhs_sync": (_I, [_VP]),
+    "mrhs_info": (_I, [_VP, ctypes.POINTER(ctypes.c_longlong)]),
+    "mrhs_field_bytes": (ctypes.c_size_t, [_VP, _I, _I, _I]),
+    "mrhs_get_tables": (_I, [_VP, _VP, _VP, _VP]),
+    "mrhs_set_gauge": (_I, [_VP, _VP]),
+    "mrhs_build_clover": (_I, [_VP, _D, _D]),
+    "mrhs_get_clover": (_I, [_VP, _VP]),
+    "mrhs_pack": (_I, [_VP, _VP, _I, _VP, _I, _I]),
+    "mrhs_unpack": (_I, [_VP, _VP, _I, _VP, _I, _I]),
+    "mrhs_pack_coarse": (_I, [_VP, _VP, _I, _VP, _I, _I]),
+    "mrhs_unpack_coarse": (_I, [_VP, _VP, _I, _VP, _I, _I]),
+    "mrhs_apply_D": (_I, [_VP, _VP, _VP, _I, _I]),
+    "mrhs_apply_D_block": (_I, [_VP, _VP, _VP, _I, _I]),
+    "mrhs_sap": (_I, [_VP, _VP, _VP, _I, _I, _I, _I]),
+    "mrhs_set_tv": (_I, [_VP, _VP, _I]),
+    "mrhs_build_P": (_I, [_VP]),
+    "mrhs_build_Dc": (_I, [_VP]),
+    "mrhs_restrict": (_I, [_VP, _VP, _VP, _I, _I]),
+    "mrhs_prolong": (_I, [_VP, _VP, _VP, _I, _I]),
+    "mrhs_apply_Dc": (_I, [_VP, _VP, _VP, _I, _I]),
+    "mrhs_coarse_solve": (_I, [_VP, _VP, _VP, _I, _I, _D, _I, _I, _VP]),
+    "mrhs_setup_init": (_I, [_VP, _VP, _I, _I, _I, _I]),
+    "mrhs_setup_refine": (_I, [_VP, _I, _I, _I, _D, _I, _I, _VP]),
+    "mrhs_get_tv": (_I, [_VP, _VP, _I]),
+    "mrhs_get_P": (_I, [_VP, _VP, _I]),
+    "mrhs_get_Dc": (_I, [_VP, _VP, _I]),
+    "mrhs_profile": (_I, [_VP, _I]),
+    "mrhs_profile_read": (_I, [_VP, _I, ctypes.c_char_p, _I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D)]),
+    "mrhs_solve_fgmres": (_I, [_VP, _VP, _VP, _D, _I, _I, _D, _I, _I, _I, _I, _VP, _VP]),
+}
+
+_lib = None
+
+
+class MrhsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("mrhs status %d: %s" % (status, msg))
+        self.status = status
+
+
+def lib():
+    """Load libmrhs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise MrhsError(MRHS_ERR_STATE, "libmrhs.so not built (run paper_1601_03184_gb300/build.py)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _ptr(a):
+    """Host numpy array or torch tensor (host or device) -> void pointer."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"], "arrays must be C-contiguous"
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous(), "tensors must be contiguous"
+        return a.data_ptr()
+    if isinstance(a, int):
+        return a
+    raise TypeError("cannot pass %r as a pointer" % type(a))
+
+
+def _check(ctx, st):
+    if st != MRHS_OK:
+        msg = lib().mrhs_last_error(ctx)
+        raise MrhsError(st, msg.decode() if msg else "")
+    return st
+
+
+def _i4(v):
+    return (ctypes.c_int * 4)(*[int(x) for x in v])
+
+
+# ------------------------------------------------------------ C ABI mirror --
+def mrhs_create(dims, agg, ntv, prec, stream=None):
+    out = ctypes.c_void_p()
+    st = lib().mrhs_create(_i4(dims), _i4(agg), int(ntv), int(prec), stream, ctypes.byref(out))
+    _check(None, st)
+    return out.value
+
+
+def mrhs_destroy(ctx):
+    lib().mrhs_destroy(ctx)
+
+
+def mrhs_last_error(ctx):
+    m = lib().mrhs_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def mrhs_sync(ctx):
+    return _check(ctx, lib().mrhs_sync(ctx))
+
+
+def mrhs_info(ctx):
+    out = (ctypes.c_longlong * 8)()
+    _check(ctx, lib().mrhs_info(ctx, out))
+    return list(out)
+
+
+def mrhs_field_bytes(ctx, nrhs, dtype, coarse=0):
+    return int(lib().mrhs_field_bytes(ctx, int(nrhs), int(dtype), int(coarse)))
+
+
+def mrhs_get_tables(ctx, nbr, aggof, aggnbr):
+    return _check(ctx, lib().mrhs_get_tables(ctx, _ptr(nbr), _ptr(aggof), _ptr(aggnbr)))
+
+
+def mrhs_set_gauge(ctx, U):
+    return _check(ctx, lib().mrhs_set_gauge(ctx, _ptr(U)))
+
+
+def mrhs_build_clover(ctx, m0, csw):
+    return _check(ctx, lib().mrhs_build_clover(ctx, float(m0), float(csw)))
+
+
+def mrhs_get_clover(ctx, out):
+    return _check(ctx, lib().mrhs_get_clover(ctx, _ptr(out)))
+
+
+def mrhs_pack(ctx, host, host_dtype, dev, dev_dtype, nrhs):
+    return _check(ctx, lib().mrhs_pack(ctx, _ptr(host), host_dtype, _ptr(dev), dev_dtype, int(nrhs)))
+
+
+def mrhs_unpack(ctx, dev, dev_dtype, host, host_dtype, nrhs):
+    return _check(ctx, lib().mrhs_unpack(ctx, _ptr(dev), dev_dtype, _ptr(host), host_dtype, int(nrhs)))
+
+
+def mrhs_pack_coarse(ctx, host, host_dtype, dev, dev_dtype, nrhs):
+    return _check(ctx, lib().mrhs_pack_coarse(ctx, _ptr(host), host_dtype, _ptr(dev), dev_dtype, int(nrhs)))
+
+
+def mrhs_unpack_coarse(ctx, dev, dev_dtype, host, host_dtype, nrhs):
+    return _check(ctx, lib().mrhs_unpack_coarse(ctx, _ptr(dev), dev_dtype, _ptr(host), host_dtype, int(nrhs)))
+
+
+def mrhs_apply_D(ctx, x, y, nrhs, dtype):
+    return _check(ctx, lib().mrhs_apply_D(ctx, _ptr(x), _ptr(y), int(nrhs), int(dtype)))
+
+
+def mrhs_apply_D_block(ctx, x, y, nrhs, dtype):
+    return _check(ctx, lib().mrhs_apply_D_block(ctx, _ptr(x), _ptr(y), int(nrhs), int(dtype)))
+
+
+def mrhs_sap(ctx, b, x, nrhs, dtype, n_sweeps, n_mr):
+    return _check(ctx, lib().mrhs_sap(ctx, _ptr(b), _ptr(x), int(nrhs), int(dtype), int(n_sweeps), int(n_mr)))
+
+
+def mrhs_set_tv(ctx, tv, dtype):
+    return _check(ctx, lib().mrhs_set_tv(ctx, _ptr(tv), int(dtype)))
+
+
+def mrhs_build_P(ctx):
+    return _check(ctx, lib().mrhs_build_P(ctx))
+
+
+def mrhs_build_Dc(ctx):
+    return _check(ctx, lib().mrhs_build_Dc(ctx))
+
+
+def mrhs_restrict(ctx, v, vc, nrhs, dtype):
+    return _check(ctx, lib().mrhs_restrict(ctx, _ptr(v), _ptr(vc), int(nrhs), int(dtype)))
+
+
+def mrhs_prolong(ctx, uc, u, nrhs, dtype):
+    return _check(ctx, lib().mrhs_prolong(ctx, _ptr(uc), _ptr(u), int(nrhs), int(dtype)))
+
+
+def mrhs_apply_Dc(ctx, xc, yc, nrhs, dtype):
+    return _check(ctx, lib().mrhs_apply_Dc(ctx, _ptr(xc), _ptr(yc), int(nrhs), int(dtype)))
+
+
+def mrhs_coarse_solve(ctx, bc, xc, nrhs, dtype, tol, restart, maxit):
+    its = np.zeros(int(nrhs), np.int32)
+    _check(ctx, lib().mrhs_coarse_solve(ctx, _ptr(bc), _ptr(xc), int(nrhs), int(dtype), float(tol), int(restart),
+                                        int(maxit), _ptr(its)))
+    return its
+
+
+def mrhs_setup_init(ctx, tv0, dtype, init_mode, n_sweeps, n_mr):
+    return _check(ctx, lib().mrhs_setup_init(ctx, _ptr(tv0), int(dtype), int(init_mode), int(n_sweeps), int(n_mr)))
+
+
+def mrhs_setup_refine(ctx, n_iter, n_sweeps, n_mr, coarse_tol, coarse_restart, coarse_maxit, ntv=None):
+    its = np.zeros((max(int(n_iter), 1), int(ntv or 64)), np.int32)
+    _check(ctx, lib().mrhs_setup_refine(ctx, int(n_iter), int(n_sweeps), int(n_mr), float(coarse_tol),
+                                        int(coarse_restart), int(coarse_maxit), _ptr(its)))
+    return its
+
+
+def mrhs_get_tv(ctx, host, host_dtype):
+    return _check(ctx, lib().mrhs_get_tv(ctx, _ptr(host), int(host_dtype)))
+
+
+def mrhs_get_P(ctx, host, host_dtype):
+    return _check(ctx, lib().mrhs_get_P(ctx, _ptr(host), int(host_dtype)))
+
+
+def mrhs_get_Dc(ctx, host, host_dtype):
+    return _check(ctx, lib().mrhs_get_Dc(ctx, _ptr(host), int(host_dtype)))
+
+
+def mrhs_profile(ctx, enable):
+    return _check(ctx, lib().mrhs_profile(ctx, int(enable)))
+
+
+def mrhs_profile_read(ctx):
+    """All per-kernel totals: {name: (launches, total_ms)}."""
+    out = {}
+    i = 0
+    name = ctypes.create_string_buffer(64)
+    n = ctypes.c_longlong(0)
+    ms = ctypes.c_double(0)
+    while lib().mrhs_profile_read(ctx, i, name, 64, ctypes.byref(n), ctypes.byref(ms)) == MRHS_OK:
+        out[name.value.decode()] = (n.value, ms.value)
+        i += 1
+    return out
+
+
+def mrhs_solve_fgmres(ctx, b, x, tol, restart, maxit, coarse_tol, coarse_restart, coarse_maxit, n_sweeps, n_mr,
+                      allow_noconv=False):
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0)
+    st = lib().mrhs_solve_fgmres(ctx, _ptr(b), _ptr(x), float(tol), int(restart), int(maxit), float(coarse_tol),
+                                 int(coarse_restart), int(coarse_maxit), int(n_sweeps), int(n_mr),
+                                 ctypes.addressof(it), ctypes.addressof(rr))
+    if not (allow_noconv and st == MRHS_ERR_NOCONV):
+        _check(ctx, st)
+    return it.value, rr.value, st
+
+
+from .lattice import Lattice  # noqa: E402  (convenience wrapper over the functions above)

@@ -1,0 +1,150 @@
+// BLAS-like operations on interleaved multi-RHS arrays (Sec. 5 of the paper:
+// with the right-hand sides innermost these are elementwise per RHS; the
+// global sums are taken for all right-hand sides in one pass).
+// Arrays are `rows` complex rows of [2][N]: element (row, re/im, rhs).
+// Reductions use a fixed two-level tree (per-CTA partials, then a fixed-order
+// sum), so results are bitwise reproducible.
+#include "common.cuh"
+
+namespace mrhs {
+namespace {
+
+constexpr int kBlock = 256;
+
+int n_chunks(size_t rows, int N) {
+  size_t work = rows * (size_t)N;
+  size_t ch = work / (kBlock * 64);
+  if (ch < 1) ch = 1;
+  if (ch > 2048) ch = 2048;
+  return (int)ch;
+}
+
+// partial[k][chunk][r] = sum over the chunk's rows of conj(X_k) * Y
+template <class S>
+__global__ void k_multi_dot(const S* X, size_t stride, const S* Y, size_t rows, int N, int nchunk, double* part) {
+  using R = typename Real<S>::type;
+  __shared__ double sre[kBlock], sim[kBlock];
+  const int k = blockIdx.y, ch = blockIdx.x;
+  const size_t r0 = rows * ch / nchunk, r1 = rows * (ch + 1) / nchunk;
+  const S* Xk = X + (size_t)k * stride;
+  const int lanes = blockDim.x / N;
+  const int tid = threadIdx.x, r = tid % N, lane = tid / N;
+  double are = 0, aim = 0;
+  if (lane < lanes) {
+    R pre = 0, pim = 0;
+    int cnt = 0;
+    for (size_t row = r0 + lane; row < r1; row += lanes) {
+      R xr = to_r(Xk[fidx(row, 0, N, r)]), xi = to_r(Xk[fidx(row, 1, N, r)]);
+      R yr = to_r(Y[fidx(row, 0, N, r)]), yi = to_r(Y[fidx(row, 1, N, r)]);
+      pre = fma(xr, yr, fma(xi, yi, pre));
+      pim = fma(xr, yi, fma(-xi, yr, pim));
+      if (++cnt == 32) {
+        are += pre;
+        aim += pim;
+        pre = pim = 0;
+        cnt = 0;
+      }
+    }
+    are += pre;
+    aim += pim;
+  }
+  sre[tid] = are;
+  sim[tid] = aim;
+  __syncthreads();
+  if (tid < N) {
+    double a = 0, b = 0;
+    for (int l = 0; l < lanes; ++l) {
+      a += sre[l * N + tid];
+      b += sim[l * N + tid];
+    }
+    double* o = part + (((size_t)k * nchunk + ch) * N + tid) * 2;
+    o[0] = a;
+    o[1] = b;
+  }
+}
+
+__global__ void k_sum_chunks(const double* part, int K, int nchunk, int N, double* out) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= K * N) return;
+  int k = t / N, r = t % N;
+  double a = 0, b = 0;
+  for (int ch = 0; ch < nchunk; ++ch) {
+    a += part[(((size_t)k * nchunk + ch) * N + r) * 2];
+    b += part[(((size_t)k * nchunk + ch) * N + r) * 2 + 1];
+  }
+  out[2 * t] = a;
+  out[2 * t + 1] = b;
+}
+
+template <class S>
+__global__ void k_multi_axpy(const S* X, size_t stride, int K, S* Y, size_t rows, int N, const double* coef,
+                             double sign) {
+  using R = typename Real<S>::type;
+  size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= rows * N) return;
+  int r = (int)(t % N);
+  size_t row = t / N;
+  R yr = to_r(Y[fidx(row, 0, N, r)]), yi = to_r(Y[fidx(row, 1, N, r)]);
+  for (int k = 0; k < K; ++k) {
+    R cr = (R)(sign * coef[((size_t)k * N + r) * 2]), ci = (R)(sign * coef[((size_t)k * N + r) * 2 + 1]);
+    const S* Xk = X + (size_t)k * stride;
+    R xr = to_r(Xk[fidx(row, 0, N, r)]), xi = to_r(Xk[fidx(row, 1, N, r)]);
+    yr = fma(cr, xr, fma(-ci, xi, yr));
+    yi = fma(cr, xi, fma(ci, xr, yi));
+  }
+  Y[fidx(row, 0, N, r)] = from_r<S>(yr);
+  Y[fidx(row, 1, N, r)] = from_r<S>(yi);
+}
+
+// X[., r] *= 1/sqrt(nrm2[r]) (0 stays 0)
+template <class S>
+__global__ void k_inv_sqrt_scale(S* X, size_t rows, int N, const double* nrm2) {
+  using R = typename Real<S>::type;
+  size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= rows * N) return;
+  int r = (int)(t % N);
+  size_t row = t / N;
+  double n = nrm2[2 * r];
+  R s = n > 0 ? (R)(1.0 / sqrt(n)) : (R)0;
+  X[fidx(row, 0, N, r)] = from_r<S>(to_r(X[fidx(row, 0, N, r)]) * s);
+  X[fidx(row, 1, N, r)] = from_r<S>(to_r(X[fidx(row, 1, N, r)]) * s);
+}
+
+}  // namespace
+
+void multi_dot(mrhs_ctx c, const void* X, size_t stride, int K, const void* Y, size_t rows, int N, int dtype,
+               double* out) {
+  MRHS_REQUIRE(N >= 1 && N <= kBlock && K >= 1, MRHS_ERR_ARG, "multi_dot: bad sizes");
+  int nch = n_chunks(rows, N);
+  double* part = (double*)scratch(c, SC_RED, sizeof(double) * 2 * (size_t)K * nch * N);
+  dim3 grid(nch, K);
+  Prof pr(c, "multi_dot");
+  MRHS_DISPATCH(dtype, S, (k_multi_dot<S><<<grid, kBlock, 0, c->stream>>>((const S*)X, stride, (const S*)Y, rows, N, nch, part)));
+  MRHS_LAUNCH_CHECK("multi_dot");
+  k_sum_chunks<<<grid_for((size_t)K * N, 128), 128, 0, c->stream>>>(part, K, nch, N, out);
+  MRHS_LAUNCH_CHECK("sum_chunks");
+}
+
+// out[r] (as [N][2], imaginary part 0) = |X_r|^2
+void norms(mrhs_ctx c, const void* X, size_t rows, int N, int dtype, double* out) {
+  multi_dot(c, X, 0, 1, X, rows, N, dtype, out);
+}
+
+void multi_axpy(mrhs_ctx c, const void* X, size_t stride, int K, void* Y, size_t rows, int N, int dtype,
+                const double* coef, double sign) {
+  size_t work = rows * N;
+  Prof pr(c, "multi_axpy");
+  MRHS_DISPATCH(dtype, S, (k_multi_axpy<S><<<grid_for(work, kBlock), kBlock, 0, c->stream>>>((const S*)X, stride, K, (S*)Y, rows, N, coef, sign)));
+  MRHS_LAUNCH_CHECK("multi_axpy");
+}
+
+// normalise every right-hand side of X to unit 2-norm
+void normalise_rhs(mrhs_ctx c, void* X, size_t rows, int N, int dtype) {
+  double* nrm = (double*)scratch(c, SC_MISC, sizeof(double) * 2 * N);
+  norms(c, X, rows, N, dtype, nrm);
+  size_t work = rows * N;
+  MRHS_DISPATCH(dtype, S, (k_inv_sqrt_scale<S><<<grid_for(work, kBlock), kBlock, 0, c->stream>>>((S*)X, rows, N, nrm)));
+  MRHS_LAUNCH_CHECK("normalise");
+}
+
+}  // namespace mrhs

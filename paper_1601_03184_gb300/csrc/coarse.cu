@@ -1,0 +1,576 @@
+// Coarse grid: D_c = P^dag D P assembly, restriction R = P^dag (Algorithm 3
+// of the paper, all right-hand sides at once), prolongation, the coarse
+// 9-point stencil and the multi-RHS coarse GMRES.
+#include "stencil.cuh"
+
+namespace mrhs {
+namespace {
+
+constexpr int kSites = 8;  // sites staged per chunk in the contractions
+
+struct Agg4 {
+  int a[4];
+};
+
+// local site index of face site f of an aggregate: l_mu fixed to lmu, the
+// other three coordinates enumerated lexicographically
+__device__ __forceinline__ int face_site(const Agg4& g, int mu, int lmu, int f) {
+  int l[4];
+  for (int m = 0; m < 4; ++m) {
+    if (m == mu) {
+      l[m] = lmu;
+    } else {
+      l[m] = f % g.a[m];
+      f /= g.a[m];
+    }
+  }
+  return l[0] + g.a[0] * (l[1] + g.a[1] * (l[2] + g.a[2] * l[3]));
+}
+
+// column col = (h', j) of P: P_j restricted to chirality h', at site n
+template <class SP, class R>
+__device__ __forceinline__ void load_pcol(cx<R> psi[12], const SP* P, int n, int Nt, int col) {
+  const int hp = col / Nt, j = col % Nt;
+#pragma unroll
+  for (int c = 0; c < 12; ++c)
+    psi[c] = (c / 6 == hp) ? ld<SP, R>(P, (size_t)n * 12 + c, Nt, j) : mk<R>(0, 0);
+}
+
+template <int MU, class SP, class R>
+__device__ __forceinline__ void hop_pcol(cx<R> out[12], const SP* P, const cx<R>* U, const int* nbr, int s, int dir,
+                                         int Nt, int col, bool only_same_block, int Va) {
+  int e = nbr[s * 8 + (dir > 0 ? 0 : 4) + MU];
+  int n = e & 0x3fffffff;
+  if (only_same_block && n / Va != s / Va) return;
+  R sg = (e & 0x40000000) ? (R)-1 : (R)1;
+  cx<R> psi[12];
+  load_pcol<SP, R>(psi, P, n, Nt, col);
+  if (dir > 0) hop_reg<MU, +1, R>(out, psi, U + (size_t)s * 36 + MU * 9, sg);
+  else hop_reg<MU, -1, R>(out, psi, U + (size_t)n * 36 + MU * 9, sg);
+}
+
+// One CTA per (aggregate A, stencil entry k). Columns (h', j), rows (h, i):
+//   k = 0:      sum_{x in A} P_(h,i)(x)^dag [A(x) + hops inside A] P_(h',j)
+//   k = 1+mu:   sum over the +mu face of A of P_(h,i)(x)^dag hop_{+mu} P_(h',j)(x+mu)
+//   k = 5+mu:   the same for the -mu face and hop_{-mu}
+template <class SP, class R, int EPT>
+__global__ void k_coarse_op(const SP* __restrict__ P, const cx<R>* __restrict__ U, const R* __restrict__ Acl,
+                            const int* __restrict__ nbr, int Nt, Agg4 ag, int Va, cx<R>* __restrict__ Dc) {
+  extern __shared__ double smem_d[];
+  const int A = blockIdx.x / 9, k = blockIdx.x % 9;
+  const int nc = 2 * Nt;
+  cx<R>* W = (cx<R>*)smem_d;               // [kSites][12][nc]
+  cx<R>* Pc = W + kSites * 12 * nc;        // [kSites][12][Nt]
+  const int mu = k == 0 ? -1 : (k - 1) % 4;
+  const int nsite = k == 0 ? Va : Va / ag.a[mu];
+  const int lmu = k == 0 ? 0 : (k <= 4 ? ag.a[mu] - 1 : 0);
+  const int dir = k <= 4 ? +1 : -1;
+  cx<R> acc[EPT];
+#pragma unroll
+  for (int m = 0; m < EPT; ++m) acc[m] = mk<R>(0, 0);
+  for (int q0 = 0; q0 < nsite; q0 += kSites) {
+    const int nq = min(kSites, nsite - q0);
+    for (int w = threadIdx.x; w < nq * nc; w += blockDim.x) {
+      int q = w / nc, col = w % nc;
+      int l = k == 0 ? q0 + q : face_site(ag, mu, lmu, q0 + q);
+      int s = A * Va + l;
+      cx<R> out[12];
+#pragma unroll
+      for (int c = 0; c < 12; ++c) out[c] = mk<R>(0, 0);
+      if (k == 0) {
+        cx<R> psi[12];
+        load_pcol<SP, R>(psi, P, s, Nt, col);
+        clover_apply_reg<R>(out, psi, Acl + (size_t)s * 72);
+        for (int d = -1; d <= 1; d += 2) {
+          hop_pcol<0, SP, R>(out, P, U, nbr, s, d, Nt, col, true, Va);
+          hop_pcol<1, SP, R>(out, P, U, nbr, s, d, Nt, col, true, Va);
+          hop_pcol<2, SP, R>(out, P, U, nbr, s, d, Nt, col, true, Va);
+          hop_pcol<3, SP, R>(out, P, U, nbr, s, d, Nt, col, true, Va);
+        }
+      } else {
+        switch (mu) {
+          case 0: hop_pcol<0, SP, R>(out, P, U, nbr, s, dir, Nt, col, false, Va); break;
+          case 1: hop_pcol<1, SP, R>(out, P, U, nbr, s, dir, Nt, col, false, Va); break;
+          case 2: hop_pcol<2, SP, R>(out, P, U, nbr, s, dir, Nt, col, false, Va); break;
+          default: hop_pcol<3, SP, R>(out, P, U, nbr, s, dir, Nt, col, false, Va); break;
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 12; ++c) W[(q * 12 + c) * nc + col] = out[c];
+    }
+    for (int w = threadIdx.x; w < nq * 12 * Nt; w += blockDim.x) {
+      int q = w / (12 * Nt), c = (w / Nt) % 12, i = w % Nt;
+      int l = k == 0 ? q0 + q : face_site(ag, mu, lmu, q0 + q);
+      Pc[w] = ld<SP, R>(P, ((size_t)A * Va + l) * 12 + c, Nt, i);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < EPT; ++m) {
+      int e = threadIdx.x + m * blockDim.x;
+      if (e < nc * nc) {
+        int row = e / nc, col = e % nc;
+        int h = row / Nt, i = row % Nt;
+        for (int q = 0; q < nq; ++q)
+#pragma unroll
+          for (int cc = 0; cc < 6; ++cc) {
+            int c = 6 * h + cc;
+            fmac_(acc[m], Pc[(q * 12 + c) * Nt + i], W[(q * 12 + c) * nc + col]);
+          }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int m = 0; m < EPT; ++m) {
+    int e = threadIdx.x + m * blockDim.x;
+    if (e < nc * nc) Dc[((size_t)A * 9 + k) * nc * nc + e] = acc[m];
+  }
+}
+
+// vc[A][(h,i)][r] = sum_{x in A, c in h} conj(P_i(x,c)) v(x,c,r)
+template <class SP, class SV, class SC, int EPT>
+__global__ void k_restrict(const SP* __restrict__ P, const SV* __restrict__ v, SC* __restrict__ vc, int Nt, int N,
+                           int Va) {
+  using R = typename Real<SC>::type;
+  extern __shared__ double smem_d[];
+  const int A = blockIdx.x;
+  const int nc = 2 * Nt;
+  cx<R>* Pc = (cx<R>*)smem_d;          // [kSites][12][Nt]
+  cx<R>* Xc = Pc + kSites * 12 * Nt;   // [kSites][12][N]
+  cx<R> acc[EPT];
+#pragma unroll
+  for (int m = 0; m < EPT; ++m) acc[m] = mk<R>(0, 0);
+  for (int q0 = 0; q0 < Va; q0 += kSites) {
+    const int nq = min(kSites, Va - q0);
+    for (int w = threadIdx.x; w < nq * 12 * Nt; w += blockDim.x) {
+      int q = w / (12 * Nt), c = (w / Nt) % 12, i = w % Nt;
+      Pc[w] = ld<SP, R>(P, ((size_t)A * Va + q0 + q) * 12 + c, Nt, i);
+    }
+    for (int w = threadIdx.x; w < nq * 12 * N; w += blockDim.x) {
+      int q = w / (12 * N), c = (w / N) % 12, r = w % N;
+      Xc[w] = ld<SV, R>(v, ((size_t)A * Va + q0 + q) * 12 + c, N, r);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < EPT; ++m) {
+      int e = threadIdx.x + m * blockDim.x;
+      if (e < nc * N) {
+        int row = e / N, r = e % N;
+        int h = row / Nt, i = row % Nt;
+        for (int q = 0; q < nq; ++q)
+#pragma unroll
+          for (int cc = 0; cc < 6; ++cc) {
+            int c = 6 * h + cc;
+            fmac_(acc[m], Pc[(q * 12 + c) * Nt + i], Xc[(q * 12 + c) * N + r]);
+          }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int m = 0; m < EPT; ++m) {
+    int e = threadIdx.x + m * blockDim.x;
+    if (e < nc * N) {
+      int row = e / N, r = e % N;
+      st<SC, R>(vc, (size_t)A * nc + row, N, r, acc[m]);
+    }
+  }
+}
+
+// u(x,c,r) = sum_j P_j(x,c) uc[A(x)][(h(c), j)][r]
+template <class SP, class SC, class SU>
+__global__ void k_prolong(const SP* __restrict__ P, const SC* __restrict__ uc, SU* __restrict__ u, int Nt, int N,
+                          int Va, size_t nwork) {
+  using R = typename Real<SC>::type;
+  size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= nwork) return;
+  int r = (int)(t % N);
+  size_t row = t / N;  // s*12 + c
+  int c = (int)(row % 12);
+  size_t s = row / 12;
+  size_t A = s / Va;
+  int h = c / 6;
+  cx<R> acc = mk<R>(0, 0);
+  for (int j = 0; j < Nt; ++j)
+    fma_(acc, ld<SP, R>(P, row, Nt, j), ld<SC, R>(uc, A * 2 * Nt + h * Nt + j, N, r));
+  st<SU, R>(u, row, N, r, acc);
+}
+
+// y[A][row][r] = sum_k sum_col Dc[A][k][row][col] x[nbr_k(A)][col][r]
+template <class SC>
+__global__ void k_apply_dc(const cx<typename Real<SC>::type>* __restrict__ Dc, const SC* __restrict__ x,
+                           SC* __restrict__ y, const int* __restrict__ aggnbr, int nc, int N, size_t nwork) {
+  using R = typename Real<SC>::type;
+  size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= nwork) return;
+  int r = (int)(t % N);
+  size_t q = t / N;
+  int row = (int)(q % nc);
+  int A = (int)(q / nc);
+  cx<R> acc = mk<R>(0, 0);
+  for (int k = 0; k < 9; ++k) {
+    int B = k == 0 ? A : aggnbr[A * 8 + k - 1];
+    const cx<R>* d = Dc + (((size_t)A * 9 + k) * nc + row) * nc;
+    for (int col = 0; col < nc; ++col) fma_(acc, d[col], ld<SC, R>(x, (size_t)B * nc + col, N, r));
+  }
+  st<SC, R>(y, (size_t)A * nc + row, N, r, acc);
+}
+
+template <class S>
+__global__ void k_sub_from(const S* b, S* w, size_t n) {  // w = b - w
+  size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t < n) w[t] = from_r<S>((double)to_r(b[t]) - (double)to_r(w[t]));
+}
+
+template <class S>
+__global__ void k_scale_rhs(const S* x, S* y, size_t rows, int N, const double* s) {
+  using R = typename Real<S>::type;
+  size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= rows * N) return;
+  int r = (int)(t % N);
+  size_t row = t / N;
+  R f = (R)s[r];
+  y[fidx(row, 0, N, r)] = from_r<S>(to_r(x[fidx(row, 0, N, r)]) * f);
+  y[fidx(row, 1, N, r)] = from_r<S>(to_r(x[fidx(row, 1, N, r)]) * f);
+}
+
+// ------------------------------------------------------- GMRES state ------
+struct GmState {
+  cx<double>* H;    // [N][m+1][m]
+  cx<double>* cs;   // [N][m]
+  cx<double>* sn;   // [N][m]
+  cx<double>* g;    // [N][m+1]
+  double* y;        // [m][N][2]  (coefficients for the solution update)
+  double* h1;       // [m+1][N][2]
+  double* h2;       // [m+1][N][2]
+  double* hn2;      // [N][2]
+  double* beta2;    // [N][2]
+  double* bnorm2;   // [N][2]
+  double* inv;      // [N]
+  int* conv;        // [N]
+  int* active;      // [N]
+  int* its;         // [N]
+  int* kend;        // [N]
+  int* counter;     // [1]
+};
+
+__global__ void k_gm_init(GmState st, int N) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  st.conv[r] = st.bnorm2[2 * r] == 0.0;
+  st.its[r] = 0;
+  st.active[r] = 0;
+  st.kend[r] = 0;
+}
+
+// start of a cycle: r = b - A x is in w with |w|^2 in beta2
+__global__ void k_gm_start(GmState st, int N, int m, double tol, int maxit) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  st.kend[r] = 0;
+  st.active[r] = 0;
+  st.inv[r] = 0;
+  if (st.conv[r] || st.its[r] >= maxit) return;
+  double beta = sqrt(st.beta2[2 * r]);
+  if (beta <= tol * sqrt(st.bnorm2[2 * r])) {
+    st.conv[r] = 1;
+    return;
+  }
+  st.active[r] = 1;
+  st.inv[r] = 1.0 / beta;
+  for (int i = 0; i <= m; ++i) st.g[(size_t)r * (m + 1) + i] = mk(0.0, 0.0);
+  st.g[(size_t)r * (m + 1)] = mk(beta, 0.0);
+  atomicAdd(st.counter, 1);
+}
+
+// Arnoldi column k: h = h1 + h2 (two classical Gram-Schmidt passes), then
+// the Givens rotations and the residual estimate |g_{k+1}|
+__global__ void k_gm_step(GmState st, int N, int m, int k, double tol, int maxit) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  st.inv[r] = 0;
+  if (!st.active[r]) return;
+  cx<double>* H = st.H + (size_t)r * (m + 1) * m;
+  cx<double>* cs = st.cs + (size_t)r * m;
+  cx<double>* sn = st.sn + (size_t)r * m;
+  cx<double>* g = st.g + (size_t)r * (m + 1);
+  for (int i = 0; i <= k; ++i)
+    H[i * m + k] = mk(st.h1[((size_t)i * N + r) * 2] + st.h2[((size_t)i * N + r) * 2],
+                      st.h1[((size_t)i * N + r) * 2 + 1] + st.h2[((size_t)i * N + r) * 2 + 1]);
+  double hk1 = sqrt(st.hn2[2 * r]);
+  H[(k + 1) * m + k] = mk(hk1, 0.0);
+  for (int i = 0; i < k; ++i) {
+    cx<double> a = H[i * m + k], b = H[(i + 1) * m + k];
+    H[i * m + k] = cnj(cs[i]) * a + cnj(sn[i]) * b;
+    H[(i + 1) * m + k] = mk(0.0, 0.0) - sn[i] * a + cs[i] * b;
+  }
+  cx<double> a = H[k * m + k], b = H[(k + 1) * m + k];
+  double nu = sqrt(a.re * a.re + a.im * a.im + b.re * b.re + b.im * b.im);
+  if (nu == 0) {
+    cs[k] = mk(1.0, 0.0);
+    sn[k] = mk(0.0, 0.0);
+  } else {
+    cs[k] = scale(a, 1.0 / nu);
+    sn[k] = scale(b, 1.0 / nu);
+  }
+  H[k * m + k] = mk(nu, 0.0);
+  H[(k + 1) * m + k] = mk(0.0, 0.0);
+  cx<double> g0 = g[k];
+  g[k] = cnj(cs[k]) * g0;
+  g[k + 1] = mk(0.0, 0.0) - sn[k] * g0;
+  st.its[r] += 1;
+  st.kend[r] = k + 1;
+  double res = sqrt(g[k + 1].re * g[k + 1].re + g[k + 1].im * g[k + 1].im);
+  bool conv = res <= tol * sqrt(st.bnorm2[2 * r]) || hk1 == 0;
+  if (conv) st.conv[r] = 1;
+  if (conv || st.its[r] >= maxit || k + 1 == m) {
+    st.active[r] = 0;
+  } else {
+    st.inv[r] = 1.0 / hk1;
+    atomicAdd(st.counter, 1);
+  }
+}
+
+// back substitution of the leading kend x kend triangle, y = coefficients
+__global__ void k_gm_solve(GmState st, int N, int m) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  const cx<double>* H = st.H + (size_t)r * (m + 1) * m;
+  const cx<double>* g = st.g + (size_t)r * (m + 1);
+  int ke = st.kend[r];
+  cx<double> yv[64];
+  for (int i = ke - 1; i >= 0; --i) {
+    cx<double> c = g[i];
+    for (int l = i + 1; l < ke; ++l) c = c - H[i * m + l] * yv[l];
+    double d = H[i * m + i].re;  // real and positive after the rotation
+    yv[i] = scale(c, 1.0 / d);
+  }
+  for (int i = 0; i < m; ++i) {
+    cx<double> v = i < ke ? yv[i] : mk(0.0, 0.0);
+    st.y[((size_t)i * N + r) * 2] = v.re;
+    st.y[((size_t)i * N + r) * 2 + 1] = v.im;
+  }
+}
+
+template <class T>
+T* carve(char*& p, size_t n) {
+  T* r = (T*)p;
+  p += ((n * sizeof(T) + 255) / 256) * 256;
+  return r;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host ---
+void build_Dc(mrhs_ctx c) {
+  MRHS_REQUIRE(c->have_P, MRHS_ERR_STATE, "mrhs_build_Dc before mrhs_build_P");
+  MRHS_REQUIRE(c->have_clover, MRHS_ERR_STATE, "mrhs_build_Dc before mrhs_build_clover");
+  const int Nt = c->ntv, nc = 2 * Nt;
+  size_t n = (size_t)c->g.nagg * 9 * nc * nc;
+  if (!c->Dc) c->Dc = dalloc(c, n * 2 * dtype_size(c->work_dtype));
+  Agg4 ag;
+  for (int m = 0; m < 4; ++m) ag.a[m] = c->g.a[m];
+  int threads = std::max(128, ((nc * nc + 15) / 16 + 31) / 32 * 32);
+  MRHS_REQUIRE(threads <= 1024, MRHS_ERR_SHAPE, "ntv too large for the coarse-operator kernel");
+  MRHS_DISPATCH(c->tv_dtype, SP, {
+    using R = typename Real<SP>::type;
+    size_t smem = sizeof(cx<R>) * kSites * 12 * (size_t)(nc + Nt);
+    const cx<R>* U = (const cx<R>*)(sizeof(R) == 8 ? (const void*)c->U64 : (const void*)c->U32);
+    const R* Acl = (const R*)(sizeof(R) == 8 ? (const void*)c->A64 : (const void*)c->A32);
+    Prof pr(c, "coarse_op");
+    auto kern = k_coarse_op<SP, R, 16>;
+    MRHS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<c->g.nagg * 9, threads, smem, c->stream>>>((const SP*)c->P, U, Acl, c->nbr, Nt, ag, c->g.Va,
+                                                      (cx<R>*)c->Dc);
+  });
+  MRHS_LAUNCH_CHECK("coarse_op");
+  c->have_Dc = true;
+}
+
+// restriction from a fine field of type dv into a coarse field of type dc
+void restrict_typed(mrhs_ctx c, const void* v, int dv, void* vc, int dc, int N) {
+  MRHS_REQUIRE(c->have_P, MRHS_ERR_STATE, "restriction before mrhs_build_P");
+  MRHS_REQUIRE(N >= 1 && N <= 64, MRHS_ERR_ARG, "restriction: 1 <= nrhs <= 64");
+  const int Nt = c->ntv, nc = 2 * Nt;
+  int threads = std::max(64, ((nc * N + 7) / 8 + 31) / 32 * 32);
+  MRHS_REQUIRE(threads <= 1024, MRHS_ERR_SHAPE, "restriction: ntv*nrhs too large");
+  MRHS_REQUIRE(dc == MRHS_F64 || dc == MRHS_F32, MRHS_ERR_ARG, "coarse fields are F64 or F32");
+  Prof pr(c, "restrict");
+  MRHS_DISPATCH(c->tv_dtype, SP, MRHS_DISPATCH(dv, SV, {
+    if (dc == MRHS_F64) {
+      size_t smem = sizeof(cx<double>) * kSites * 12 * (size_t)(Nt + N);
+      auto kern = k_restrict<SP, SV, double, 8>;
+      MRHS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      kern<<<c->g.nagg, threads, smem, c->stream>>>((const SP*)c->P, (const SV*)v, (double*)vc, Nt, N, c->g.Va);
+    } else {
+      size_t smem = sizeof(cx<float>) * kSites * 12 * (size_t)(Nt + N);
+      auto kern = k_restrict<SP, SV, float, 8>;
+      MRHS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      kern<<<c->g.nagg, threads, smem, c->stream>>>((const SP*)c->P, (const SV*)v, (float*)vc, Nt, N, c->g.Va);
+    }
+  }));
+  MRHS_LAUNCH_CHECK("restrict");
+}
+
+void prolong_typed(mrhs_ctx c, const void* uc, int dc, void* u, int du, int N) {
+  MRHS_REQUIRE(c->have_P, MRHS_ERR_STATE, "prolongation before mrhs_build_P");
+  MRHS_REQUIRE(dc == MRHS_F64 || dc == MRHS_F32, MRHS_ERR_ARG, "coarse fields are F64 or F32");
+  size_t work = (size_t)c->g.V * 12 * N;
+  Prof pr(c, "prolong");
+  MRHS_DISPATCH(c->tv_dtype, SP, MRHS_DISPATCH(du, SU, {
+    if (dc == MRHS_F64)
+      k_prolong<SP, double, SU><<<grid_for(work, 256), 256, 0, c->stream>>>((const SP*)c->P, (const double*)uc, (SU*)u, c->ntv, N, c->g.Va, work);
+    else
+      k_prolong<SP, float, SU><<<grid_for(work, 256), 256, 0, c->stream>>>((const SP*)c->P, (const float*)uc, (SU*)u, c->ntv, N, c->g.Va, work);
+  }));
+  MRHS_LAUNCH_CHECK("prolong");
+}
+
+void restrict_(mrhs_ctx c, const void* v, void* vc, int nrhs, int dtype) {
+  MRHS_REQUIRE(dtype == c->work_dtype, MRHS_ERR_ARG, "restriction: dtype must be the context's work type");
+  restrict_typed(c, v, dtype, vc, dtype, nrhs);
+}
+
+void prolong(mrhs_ctx c, const void* uc, void* u, int nrhs, int dtype) {
+  MRHS_REQUIRE(dtype == c->work_dtype, MRHS_ERR_ARG, "prolongation: dtype must be the context's work type");
+  prolong_typed(c, uc, dtype, u, dtype, nrhs);
+}
+
+void apply_Dc(mrhs_ctx c, const void* xc, void* yc, int nrhs, int dtype) {
+  MRHS_REQUIRE(c->have_Dc, MRHS_ERR_STATE, "D_c used before mrhs_build_Dc");
+  MRHS_REQUIRE(dtype == c->work_dtype, MRHS_ERR_ARG, "D_c apply: dtype must be the context's work type");
+  const int nc = 2 * c->ntv;
+  size_t work = (size_t)c->g.nagg * nc * nrhs;
+  Prof pr(c, "apply_dc");
+  if (dtype == MRHS_F64)
+    k_apply_dc<double><<<grid_for(work, 256), 256, 0, c->stream>>>((const cx<double>*)c->Dc, (const double*)xc, (double*)yc, c->aggnbr, nc, nrhs, work);
+  else
+    k_apply_dc<float><<<grid_for(work, 256), 256, 0, c->stream>>>((const cx<float>*)c->Dc, (const float*)xc, (float*)yc, c->aggnbr, nc, nrhs, work);
+  MRHS_LAUNCH_CHECK("apply_dc");
+}
+
+void coarse_solve(mrhs_ctx c, const void* bc, void* xc, int N, int dtype, double tol, int m, int maxit, int* iters) {
+  MRHS_REQUIRE(c->have_Dc, MRHS_ERR_STATE, "coarse solve before mrhs_build_Dc");
+  MRHS_REQUIRE(dtype == c->work_dtype, MRHS_ERR_ARG, "coarse solve: dtype must be the context's work type");
+  MRHS_REQUIRE(N >= 1 && N <= 256 && m >= 1 && m <= 64 && maxit >= 0 && tol >= 0, MRHS_ERR_ARG,
+               "coarse solve: need 1 <= nrhs <= 256, 1 <= restart <= 64, maxit >= 0, tol >= 0");
+  const size_t rows = (size_t)c->g.nagg * 2 * c->ntv;
+  const size_t fe = rows * 2 * N;  // elements of one coarse field
+  const size_t es = dtype_size(dtype);
+  char* basis = (char*)scratch(c, SC_KRYLOV, (size_t)(m + 2) * fe * es);
+  char* w = basis + (size_t)(m + 1) * fe * es;
+  auto Vk = [&](int k) { return (void*)(basis + (size_t)k * fe * es); };
+  size_t sbytes = 0;
+  sbytes += 3 * sizeof(cx<double>) * N * (size_t)(m + 1) * m + 256 * 16;
+  char* sp = (char*)scratch(c, SC_HESS, sbytes + sizeof(double) * 16 * N * (size_t)(m + 2) + 4096);
+  GmState st;
+  st.H = carve<cx<double>>(sp, (size_t)N * (m + 1) * m);
+  st.cs = carve<cx<double>>(sp, (size_t)N * m);
+  st.sn = carve<cx<double>>(sp, (size_t)N * m);
+  st.g = carve<cx<double>>(sp, (size_t)N * (m + 1));
+  st.y = carve<double>(sp, (size_t)m * N * 2);
+  st.h1 = carve<double>(sp, (size_t)(m + 1) * N * 2);
+  st.h2 = carve<double>(sp, (size_t)(m + 1) * N * 2);
+  st.hn2 = carve<double>(sp, (size_t)N * 2);
+  st.beta2 = carve<double>(sp, (size_t)N * 2);
+  st.bnorm2 = carve<double>(sp, (size_t)N * 2);
+  st.inv = carve<double>(sp, (size_t)N);
+  st.conv = carve<int>(sp, N);
+  st.active = carve<int>(sp, N);
+  st.its = carve<int>(sp, N);
+  st.kend = carve<int>(sp, N);
+  st.counter = carve<int>(sp, 1);
+  int* hcount = c->hflag + 1;
+  auto read_counter = [&]() {
+    MRHS_CUDA(cudaMemcpyAsync(hcount, st.counter, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    MRHS_CUDA(cudaStreamSynchronize(c->stream));
+    return *hcount;
+  };
+  auto scale_into = [&](const void* x, void* y) {
+    MRHS_DISPATCH(dtype, S, (k_scale_rhs<S><<<grid_for(rows * N, 256), 256, 0, c->stream>>>((const S*)x, (S*)y, rows, N, st.inv)));
+    MRHS_LAUNCH_CHECK("scale_rhs");
+  };
+  MRHS_CUDA(cudaMemsetAsync(xc, 0, fe * es, c->stream));
+  norms(c, bc, rows, N, dtype, st.bnorm2);
+  k_gm_init<<<grid_for(N, 64), 64, 0, c->stream>>>(st, N);
+  MRHS_LAUNCH_CHECK("gm_init");
+  for (;;) {
+    apply_Dc(c, xc, w, N, dtype);
+    MRHS_DISPATCH(dtype, S, (k_sub_from<S><<<grid_for(fe, 256), 256, 0, c->stream>>>((const S*)bc, (S*)w, fe)));
+    MRHS_LAUNCH_CHECK("sub_from");
+    norms(c, w, rows, N, dtype, st.beta2);
+    MRHS_CUDA(cudaMemsetAsync(st.counter, 0, sizeof(int), c->stream));
+    k_gm_start<<<grid_for(N, 64), 64, 0, c->stream>>>(st, N, m, tol, maxit);
+    MRHS_LAUNCH_CHECK("gm_start");
+    if (read_counter() == 0) break;
+    scale_into(w, Vk(0));
+    int kmax = 0;
+    for (int k = 0; k < m; ++k) {
+      apply_Dc(c, Vk(k), w, N, dtype);
+      multi_dot(c, Vk(0), fe, k + 1, w, rows, N, dtype, st.h1);
+      multi_axpy(c, Vk(0), fe, k + 1, w, rows, N, dtype, st.h1, -1.0);
+      multi_dot(c, Vk(0), fe, k + 1, w, rows, N, dtype, st.h2);
+      multi_axpy(c, Vk(0), fe, k + 1, w, rows, N, dtype, st.h2, -1.0);
+      norms(c, w, rows, N, dtype, st.hn2);
+      MRHS_CUDA(cudaMemsetAsync(st.counter, 0, sizeof(int), c->stream));
+      k_gm_step<<<grid_for(N, 64), 64, 0, c->stream>>>(st, N, m, k, tol, maxit);
+      MRHS_LAUNCH_CHECK("gm_step");
+      kmax = k + 1;
+      int more = read_counter();
+      if (more == 0) break;
+      scale_into(w, Vk(k + 1));
+    }
+    k_gm_solve<<<grid_for(N, 64), 64, 0, c->stream>>>(st, N, m);
+    MRHS_LAUNCH_CHECK("gm_solve");
+    multi_axpy(c, Vk(0), fe, kmax, xc, rows, N, dtype, st.y, 1.0);
+  }
+  if (iters) {
+    MRHS_CUDA(cudaMemcpyAsync(iters, st.its, sizeof(int) * N, cudaMemcpyDeviceToHost, c->stream));
+    MRHS_CUDA(cudaStreamSynchronize(c->stream));
+  }
+}
+
+}  // namespace mrhs
+
+using namespace mrhs;
+
+extern "C" {
+
+int mrhs_build_Dc(mrhs_ctx c) {
+  return guarded(c, [&] {
+    MRHS_REQUIRE(c, MRHS_ERR_ARG, "null context");
+    build_Dc(c);
+  });
+}
+
+int mrhs_restrict(mrhs_ctx c, const void* v, void* vc, int nrhs, int dtype) {
+  return guarded(c, [&] {
+    MRHS_REQUIRE(c && v && vc, MRHS_ERR_ARG, "null argument");
+    restrict_(c, v, vc, nrhs, dtype);
+  });
+}
+
+int mrhs_prolong(mrhs_ctx c, const void* uc, void* u, int nrhs, int dtype) {
+  return guarded(c, [&] {
+    MRHS_REQUIRE(c && uc && u, MRHS_ERR_ARG, "null argument");
+    prolong(c, uc, u, nrhs, dtype);
+  });
+}
+
+int mrhs_apply_Dc(mrhs_ctx c, const void* xc, void* yc, int nrhs, int dtype) {
+  return guarded(c, [&] {
+    MRHS_REQUIRE(c && xc && yc, MRHS_ERR_ARG, "null argument");
+    MRHS_REQUIRE(nrhs >= 1, MRHS_ERR_ARG, "nrhs must be >= 1");
+    apply_Dc(c, xc, yc, nrhs, dtype);
+  });
+}
+
+int mrhs_coarse_solve(mrhs_ctx c, const void* bc, void* xc, int nrhs, int dtype, double tol, int restart, int maxit,
+                      int* iters) {
+  return guarded(c, [&] {
+    MRHS_REQUIRE(c && bc && xc, MRHS_ERR_ARG, "null argument");
+    coarse_solve(c, bc, xc, nrhs, dtype, tol, restart, maxit, iters);
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,283 @@
+// Shared definitions of the CUDA library: context, types, complex helpers,
+// error handling and the internal launch interfaces between translation units.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/mrhs.h"
+
+namespace mrhs {
+
+// ------------------------------------------------------------- errors -----
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define MRHS_CUDA(call)                                                                              \
+  do {                                                                                               \
+    cudaError_t e_ = (call);                                                                         \
+    if (e_ != cudaSuccess)                                                                           \
+      throw ::mrhs::Error(e_ == cudaErrorMemoryAllocation ? MRHS_ERR_OOM : MRHS_ERR_CUDA,           \
+                          std::string(#call) + ": " + cudaGetErrorString(e_));                       \
+  } while (0)
+
+#define MRHS_LAUNCH_CHECK(name)                                                                      \
+  do {                                                                                               \
+    cudaError_t e_ = cudaGetLastError();                                                             \
+    if (e_ != cudaSuccess) throw ::mrhs::Error(MRHS_ERR_CUDA, std::string(name) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define MRHS_REQUIRE(cond, code, msg)                                                                \
+  do {                                                                                               \
+    if (!(cond)) throw ::mrhs::Error(code, msg);                                                     \
+  } while (0)
+
+// ------------------------------------------------------------ complex -----
+template <class R>
+struct cx {
+  R re, im;
+};
+
+template <class R>
+__host__ __device__ __forceinline__ cx<R> mk(R a, R b) {
+  cx<R> r;
+  r.re = a;
+  r.im = b;
+  return r;
+}
+template <class R>
+__host__ __device__ __forceinline__ cx<R> operator+(cx<R> a, cx<R> b) { return mk(a.re + b.re, a.im + b.im); }
+template <class R>
+__host__ __device__ __forceinline__ cx<R> operator-(cx<R> a, cx<R> b) { return mk(a.re - b.re, a.im - b.im); }
+template <class R>
+__host__ __device__ __forceinline__ cx<R> operator*(cx<R> a, cx<R> b) {
+  return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <class R>
+__host__ __device__ __forceinline__ cx<R> scale(cx<R> a, R s) { return mk(a.re * s, a.im * s); }
+template <class R>
+__host__ __device__ __forceinline__ cx<R> cnj(cx<R> a) { return mk(a.re, -a.im); }
+// i*a and -i*a
+template <class R>
+__host__ __device__ __forceinline__ cx<R> ti(cx<R> a) { return mk(-a.im, a.re); }
+template <class R>
+__host__ __device__ __forceinline__ cx<R> tmi(cx<R> a) { return mk(a.im, -a.re); }
+// acc += a*b ; acc += conj(a)*b
+template <class R>
+__host__ __device__ __forceinline__ void fma_(cx<R>& acc, cx<R> a, cx<R> b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(a.im, b.re, acc.im);
+}
+template <class R>
+__host__ __device__ __forceinline__ void fmac_(cx<R>& acc, cx<R> a, cx<R> b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(-a.im, b.re, acc.im);
+}
+
+// ------------------------------------------------------ storage types -----
+template <class S>
+struct Real {
+  using type = float;
+};
+template <>
+struct Real<double> {
+  using type = double;
+};
+
+__device__ __forceinline__ double to_r(double v) { return v; }
+__device__ __forceinline__ float to_r(float v) { return v; }
+__device__ __forceinline__ float to_r(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_r(__half v) { return __half2float(v); }
+
+template <class S>
+__device__ __forceinline__ S from_r(double v);
+template <>
+__device__ __forceinline__ double from_r<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ float from_r<float>(double v) { return (float)v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_r<__nv_bfloat16>(double v) { return __float2bfloat16((float)v); }
+template <>
+__device__ __forceinline__ __half from_r<__half>(double v) { return __float2half((float)v); }
+
+inline size_t dtype_size(int dt) {
+  switch (dt) {
+    case MRHS_F64: return 8;
+    case MRHS_F32: return 4;
+    case MRHS_BF16:
+    case MRHS_F16: return 2;
+  }
+  throw Error(MRHS_ERR_ARG, "unknown dtype " + std::to_string(dt));
+}
+
+#define MRHS_DISPATCH(dt, S, ...)                                                                    \
+  switch (dt) {                                                                                      \
+    case MRHS_F64: { using S = double; __VA_ARGS__; } break;                                        \
+    case MRHS_F32: { using S = float; __VA_ARGS__; } break;                                         \
+    case MRHS_BF16: { using S = __nv_bfloat16; __VA_ARGS__; } break;                                \
+    case MRHS_F16: { using S = __half; __VA_ARGS__; } break;                                        \
+    default: throw ::mrhs::Error(MRHS_ERR_ARG, "unknown dtype " + std::to_string(dt));              \
+  }
+
+// interleaved field element index
+__host__ __device__ __forceinline__ size_t fidx(size_t row, int reim, int N, int r) {
+  return (row * 2 + reim) * (size_t)N + r;
+}
+
+// ------------------------------------------------------------ context -----
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct Geometry {
+  int L[4], a[4], nb[4];
+  int V, Va, nagg;
+};
+
+}  // namespace mrhs
+
+struct mrhs_ctx_s {
+  mrhs::Geometry g;
+  int ntv = 0, prec = 0;
+  int tv_dtype = 0;     // storage of test vectors and P
+  int work_dtype = 0;   // storage/compute of smoother work fields, D_c, coarse fields (F64 or F32)
+  cudaStream_t stream = nullptr;
+  int device = 0, num_sms = 0;
+  std::string err;
+  size_t held_bytes = 0;
+  std::vector<void*> allocs;
+
+  // tables (device)
+  int* nbr = nullptr;        // [V][8] device-order neighbours, bit 30 = t-boundary sign
+  int* perm = nullptr;       // canonical site -> device site
+  int* iperm = nullptr;      // device site -> canonical site
+  int* aggnbr = nullptr;     // [nagg][8]
+  int* blocks_col = nullptr; // [2][nagg/2] aggregate ids of colour 0, then colour 1
+  int ncol[2] = {0, 0};
+
+  // gauge field and clover, device order
+  double* U64 = nullptr;  // [V][4][9] complex
+  float* U32 = nullptr;
+  double* A64 = nullptr;  // [V][2][36]
+  float* A32 = nullptr;
+  bool have_gauge = false, have_clover = false;
+
+  // setup state
+  void* tv = nullptr;   // [V][12][2][ntv] in tv_dtype
+  void* P = nullptr;    // same
+  void* Dc = nullptr;   // [nagg][9][2ntv][2ntv] complex in work dtype
+  bool have_tv = false, have_P = false, have_Dc = false;
+
+  int* dflag = nullptr;      // device error flag
+  int* hflag = nullptr;      // pinned host mirror
+  double* hbuf = nullptr;    // pinned host scratch
+  size_t hbuf_bytes = 0;
+
+  // named scratch buffers, grown on demand
+  mrhs::DevBuf scratch[16];
+
+  // per-kernel CUDA-event timing (off unless enabled through mrhs_profile)
+  bool prof = false;
+  std::vector<std::string> prof_names;        // kernel class names
+  std::vector<long long> prof_launches;       // per name
+  std::vector<double> prof_ms;                // per name, folded totals
+  std::vector<cudaEvent_t> prof_events;       // pool, used in (start, stop) pairs
+  std::vector<int> prof_rec_name;             // name of every recorded pair
+  size_t prof_used = 0;                       // events of the pool in use
+};
+
+namespace mrhs {
+
+enum Scratch {
+  SC_STAGE = 0,   // host<->device staging
+  SC_X,           // smoother iterate / work field
+  SC_R,           // residual / rho
+  SC_Q,           // q = D_B rho
+  SC_ALPHA,       // per block per rhs MR coefficients
+  SC_RED,         // reduction partials
+  SC_GS,          // Gram-Schmidt workspace
+  SC_KRYLOV,      // coarse Krylov basis
+  SC_COARSE,      // coarse vectors for the refinement
+  SC_HESS,        // Hessenberg and rotation data
+  SC_FINE1,       // FGMRES work
+  SC_FINE2,
+  SC_FINE3,
+  SC_KRYLOV_F,    // FGMRES basis
+  SC_MISC,
+  SC_COUNT
+};
+
+void* scratch(mrhs_ctx c, int which, size_t bytes);
+void* dalloc(mrhs_ctx c, size_t bytes);
+double* host_scratch(mrhs_ctx c, size_t bytes);
+
+inline size_t fine_elems(const mrhs_ctx c, int nrhs) { return (size_t)c->g.V * 24 * nrhs; }
+inline size_t coarse_elems(const mrhs_ctx c, int nrhs) { return (size_t)c->g.nagg * 2 * c->ntv * 2 * nrhs; }
+inline int compute_dtype(int dtype) { return dtype == MRHS_F64 ? MRHS_F64 : MRHS_F32; }
+
+inline int grid_for(size_t work, int block) { return (int)((work + block - 1) / block); }
+
+// --------------------------------------------------- internal interfaces --
+// dslash.cu
+enum DslashMode { DS_FULL = 0, DS_BLOCK = 1, DS_RESID = 2 };
+void dslash(mrhs_ctx c, const void* x, void* y, const void* b, int nrhs, int dtype, int mode, int colour);
+void sap(mrhs_ctx c, const void* b, void* x, int nrhs, int dtype, int n_sweeps, int n_mr);
+// gs.cu
+void build_P(mrhs_ctx c);
+// coarse.cu
+void build_Dc(mrhs_ctx c);
+void restrict_(mrhs_ctx c, const void* v, void* vc, int nrhs, int dtype);
+void prolong(mrhs_ctx c, const void* uc, void* u, int nrhs, int dtype);
+void apply_Dc(mrhs_ctx c, const void* xc, void* yc, int nrhs, int dtype);
+void coarse_solve(mrhs_ctx c, const void* bc, void* xc, int nrhs, int dtype, double tol, int restart, int maxit,
+                  int* iters);
+// blas.cu: per right-hand-side reductions and updates on interleaved arrays of
+// `rows` complex rows, each [2][N]
+void multi_dot(mrhs_ctx c, const void* X, size_t stride, int K, const void* Y, size_t rows, int N, int dtype,
+               double* out /* device [K][N][2] */);
+void norms(mrhs_ctx c, const void* X, size_t rows, int N, int dtype, double* out /* device [N] (squared) */);
+void convert(mrhs_ctx c, const void* x, int dx, void* y, int dy, size_t n);
+void sap_mixed(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int dtype, int n_sweeps, int n_mr);
+// blas.cu: y[row][r] += sign * sum_k coef[k][r] * X_k[row][r], X_k = X + k*stride elements
+void multi_axpy(mrhs_ctx c, const void* X, size_t stride, int K, void* Y, size_t rows, int N, int dtype,
+                const double* coef /* device [K][N][2] */, double sign);
+void normalise_rhs(mrhs_ctx c, void* X, size_t rows, int N, int dtype);
+
+// RAII timer of one launch (or a group of launches) on the context stream
+struct Prof {
+  mrhs_ctx c;
+  size_t idx = (size_t)-1;
+  Prof(mrhs_ctx ctx, const char* name);
+  ~Prof();
+};
+
+// every extern "C" entry point runs its body through this guard
+std::string& create_error_slot();
+template <class F>
+int guarded(mrhs_ctx c, F&& f) {
+  try {
+    f();
+    return MRHS_OK;
+  } catch (const Error& e) {
+    (c ? c->err : create_error_slot()) = e.what();
+    return e.code;
+  } catch (const std::exception& e) {
+    (c ? c->err : create_error_slot()) = e.what();
+    return MRHS_ERR_ARG;
+  }
+}
+
+}  // namespace mrhs
