@@ -145,14 +145,16 @@ __global__ void k_tables_canon(GeomArgs g, const int* nbr, const int* perm, cons
   aggof_c[2 * s + 1] = sd % g.Va;
 }
 
-// gauge field: canonical [V][4][9] complex128 (staging) -> device order, f64 + f32
-__global__ void k_gauge_in(int V, const int* iperm, const double* Uc, double* U64, float* U32) {
+// gauge field: canonical sites s0.. of [V][4][9] complex128 (staging) ->
+// device order, f64 + f32 copies
+__global__ void k_gauge_in(int s0, int ns, const int* perm, const double* Uc, double* U64, float* U32) {
   size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (t >= (size_t)V * 72) return;
-  size_t sd = t / 72, e = t % 72;
-  double v = Uc[(size_t)iperm[sd] * 72 + e];
-  U64[t] = v;
-  U32[t] = (float)v;
+  if (t >= (size_t)ns * 72) return;
+  size_t s = t / 72, e = t % 72;
+  size_t o = (size_t)perm[s0 + s] * 72 + e;
+  double v = Uc[t];
+  U64[o] = v;
+  U32[o] = (float)v;
 }
 
 // ------------------------------------------------------------ clover ------
@@ -585,11 +587,16 @@ int mrhs_set_gauge(mrhs_ctx c, const double* U) {
       c->U64 = (double*)dalloc(c, n * sizeof(double));
       c->U32 = (float*)dalloc(c, n * sizeof(float));
     }
-    // chunk through staging to bound the extra device memory
-    double* st = (double*)scratch(c, SC_STAGE, n * sizeof(double));
-    MRHS_CUDA(cudaMemcpyAsync(st, U, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    k_gauge_in<<<grid_for(n, 256), 256, 0, c->stream>>>(c->g.V, c->iperm, st, c->U64, c->U32);
-    MRHS_LAUNCH_CHECK("gauge_in");
+    // chunks of sites through the staging buffer bound the extra device memory
+    const size_t per_site = 72 * sizeof(double);
+    const size_t chunk = std::max<size_t>(1, std::min<size_t>(c->g.V, (size_t(1) << 30) / per_site));
+    double* st = (double*)scratch(c, SC_STAGE, chunk * per_site);
+    for (size_t s0 = 0; s0 < (size_t)c->g.V; s0 += chunk) {
+      int ns = (int)std::min(chunk, (size_t)c->g.V - s0);
+      MRHS_CUDA(cudaMemcpyAsync(st, U + s0 * 72, ns * per_site, cudaMemcpyHostToDevice, c->stream));
+      k_gauge_in<<<grid_for((size_t)ns * 72, 256), 256, 0, c->stream>>>((int)s0, ns, c->perm, st, c->U64, c->U32);
+      MRHS_LAUNCH_CHECK("gauge_in");
+    }
     MRHS_CUDA(cudaStreamSynchronize(c->stream));
     c->have_gauge = true;
     c->have_clover = false;

@@ -78,15 +78,35 @@ def _exp_i_eps_h(h: np.ndarray, eps: float) -> np.ndarray:
     return _project_su3(U)
 
 
-def gauge_field(dims, eps: float, seed: int, chunk_sites: int = 1 << 18) -> np.ndarray:
-    """Seeded SU(3) gauge field, complex128 [V, 4, 3, 3]."""
+def _exp_i_eps_h_torch(h: np.ndarray, eps: float, device) -> np.ndarray:
+    """The same map as _exp_i_eps_h, evaluated with torch on `device` (used to
+    generate large fields quickly; equal to the numpy path up to rounding)."""
+    import torch
+
+    lam = torch.as_tensor(gell_mann() / 2, device=device)
+    ht = torch.as_tensor(h, device=device).to(torch.complex128)
+    H = torch.einsum("...a,aij->...ij", ht, lam)
+    U = torch.linalg.matrix_exp(1j * eps * H)
+    r0 = U[..., 0, :]
+    r0 = r0 / torch.linalg.vector_norm(r0, dim=-1, keepdim=True)
+    r1 = U[..., 1, :]
+    r1 = r1 - torch.sum(r0.conj() * r1, dim=-1, keepdim=True) * r0
+    r1 = r1 / torch.linalg.vector_norm(r1, dim=-1, keepdim=True)
+    r2 = torch.linalg.cross(r0, r1).conj()
+    return torch.stack([r0, r1, r2], dim=-2).cpu().numpy()
+
+
+def gauge_field(dims, eps: float, seed: int, chunk_sites: int = 1 << 18, device=None) -> np.ndarray:
+    """Seeded SU(3) gauge field, complex128 [V, 4, 3, 3]. With device (e.g.
+    "cuda") the exponential is evaluated there with torch; the random draws
+    are the same."""
     V = volume(dims)
     rng = np.random.Generator(np.random.PCG64(seed))
     U = np.empty((V, 4, 3, 3), dtype=np.complex128)
     for s0 in range(0, V, chunk_sites):
         s1 = min(V, s0 + chunk_sites)
         h = rng.standard_normal((s1 - s0, 4, 8))
-        U[s0:s1] = _exp_i_eps_h(h, eps)
+        U[s0:s1] = _exp_i_eps_h(h, eps) if device is None else _exp_i_eps_h_torch(h, eps, device)
     return U
 
 
