@@ -251,10 +251,20 @@ void multi_dot(mrhs_ctx c, const void* X, size_t stride, int K, const void* Y, s
 void norms(mrhs_ctx c, const void* X, size_t rows, int N, int dtype, double* out /* device [N] (squared) */);
 void convert(mrhs_ctx c, const void* x, int dx, void* y, int dy, size_t n);
 void sap_mixed(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int dtype, int n_sweeps, int n_mr);
+// sap.cu: the on-chip SAP (FP32 work fields)
+bool sap_fused_ok(mrhs_ctx c, int dtype);
+void sap_fused(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int n_sweeps, int n_mr);
 // blas.cu: y[row][r] += sign * sum_k coef[k][r] * X_k[row][r], X_k = X + k*stride elements
 void multi_axpy(mrhs_ctx c, const void* X, size_t stride, int K, void* Y, size_t rows, int N, int dtype,
                 const double* coef /* device [K][N][2] */, double sign);
 void normalise_rhs(mrhs_ctx c, void* X, size_t rows, int N, int dtype);
+size_t multi_dot_partials_bytes(size_t rows, int N, int K);
+void multi_dot_ws(mrhs_ctx c, const void* X, size_t stride, int K, const void* Y, size_t rows, int N, int dtype,
+                  double* out, double* part);
+// coarse.cu: the coarse solve on a caller-supplied workspace (no allocation)
+size_t coarse_solve_ws_bytes(mrhs_ctx c, int nrhs, int dtype, int restart);
+void coarse_solve_ws(mrhs_ctx c, const void* bc, void* xc, int nrhs, int dtype, double tol, int restart, int maxit,
+                     int* iters, void* ws, size_t ws_bytes);
 
 // RAII timer of one launch (or a group of launches) on the context stream
 struct Prof {

@@ -186,6 +186,10 @@ static void resid_mixed(mrhs_ctx c, const void* x, void* y, const void* b, int b
 void sap_mixed(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int dtype, int n_sweeps, int n_mr) {
   MRHS_REQUIRE(c->have_clover, MRHS_ERR_STATE, "smoother used before mrhs_build_clover");
   MRHS_REQUIRE(n_sweeps >= 0 && n_mr >= 0 && nrhs >= 1, MRHS_ERR_ARG, "bad smoother parameters");
+  if (sap_fused_ok(c, dtype)) {
+    sap_fused(c, b, bdtype, x, nrhs, n_sweeps, n_mr);
+    return;
+  }
   size_t bytes = fine_elems(c, nrhs) * dtype_size(dtype);
   void* r = scratch(c, SC_R, bytes);
   void* q = scratch(c, SC_Q, bytes);

@@ -46,7 +46,7 @@ __device__ __forceinline__ void bdag(const cx<R>& c0, const cx<R>& c1, cx<R>& o0
 // neighbour spinor psi with link Ul (U_mu(x) forward, U_mu(x-mu) backward,
 // applied as dagger), sign sg (-1 across the t boundary)
 template <int MU, int DIR, class R>
-__device__ __forceinline__ void hop_reg(cx<R> out[12], const cx<R> psi[12], const cx<R>* Ul, R sg) {
+__device__ __forceinline__ void hop_reg_u(cx<R> out[12], const cx<R> psi[12], const cx<R> u[3][3], R sg) {
   cx<R> h[2][3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -59,11 +59,6 @@ __device__ __forceinline__ void hop_reg(cx<R> out[12], const cx<R> psi[12], cons
     if (DIR > 0) { h[0][c] = p0 - b0; h[1][c] = p1 - b1; }
     else { h[0][c] = p0 + b0; h[1][c] = p1 + b1; }
   }
-  cx<R> u[3][3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) u[a][b] = Ul[a * 3 + b];
   cx<R> ch[2][3];
 #pragma unroll
   for (int s = 0; s < 2; ++s)
@@ -86,6 +81,16 @@ __device__ __forceinline__ void hop_reg(cx<R> out[12], const cx<R> psi[12], cons
     if (DIR > 0) { out[6 + a] = out[6 + a] + l0; out[9 + a] = out[9 + a] + l1; }
     else { out[6 + a] = out[6 + a] - l0; out[9 + a] = out[9 + a] - l1; }
   }
+}
+
+template <int MU, int DIR, class R>
+__device__ __forceinline__ void hop_reg(cx<R> out[12], const cx<R> psi[12], const cx<R>* Ul, R sg) {
+  cx<R> u[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) u[a][b] = Ul[a * 3 + b];
+  hop_reg_u<MU, DIR, R>(out, psi, u, sg);
 }
 
 // the same, loading the neighbour spinor at row base nrow (= n*12)
