@@ -193,6 +193,27 @@ int mrhs_apply_Dc(mrhs_ctx ctx, const void* xc, void* yc, int nrhs, int dtype);
 int mrhs_coarse_solve(mrhs_ctx ctx, const void* bc, void* xc, int nrhs, int dtype, double tol, int restart,
                       int maxit, int* iters);
 
+/* The same coarse solve without any allocation. The paper has no counterpart:
+ * this entry point is for callers that cannot let the library call
+ * cudaMalloc (device memory handed out entirely by the caller's own pool or
+ * caching allocator, no device-wide synchronisation wanted in the middle of
+ * a solve, or no allocation allowed after start-up). The Krylov basis, the
+ * GMRES state and the reduction partials live in one fixed 64 MiB device
+ * array inside the library (held by every GPU that loads the library until
+ * the process exits); results equal those of mrhs_coarse_solve.
+ * - MRHS_ERR_SHAPE (with the needed size in mrhs_last_error) when the
+ *   problem needs more than 64 MiB: (restart + 2) coarse fields of nrhs
+ *   right-hand sides plus the GMRES state and partials.
+ * - The context's device must be the current device (MRHS_ERR_ARG if not).
+ * - The first call on a device looks up the array's device address (this may
+ *   load the library's device code on that device); make that first call
+ *   before any stream capture.
+ * - Every call uses the same array and leaves its contents behind; each
+ *   call initialises everything it reads. Calls that overlap on the GPU
+ *   (different streams or contexts at the same time) race on the array. */
+int mrhs_coarse_solve_noalloc(mrhs_ctx ctx, const void* bc, void* xc, int nrhs, int dtype, double tol, int restart,
+                              int maxit, int* iters);
+
 /* ------------------------------------------------------------------ setup */
 
 /* Initial phase (Sec. 2): the SAP smoother on every test vector from x0 = 0

@@ -56,6 +56,7 @@ _SIGS = {
     "mrhs_prolong": (_I, [_VP, _VP, _VP, _I, _I]),
     "mrhs_apply_Dc": (_I, [_VP, _VP, _VP, _I, _I]),
     "mrhs_coarse_solve": (_I, [_VP, _VP, _VP, _I, _I, _D, _I, _I, _VP]),
+    "mrhs_coarse_solve_noalloc": (_I, [_VP, _VP, _VP, _I, _I, _D, _I, _I, _VP]),
     "mrhs_setup_init": (_I, [_VP, _VP, _I, _I, _I, _I]),
     "mrhs_setup_refine": (_I, [_VP, _I, _I, _I, _D, _I, _I, _VP]),
     "mrhs_get_tv": (_I, [_VP, _VP, _I]),
@@ -223,6 +224,14 @@ def mrhs_coarse_solve(ctx, bc, xc, nrhs, dtype, tol, restart, maxit):
     its = np.zeros(int(nrhs), np.int32)
     _check(ctx, lib().mrhs_coarse_solve(ctx, _ptr(bc), _ptr(xc), int(nrhs), int(dtype), float(tol), int(restart),
                                         int(maxit), _ptr(its)))
+    return its
+
+
+def mrhs_coarse_solve_noalloc(ctx, bc, xc, nrhs, dtype, tol, restart, maxit):
+    """mrhs_coarse_solve without allocation (fixed 64 MiB device workspace)."""
+    its = np.zeros(int(nrhs), np.int32)
+    _check(ctx, lib().mrhs_coarse_solve_noalloc(ctx, _ptr(bc), _ptr(xc), int(nrhs), int(dtype), float(tol),
+                                                int(restart), int(maxit), _ptr(its)))
     return its
 
 

@@ -125,6 +125,24 @@ void multi_dot(mrhs_ctx c, const void* X, size_t stride, int K, const void* Y, s
   MRHS_LAUNCH_CHECK("sum_chunks");
 }
 
+// multi_dot with the per-CTA partials in a caller-supplied buffer of at
+// least multi_dot_partials_bytes(rows, N, K) bytes (no allocation)
+size_t multi_dot_partials_bytes(size_t rows, int N, int K) {
+  return sizeof(double) * 2 * (size_t)K * n_chunks(rows, N) * N;
+}
+
+void multi_dot_ws(mrhs_ctx c, const void* X, size_t stride, int K, const void* Y, size_t rows, int N, int dtype,
+                  double* out, double* part) {
+  MRHS_REQUIRE(N >= 1 && N <= kBlock && K >= 1, MRHS_ERR_ARG, "multi_dot: bad sizes");
+  int nch = n_chunks(rows, N);
+  dim3 grid(nch, K);
+  Prof pr(c, "multi_dot");
+  MRHS_DISPATCH(dtype, S, (k_multi_dot<S><<<grid, kBlock, 0, c->stream>>>((const S*)X, stride, (const S*)Y, rows, N, nch, part)));
+  MRHS_LAUNCH_CHECK("multi_dot");
+  k_sum_chunks<<<grid_for((size_t)K * N, 128), 128, 0, c->stream>>>(part, K, nch, N, out);
+  MRHS_LAUNCH_CHECK("sum_chunks");
+}
+
 // out[r] (as [N][2], imaginary part 0) = |X_r|^2
 void norms(mrhs_ctx c, const void* X, size_t rows, int N, int dtype, double* out) {
   multi_dot(c, X, 0, 1, X, rows, N, dtype, out);

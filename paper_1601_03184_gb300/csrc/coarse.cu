@@ -530,6 +530,121 @@ void coarse_solve(mrhs_ctx c, const void* bc, void* xc, int N, int dtype, double
   }
 }
 
+// ------------------------------------------------------------------------
+// The same coarse GMRES on one caller-supplied workspace: basis, GMRES state
+// and reduction partials are carved from ws; nothing is allocated.
+namespace {
+struct WsLayout {
+  size_t basis, state, part, total;
+};
+WsLayout ws_layout(mrhs_ctx c, int N, int dtype, int m) {
+  const size_t rows = (size_t)c->g.nagg * 2 * c->ntv;
+  const size_t fe = rows * 2 * N;
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  WsLayout L;
+  L.basis = up((size_t)(m + 2) * fe * dtype_size(dtype));
+  size_t st = 0;
+  st += up(sizeof(cx<double>) * (size_t)N * (m + 1) * m);      // H
+  st += 2 * up(sizeof(cx<double>) * (size_t)N * m);            // cs, sn
+  st += up(sizeof(cx<double>) * (size_t)N * (m + 1));          // g
+  st += up(sizeof(double) * (size_t)m * N * 2);                 // y
+  st += 2 * up(sizeof(double) * (size_t)(m + 1) * N * 2);      // h1, h2
+  st += 3 * up(sizeof(double) * (size_t)N * 2);                // hn2, beta2, bnorm2
+  st += up(sizeof(double) * (size_t)N);                        // inv
+  st += 4 * up(sizeof(int) * (size_t)N) + up(sizeof(int));     // conv, active, its, kend, counter
+  L.state = st;
+  L.part = up(multi_dot_partials_bytes(rows, N, m + 1));
+  L.total = L.basis + L.state + L.part;
+  return L;
+}
+}  // namespace
+
+size_t coarse_solve_ws_bytes(mrhs_ctx c, int nrhs, int dtype, int restart) {
+  return ws_layout(c, nrhs, dtype, restart).total;
+}
+
+void coarse_solve_ws(mrhs_ctx c, const void* bc, void* xc, int N, int dtype, double tol, int m, int maxit, int* iters,
+                     void* ws, size_t ws_bytes) {
+  MRHS_REQUIRE(c->have_Dc, MRHS_ERR_STATE, "coarse solve before mrhs_build_Dc");
+  MRHS_REQUIRE(dtype == c->work_dtype, MRHS_ERR_ARG, "coarse solve: dtype must be the context's work type");
+  MRHS_REQUIRE(N >= 1 && N <= 256 && m >= 1 && m <= 64 && maxit >= 0 && tol >= 0, MRHS_ERR_ARG,
+               "coarse solve: need 1 <= nrhs <= 256, 1 <= restart <= 64, maxit >= 0, tol >= 0");
+  const WsLayout L = ws_layout(c, N, dtype, m);
+  MRHS_REQUIRE(L.total <= ws_bytes, MRHS_ERR_SHAPE, "coarse solve workspace too small");
+  const size_t rows = (size_t)c->g.nagg * 2 * c->ntv;
+  const size_t fe = rows * 2 * N;
+  const size_t es = dtype_size(dtype);
+  char* basis = (char*)ws;
+  char* w = basis + (size_t)(m + 1) * fe * es;
+  auto Vk = [&](int k) { return (void*)(basis + (size_t)k * fe * es); };
+  char* sp = basis + L.basis;
+  GmState st;
+  st.H = carve<cx<double>>(sp, (size_t)N * (m + 1) * m);
+  st.cs = carve<cx<double>>(sp, (size_t)N * m);
+  st.sn = carve<cx<double>>(sp, (size_t)N * m);
+  st.g = carve<cx<double>>(sp, (size_t)N * (m + 1));
+  st.y = carve<double>(sp, (size_t)m * N * 2);
+  st.h1 = carve<double>(sp, (size_t)(m + 1) * N * 2);
+  st.h2 = carve<double>(sp, (size_t)(m + 1) * N * 2);
+  st.hn2 = carve<double>(sp, (size_t)N * 2);
+  st.beta2 = carve<double>(sp, (size_t)N * 2);
+  st.bnorm2 = carve<double>(sp, (size_t)N * 2);
+  st.inv = carve<double>(sp, (size_t)N);
+  st.conv = carve<int>(sp, N);
+  st.active = carve<int>(sp, N);
+  st.its = carve<int>(sp, N);
+  st.kend = carve<int>(sp, N);
+  st.counter = carve<int>(sp, 1);
+  double* part = (double*)(basis + L.basis + L.state);
+  int* hcount = c->hflag + 1;
+  auto read_counter = [&]() {
+    MRHS_CUDA(cudaMemcpyAsync(hcount, st.counter, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    MRHS_CUDA(cudaStreamSynchronize(c->stream));
+    return *hcount;
+  };
+  auto scale_into = [&](const void* x, void* y) {
+    MRHS_DISPATCH(dtype, S, (k_scale_rhs<S><<<grid_for(rows * N, 256), 256, 0, c->stream>>>((const S*)x, (S*)y, rows, N, st.inv)));
+    MRHS_LAUNCH_CHECK("scale_rhs");
+  };
+  MRHS_CUDA(cudaMemsetAsync(xc, 0, fe * es, c->stream));
+  multi_dot_ws(c, bc, 0, 1, bc, rows, N, dtype, st.bnorm2, part);
+  k_gm_init<<<grid_for(N, 64), 64, 0, c->stream>>>(st, N);
+  MRHS_LAUNCH_CHECK("gm_init");
+  for (;;) {
+    apply_Dc(c, xc, w, N, dtype);
+    MRHS_DISPATCH(dtype, S, (k_sub_from<S><<<grid_for(fe, 256), 256, 0, c->stream>>>((const S*)bc, (S*)w, fe)));
+    MRHS_LAUNCH_CHECK("sub_from");
+    multi_dot_ws(c, w, 0, 1, w, rows, N, dtype, st.beta2, part);
+    MRHS_CUDA(cudaMemsetAsync(st.counter, 0, sizeof(int), c->stream));
+    k_gm_start<<<grid_for(N, 64), 64, 0, c->stream>>>(st, N, m, tol, maxit);
+    MRHS_LAUNCH_CHECK("gm_start");
+    if (read_counter() == 0) break;
+    scale_into(w, Vk(0));
+    int kmax = 0;
+    for (int k = 0; k < m; ++k) {
+      apply_Dc(c, Vk(k), w, N, dtype);
+      multi_dot_ws(c, Vk(0), fe, k + 1, w, rows, N, dtype, st.h1, part);
+      multi_axpy(c, Vk(0), fe, k + 1, w, rows, N, dtype, st.h1, -1.0);
+      multi_dot_ws(c, Vk(0), fe, k + 1, w, rows, N, dtype, st.h2, part);
+      multi_axpy(c, Vk(0), fe, k + 1, w, rows, N, dtype, st.h2, -1.0);
+      multi_dot_ws(c, w, 0, 1, w, rows, N, dtype, st.hn2, part);
+      MRHS_CUDA(cudaMemsetAsync(st.counter, 0, sizeof(int), c->stream));
+      k_gm_step<<<grid_for(N, 64), 64, 0, c->stream>>>(st, N, m, k, tol, maxit);
+      MRHS_LAUNCH_CHECK("gm_step");
+      kmax = k + 1;
+      if (read_counter() == 0) break;
+      scale_into(w, Vk(k + 1));
+    }
+    k_gm_solve<<<grid_for(N, 64), 64, 0, c->stream>>>(st, N, m);
+    MRHS_LAUNCH_CHECK("gm_solve");
+    multi_axpy(c, Vk(0), fe, kmax, xc, rows, N, dtype, st.y, 1.0);
+  }
+  if (iters) {
+    MRHS_CUDA(cudaMemcpyAsync(iters, st.its, sizeof(int) * N, cudaMemcpyDeviceToHost, c->stream));
+    MRHS_CUDA(cudaStreamSynchronize(c->stream));
+  }
+}
+
 }  // namespace mrhs
 
 using namespace mrhs;
