@@ -136,6 +136,11 @@ def kernel_work(name, cfg, launches_per_step, bytes_f=4):
         return V * (link4 + clov + 2 * N * spin), V * N * flop_site_rhs
     if name == "dslash_resid":  # one colour: r = b - D x on half of the sites
         return V / 2 * (link4 + clov + 3 * N * spin), V / 2 * N * flop_site_rhs
+    if name in ("sap_fused8", "sap_fused"):  # one colour: residual + n_mr MR steps, on chip
+        nmr = SCHEDULE["smooth_mr"]
+        flops = V / 2 * N * (flop_site_rhs + nmr * (flop_site_rhs + 336))
+        byt = V / 2 * (link4 + clov + 3 * N * spin)  # b in, x in and out, links and clover once
+        return byt, flops
     if name == "sap_block_mr":  # one colour, n_mr MR steps of D_B, two dots and two updates
         nmr = SCHEDULE["smooth_mr"]
         flops = V / 2 * N * nmr * (flop_site_rhs + 4 * 96)

@@ -76,9 +76,14 @@ __global__ void k_sum_chunks(const double* part, int K, int nchunk, int N, doubl
   out[2 * t + 1] = b;
 }
 
-template <class S>
-__global__ void k_multi_axpy(const S* X, size_t stride, int K, S* Y, size_t rows, int N, const double* coef,
-                             double sign) {
+// coefficients sign*coef in the compute precision, once per (k, r)
+__global__ void k_coef_to_float(const double* coef, double sign, float* out, int n) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) out[t] = (float)(sign * coef[t]);
+}
+
+template <class S, class C>
+__global__ void k_multi_axpy(const S* X, size_t stride, int K, S* Y, size_t rows, int N, const C* coef, C sign) {
   using R = typename Real<S>::type;
   size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (t >= rows * N) return;
@@ -96,18 +101,25 @@ __global__ void k_multi_axpy(const S* X, size_t stride, int K, S* Y, size_t rows
   Y[fidx(row, 1, N, r)] = from_r<S>(yi);
 }
 
-// X[., r] *= 1/sqrt(nrm2[r]) (0 stays 0)
+// s[r] = 1/sqrt(nrm2[r]) (0 for a zero vector), once per right-hand side
+__global__ void k_inv_sqrt(const double* nrm2, double* s, int N) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  double n = nrm2[2 * r];
+  s[r] = n > 0 ? 1.0 / sqrt(n) : 0.0;
+}
+
+// X[., r] *= s[r]
 template <class S>
-__global__ void k_inv_sqrt_scale(S* X, size_t rows, int N, const double* nrm2) {
+__global__ void k_scale_by(S* X, size_t rows, int N, const double* s) {
   using R = typename Real<S>::type;
   size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (t >= rows * N) return;
   int r = (int)(t % N);
   size_t row = t / N;
-  double n = nrm2[2 * r];
-  R s = n > 0 ? (R)(1.0 / sqrt(n)) : (R)0;
-  X[fidx(row, 0, N, r)] = from_r<S>(to_r(X[fidx(row, 0, N, r)]) * s);
-  X[fidx(row, 1, N, r)] = from_r<S>(to_r(X[fidx(row, 1, N, r)]) * s);
+  R f = (R)s[r];
+  X[fidx(row, 0, N, r)] = from_r<S>(to_r(X[fidx(row, 0, N, r)]) * f);
+  X[fidx(row, 1, N, r)] = from_r<S>(to_r(X[fidx(row, 1, N, r)]) * f);
 }
 
 }  // namespace
@@ -152,16 +164,26 @@ void multi_axpy(mrhs_ctx c, const void* X, size_t stride, int K, void* Y, size_t
                 const double* coef, double sign) {
   size_t work = rows * N;
   Prof pr(c, "multi_axpy");
-  MRHS_DISPATCH(dtype, S, (k_multi_axpy<S><<<grid_for(work, kBlock), kBlock, 0, c->stream>>>((const S*)X, stride, K, (S*)Y, rows, N, coef, sign)));
+  if (dtype == MRHS_F64) {
+    k_multi_axpy<double, double><<<grid_for(work, kBlock), kBlock, 0, c->stream>>>((const double*)X, stride, K, (double*)Y, rows, N, coef, sign);
+  } else {
+    MRHS_REQUIRE(K <= 65 && N <= 256, MRHS_ERR_ARG, "multi_axpy: K <= 65 and N <= 256");
+    const int n = 2 * K * N;
+    k_coef_to_float<<<grid_for(n, 256), 256, 0, c->stream>>>(coef, sign, c->coef32, n);
+    MRHS_DISPATCH(dtype, S, (k_multi_axpy<S, float><<<grid_for(work, kBlock), kBlock, 0, c->stream>>>((const S*)X, stride, K, (S*)Y, rows, N, (const float*)c->coef32, 1.0f)));
+  }
   MRHS_LAUNCH_CHECK("multi_axpy");
 }
 
 // normalise every right-hand side of X to unit 2-norm
 void normalise_rhs(mrhs_ctx c, void* X, size_t rows, int N, int dtype) {
-  double* nrm = (double*)scratch(c, SC_MISC, sizeof(double) * 2 * N);
+  double* nrm = (double*)scratch(c, SC_MISC, sizeof(double) * 3 * N);
   norms(c, X, rows, N, dtype, nrm);
+  k_inv_sqrt<<<grid_for(N, 64), 64, 0, c->stream>>>(nrm, nrm + 2 * N, N);
+  MRHS_LAUNCH_CHECK("inv_sqrt");
   size_t work = rows * N;
-  MRHS_DISPATCH(dtype, S, (k_inv_sqrt_scale<S><<<grid_for(work, kBlock), kBlock, 0, c->stream>>>((S*)X, rows, N, nrm)));
+  Prof pr(c, "normalise");
+  MRHS_DISPATCH(dtype, S, (k_scale_by<S><<<grid_for(work, kBlock), kBlock, 0, c->stream>>>((S*)X, rows, N, nrm + 2 * N)));
   MRHS_LAUNCH_CHECK("normalise");
 }
 

@@ -127,6 +127,119 @@ __global__ void k_coarse_op(const SP* __restrict__ P, const cx<R>* __restrict__ 
   }
 }
 
+// Tiled form for ntv % 4 == 0 and 2*ntv <= 64. One CTA per (aggregate A,
+// k in 0..4): k = 0 the self block, k = 1+mu the forward block (A+mu). Per
+// chunk of sites Y[q][c][col] = (D_k P_col)(x_q, c) is built in shared memory
+// (one (site, column) per thread), then every thread accumulates a 4x4 tile
+// of P^dag Y (rows (h,i0..i0+3), columns col0..col0+3) over the chunk.
+// The backward blocks follow from gamma_5-hermiticity (k_coarse_backward).
+constexpr int kTileSites = 8;
+
+template <class SP, class R>
+__global__ void __launch_bounds__(256) k_coarse_op_tiled(const SP* __restrict__ P, const cx<R>* __restrict__ U,
+                                                         const R* __restrict__ Acl, const int* __restrict__ nbr, int Nt,
+                                                         Agg4 ag, int Va, cx<R>* __restrict__ Dc) {
+  extern __shared__ double smem_d[];
+  const int A = blockIdx.x / 5, k = blockIdx.x % 5;
+  const int nc = 2 * Nt;
+  cx<R>* Y = (cx<R>*)smem_d;                 // [kTileSites][12][nc]
+  cx<R>* Pc = Y + kTileSites * 12 * nc;      // [kTileSites][12][Nt]
+  const int mu = k - 1;
+  const int nsite = k == 0 ? Va : Va / ag.a[mu];
+  const int lmu = k == 0 ? 0 : ag.a[mu] - 1;
+  const int ntile = nc / 4;
+  const int rt = threadIdx.x / ntile, ct = threadIdx.x % ntile;
+  const bool tile_on = threadIdx.x < ntile * ntile;
+  const int r0 = 4 * rt, c0 = 4 * ct;
+  const int h = r0 / Nt, i0 = r0 % Nt;
+  cx<R> acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = mk<R>(0, 0);
+  for (int q0 = 0; q0 < nsite; q0 += kTileSites) {
+    const int nq = min(kTileSites, nsite - q0);
+    for (int w = threadIdx.x; w < nq * nc; w += blockDim.x) {
+      int q = w / nc, col = w % nc;
+      int l = k == 0 ? q0 + q : face_site(ag, mu, lmu, q0 + q);
+      int s = A * Va + l;
+      cx<R> out[12];
+#pragma unroll
+      for (int c = 0; c < 12; ++c) out[c] = mk<R>(0, 0);
+      if (k == 0) {
+        cx<R> psi[12];
+        load_pcol<SP, R>(psi, P, s, Nt, col);
+        clover_apply_reg<R>(out, psi, Acl + (size_t)s * 72);
+        for (int d = -1; d <= 1; d += 2) {
+          hop_pcol<0, SP, R>(out, P, U, nbr, s, d, Nt, col, true, Va);
+          hop_pcol<1, SP, R>(out, P, U, nbr, s, d, Nt, col, true, Va);
+          hop_pcol<2, SP, R>(out, P, U, nbr, s, d, Nt, col, true, Va);
+          hop_pcol<3, SP, R>(out, P, U, nbr, s, d, Nt, col, true, Va);
+        }
+      } else {
+        switch (mu) {
+          case 0: hop_pcol<0, SP, R>(out, P, U, nbr, s, +1, Nt, col, false, Va); break;
+          case 1: hop_pcol<1, SP, R>(out, P, U, nbr, s, +1, Nt, col, false, Va); break;
+          case 2: hop_pcol<2, SP, R>(out, P, U, nbr, s, +1, Nt, col, false, Va); break;
+          default: hop_pcol<3, SP, R>(out, P, U, nbr, s, +1, Nt, col, false, Va); break;
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 12; ++c) Y[(q * 12 + c) * nc + col] = out[c];
+    }
+    for (int w = threadIdx.x; w < nq * 12 * Nt; w += blockDim.x) {
+      int q = w / (12 * Nt), c = (w / Nt) % 12, i = w % Nt;
+      int l = k == 0 ? q0 + q : face_site(ag, mu, lmu, q0 + q);
+      Pc[w] = ld<SP, R>(P, ((size_t)A * Va + l) * 12 + c, Nt, i);
+    }
+    __syncthreads();
+    if (tile_on) {
+      for (int q = 0; q < nq; ++q)
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) {
+          const int c = 6 * h + cc;
+          cx<R> pv[4], yv[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) pv[a] = Pc[(q * 12 + c) * Nt + i0 + a];
+#pragma unroll
+          for (int b = 0; b < 4; ++b) yv[b] = Y[(q * 12 + c) * nc + c0 + b];
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) fmac_(acc[a][b], pv[a], yv[b]);
+        }
+    }
+    __syncthreads();
+  }
+  if (tile_on) {
+    const int kk = k;  // self and forward blocks keep their stencil index
+    cx<R>* out = Dc + ((size_t)A * 9 + kk) * nc * nc;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) out[(size_t)(r0 + a) * nc + c0 + b] = acc[a][b];
+  }
+}
+
+// D_c[A][5+mu][r][c] = eta(r) eta(c) conj(D_c[A-mu][1+mu][c][r]), eta = +1 for
+// chirality 0 rows/columns and -1 for chirality 1 (gamma_5-hermiticity of D
+// and the chirality-split P).
+template <class R>
+__global__ void k_coarse_backward(cx<R>* Dc, const int* __restrict__ aggnbr, int nagg, int Nt) {
+  const int nc = 2 * Nt;
+  size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  size_t tot = (size_t)nagg * 4 * nc * nc;
+  if (t >= tot) return;
+  int c = (int)(t % nc);
+  int r = (int)((t / nc) % nc);
+  int mu = (int)((t / ((size_t)nc * nc)) % 4);
+  int A = (int)(t / ((size_t)4 * nc * nc));
+  int B = aggnbr[A * 8 + 4 + mu];
+  cx<R> v = Dc[(((size_t)B * 9 + 1 + mu) * nc + c) * nc + r];
+  R sgn = ((r / Nt) == (c / Nt)) ? (R)1 : (R)-1;
+  Dc[(((size_t)A * 9 + 5 + mu) * nc + r) * nc + c] = mk<R>(sgn * v.re, -sgn * v.im);
+}
+
 // vc[A][(h,i)][r] = sum_{x in A, c in h} conj(P_i(x,c)) v(x,c,r)
 template <class SP, class SV, class SC, int EPT>
 __global__ void k_restrict(const SP* __restrict__ P, const SV* __restrict__ v, SC* __restrict__ vc, int Nt, int N,
@@ -177,6 +290,63 @@ __global__ void k_restrict(const SP* __restrict__ P, const SV* __restrict__ v, S
   }
 }
 
+// Tiled restriction for ntv % 4 == 0 and an even number of right-hand
+// sides: each thread accumulates 4 rows (h, i0..i0+3) x 2 right-hand sides.
+template <class SP, class SV, class SC>
+__global__ void __launch_bounds__(256) k_restrict_tiled(const SP* __restrict__ P, const SV* __restrict__ v,
+                                                        SC* __restrict__ vc, int Nt, int N, int Va) {
+  using R = typename Real<SC>::type;
+  extern __shared__ double smem_d[];
+  const int A = blockIdx.x;
+  const int nc = 2 * Nt;
+  cx<R>* Pc = (cx<R>*)smem_d;                 // [kSites][12][Nt]
+  cx<R>* Xc = Pc + kSites * 12 * Nt;          // [kSites][12][N]
+  const int nrt = nc / 4, nct = N / 2;
+  const int rt = threadIdx.x / nct, ct = threadIdx.x % nct;
+  const bool on = threadIdx.x < nrt * nct;
+  const int r0 = 4 * rt, j0 = 2 * ct;
+  const int h = r0 / Nt, i0 = r0 % Nt;
+  cx<R> acc[4][2];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) acc[a][0] = acc[a][1] = mk<R>(0, 0);
+  for (int q0 = 0; q0 < Va; q0 += kSites) {
+    const int nq = min(kSites, Va - q0);
+    for (int w = threadIdx.x; w < nq * 12 * Nt; w += blockDim.x) {
+      int q = w / (12 * Nt), c = (w / Nt) % 12, i = w % Nt;
+      Pc[w] = ld<SP, R>(P, ((size_t)A * Va + q0 + q) * 12 + c, Nt, i);
+    }
+    for (int w = threadIdx.x; w < nq * 12 * N; w += blockDim.x) {
+      int q = w / (12 * N), c = (w / N) % 12, r = w % N;
+      Xc[w] = ld<SV, R>(v, ((size_t)A * Va + q0 + q) * 12 + c, N, r);
+    }
+    __syncthreads();
+    if (on) {
+      for (int q = 0; q < nq; ++q)
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) {
+          const int c = 6 * h + cc;
+          cx<R> pv[4], xv[2];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) pv[a] = Pc[(q * 12 + c) * Nt + i0 + a];
+          xv[0] = Xc[(q * 12 + c) * N + j0];
+          xv[1] = Xc[(q * 12 + c) * N + j0 + 1];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            fmac_(acc[a][0], pv[a], xv[0]);
+            fmac_(acc[a][1], pv[a], xv[1]);
+          }
+        }
+    }
+    __syncthreads();
+  }
+  if (on) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) st<SC, R>(vc, (size_t)A * nc + r0 + a, N, j0 + b, acc[a][b]);
+  }
+}
+
 // u(x,c,r) = sum_j P_j(x,c) uc[A(x)][(h(c), j)][r]
 template <class SP, class SC, class SU>
 __global__ void k_prolong(const SP* __restrict__ P, const SC* __restrict__ uc, SU* __restrict__ u, int Nt, int N,
@@ -216,10 +386,68 @@ __global__ void k_apply_dc(const cx<typename Real<SC>::type>* __restrict__ Dc, c
   st<SC, R>(y, (size_t)A * nc + row, N, r, acc);
 }
 
+// 8 rows x 1 right-hand side per thread; pairs of columns read as one
+// 16-byte (FP32) load per row; requires 2*ntv % 8 == 0.
+template <class SC>
+__global__ void k_apply_dc_tiled(const cx<typename Real<SC>::type>* __restrict__ Dc, const SC* __restrict__ x,
+                                 SC* __restrict__ y, const int* __restrict__ aggnbr, int nc, int N, size_t nwork) {
+  using R = typename Real<SC>::type;
+  size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= nwork) return;
+  const int r = (int)(t % N);
+  const size_t q = t / N;
+  const int nrt = nc / 8;
+  const int row0 = 8 * (int)(q % nrt);
+  const int A = (int)(q / nrt);
+  cx<R> acc[8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) acc[a] = mk<R>(0, 0);
+  for (int k = 0; k < 9; ++k) {
+    const int B = k == 0 ? A : aggnbr[A * 8 + k - 1];
+    const cx<R>* d = Dc + (((size_t)A * 9 + k) * nc + row0) * nc;
+    for (int col = 0; col < nc; col += 2) {
+      cx<R> x0 = ld<SC, R>(x, (size_t)B * nc + col, N, r);
+      cx<R> x1 = ld<SC, R>(x, (size_t)B * nc + col + 1, N, r);
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        fma_(acc[a], d[(size_t)a * nc + col], x0);
+        fma_(acc[a], d[(size_t)a * nc + col + 1], x1);
+      }
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 8; ++a) st<SC, R>(y, (size_t)A * nc + row0 + a, N, r, acc[a]);
+}
+
+// u = P uc with one thread per (site, chirality, right-hand side): 6 outputs
+// share every load of uc
+template <class SP, class SC, class SU>
+__global__ void k_prolong6(const SP* __restrict__ P, const SC* __restrict__ uc, SU* __restrict__ u, int Nt, int N,
+                           int Va, size_t nwork) {
+  using R = typename Real<SC>::type;
+  size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= nwork) return;
+  const int r = (int)(t % N);
+  const size_t q = t / N;
+  const int h = (int)(q % 2);
+  const size_t s = q / 2;
+  const size_t A = s / Va;
+  cx<R> acc[6];
+#pragma unroll
+  for (int cc = 0; cc < 6; ++cc) acc[cc] = mk<R>(0, 0);
+  for (int j = 0; j < Nt; ++j) {
+    cx<R> w = ld<SC, R>(uc, A * 2 * Nt + h * Nt + j, N, r);
+#pragma unroll
+    for (int cc = 0; cc < 6; ++cc) fma_(acc[cc], ld<SP, R>(P, s * 12 + 6 * h + cc, Nt, j), w);
+  }
+#pragma unroll
+  for (int cc = 0; cc < 6; ++cc) st<SU, R>(u, s * 12 + 6 * h + cc, N, r, acc[cc]);
+}
+
 template <class S>
 __global__ void k_sub_from(const S* b, S* w, size_t n) {  // w = b - w
   size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (t < n) w[t] = from_r<S>((double)to_r(b[t]) - (double)to_r(w[t]));
+  if (t < n) w[t] = from_r<S>(to_r(b[t]) - to_r(w[t]));
 }
 
 template <class S>
@@ -370,20 +598,32 @@ void build_Dc(mrhs_ctx c) {
   if (!c->Dc) c->Dc = dalloc(c, n * 2 * dtype_size(c->work_dtype));
   Agg4 ag;
   for (int m = 0; m < 4; ++m) ag.a[m] = c->g.a[m];
-  int threads = std::max(128, ((nc * nc + 15) / 16 + 31) / 32 * 32);
-  MRHS_REQUIRE(threads <= 1024, MRHS_ERR_SHAPE, "ntv too large for the coarse-operator kernel");
+  const bool tiled = Nt % 4 == 0 && nc <= 64;
+  Prof pr(c, "coarse_op");
   MRHS_DISPATCH(c->tv_dtype, SP, {
     using R = typename Real<SP>::type;
-    size_t smem = sizeof(cx<R>) * kSites * 12 * (size_t)(nc + Nt);
     const cx<R>* U = (const cx<R>*)(sizeof(R) == 8 ? (const void*)c->U64 : (const void*)c->U32);
     const R* Acl = (const R*)(sizeof(R) == 8 ? (const void*)c->A64 : (const void*)c->A32);
-    Prof pr(c, "coarse_op");
-    auto kern = k_coarse_op<SP, R, 16>;
-    MRHS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<c->g.nagg * 9, threads, smem, c->stream>>>((const SP*)c->P, U, Acl, c->nbr, Nt, ag, c->g.Va,
-                                                      (cx<R>*)c->Dc);
+    if (tiled) {
+      size_t smem = sizeof(cx<R>) * kTileSites * 12 * (size_t)(nc + Nt);
+      auto kern = k_coarse_op_tiled<SP, R>;
+      MRHS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      kern<<<c->g.nagg * 5, 256, smem, c->stream>>>((const SP*)c->P, U, Acl, c->nbr, Nt, ag, c->g.Va, (cx<R>*)c->Dc);
+      MRHS_LAUNCH_CHECK("coarse_op_tiled");
+      size_t tot = (size_t)c->g.nagg * 4 * nc * nc;
+      k_coarse_backward<R><<<grid_for(tot, 256), 256, 0, c->stream>>>((cx<R>*)c->Dc, c->aggnbr, c->g.nagg, Nt);
+      MRHS_LAUNCH_CHECK("coarse_backward");
+    } else {
+      int threads = std::max(128, ((nc * nc + 15) / 16 + 31) / 32 * 32);
+      MRHS_REQUIRE(threads <= 1024, MRHS_ERR_SHAPE, "ntv too large for the coarse-operator kernel");
+      size_t smem = sizeof(cx<R>) * kSites * 12 * (size_t)(nc + Nt);
+      auto kern = k_coarse_op<SP, R, 16>;
+      MRHS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      kern<<<c->g.nagg * 9, threads, smem, c->stream>>>((const SP*)c->P, U, Acl, c->nbr, Nt, ag, c->g.Va,
+                                                        (cx<R>*)c->Dc);
+      MRHS_LAUNCH_CHECK("coarse_op");
+    }
   });
-  MRHS_LAUNCH_CHECK("coarse_op");
   c->have_Dc = true;
 }
 
@@ -396,8 +636,21 @@ void restrict_typed(mrhs_ctx c, const void* v, int dv, void* vc, int dc, int N) 
   MRHS_REQUIRE(threads <= 1024, MRHS_ERR_SHAPE, "restriction: ntv*nrhs too large");
   MRHS_REQUIRE(dc == MRHS_F64 || dc == MRHS_F32, MRHS_ERR_ARG, "coarse fields are F64 or F32");
   Prof pr(c, "restrict");
+  const bool tiled = Nt % 4 == 0 && N % 2 == 0 && (nc / 4) * (N / 2) <= 256;
   MRHS_DISPATCH(c->tv_dtype, SP, MRHS_DISPATCH(dv, SV, {
-    if (dc == MRHS_F64) {
+    if (tiled) {
+      if (dc == MRHS_F64) {
+        size_t smem = sizeof(cx<double>) * kSites * 12 * (size_t)(Nt + N);
+        auto kern = k_restrict_tiled<SP, SV, double>;
+        MRHS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<c->g.nagg, 256, smem, c->stream>>>((const SP*)c->P, (const SV*)v, (double*)vc, Nt, N, c->g.Va);
+      } else {
+        size_t smem = sizeof(cx<float>) * kSites * 12 * (size_t)(Nt + N);
+        auto kern = k_restrict_tiled<SP, SV, float>;
+        MRHS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<c->g.nagg, 256, smem, c->stream>>>((const SP*)c->P, (const SV*)v, (float*)vc, Nt, N, c->g.Va);
+      }
+    } else if (dc == MRHS_F64) {
       size_t smem = sizeof(cx<double>) * kSites * 12 * (size_t)(Nt + N);
       auto kern = k_restrict<SP, SV, double, 8>;
       MRHS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -415,13 +668,13 @@ void restrict_typed(mrhs_ctx c, const void* v, int dv, void* vc, int dc, int N) 
 void prolong_typed(mrhs_ctx c, const void* uc, int dc, void* u, int du, int N) {
   MRHS_REQUIRE(c->have_P, MRHS_ERR_STATE, "prolongation before mrhs_build_P");
   MRHS_REQUIRE(dc == MRHS_F64 || dc == MRHS_F32, MRHS_ERR_ARG, "coarse fields are F64 or F32");
-  size_t work = (size_t)c->g.V * 12 * N;
+  size_t work = (size_t)c->g.V * 2 * N;
   Prof pr(c, "prolong");
   MRHS_DISPATCH(c->tv_dtype, SP, MRHS_DISPATCH(du, SU, {
     if (dc == MRHS_F64)
-      k_prolong<SP, double, SU><<<grid_for(work, 256), 256, 0, c->stream>>>((const SP*)c->P, (const double*)uc, (SU*)u, c->ntv, N, c->g.Va, work);
+      k_prolong6<SP, double, SU><<<grid_for(work, 256), 256, 0, c->stream>>>((const SP*)c->P, (const double*)uc, (SU*)u, c->ntv, N, c->g.Va, work);
     else
-      k_prolong<SP, float, SU><<<grid_for(work, 256), 256, 0, c->stream>>>((const SP*)c->P, (const float*)uc, (SU*)u, c->ntv, N, c->g.Va, work);
+      k_prolong6<SP, float, SU><<<grid_for(work, 256), 256, 0, c->stream>>>((const SP*)c->P, (const float*)uc, (SU*)u, c->ntv, N, c->g.Va, work);
   }));
   MRHS_LAUNCH_CHECK("prolong");
 }
@@ -440,8 +693,17 @@ void apply_Dc(mrhs_ctx c, const void* xc, void* yc, int nrhs, int dtype) {
   MRHS_REQUIRE(c->have_Dc, MRHS_ERR_STATE, "D_c used before mrhs_build_Dc");
   MRHS_REQUIRE(dtype == c->work_dtype, MRHS_ERR_ARG, "D_c apply: dtype must be the context's work type");
   const int nc = 2 * c->ntv;
-  size_t work = (size_t)c->g.nagg * nc * nrhs;
   Prof pr(c, "apply_dc");
+  if (nc % 8 == 0) {
+    size_t work = (size_t)c->g.nagg * (nc / 8) * nrhs;
+    if (dtype == MRHS_F64)
+      k_apply_dc_tiled<double><<<grid_for(work, 128), 128, 0, c->stream>>>((const cx<double>*)c->Dc, (const double*)xc, (double*)yc, c->aggnbr, nc, nrhs, work);
+    else
+      k_apply_dc_tiled<float><<<grid_for(work, 128), 128, 0, c->stream>>>((const cx<float>*)c->Dc, (const float*)xc, (float*)yc, c->aggnbr, nc, nrhs, work);
+    MRHS_LAUNCH_CHECK("apply_dc");
+    return;
+  }
+  size_t work = (size_t)c->g.nagg * nc * nrhs;
   if (dtype == MRHS_F64)
     k_apply_dc<double><<<grid_for(work, 256), 256, 0, c->stream>>>((const cx<double>*)c->Dc, (const double*)xc, (double*)yc, c->aggnbr, nc, nrhs, work);
   else

@@ -101,8 +101,12 @@ __device__ __forceinline__ float to_r(float v) { return v; }
 __device__ __forceinline__ float to_r(__nv_bfloat16 v) { return __bfloat162float(v); }
 __device__ __forceinline__ float to_r(__half v) { return __half2float(v); }
 
+// storage conversions; the float overloads keep FP32 data off the FP64 pipe
+// (conversions to and from double run at the FP64 rate, which is low here)
 template <class S>
 __device__ __forceinline__ S from_r(double v);
+template <class S>
+__device__ __forceinline__ S from_r(float v);
 template <>
 __device__ __forceinline__ double from_r<double>(double v) { return v; }
 template <>
@@ -111,6 +115,14 @@ template <>
 __device__ __forceinline__ __nv_bfloat16 from_r<__nv_bfloat16>(double v) { return __float2bfloat16((float)v); }
 template <>
 __device__ __forceinline__ __half from_r<__half>(double v) { return __float2half((float)v); }
+template <>
+__device__ __forceinline__ double from_r<double>(float v) { return (double)v; }
+template <>
+__device__ __forceinline__ float from_r<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_r<__nv_bfloat16>(float v) { return __float2bfloat16(v); }
+template <>
+__device__ __forceinline__ __half from_r<__half>(float v) { return __float2half(v); }
 
 inline size_t dtype_size(int dt) {
   switch (dt) {
@@ -171,6 +183,7 @@ struct mrhs_ctx_s {
   // gauge field and clover, device order
   double* U64 = nullptr;  // [V][4][9] complex
   float* U32 = nullptr;
+  float* U20 = nullptr;   // [V][4][20]: FP32 links padded to 80 bytes (float4-aligned records)
   double* A64 = nullptr;  // [V][2][36]
   float* A32 = nullptr;
   bool have_gauge = false, have_clover = false;
@@ -181,6 +194,7 @@ struct mrhs_ctx_s {
   void* Dc = nullptr;   // [nagg][9][2ntv][2ntv] complex in work dtype
   bool have_tv = false, have_P = false, have_Dc = false;
 
+  float* coef32 = nullptr;   // [65][256][2] float copy of BLAS coefficients
   int* dflag = nullptr;      // device error flag
   int* hflag = nullptr;      // pinned host mirror
   double* hbuf = nullptr;    // pinned host scratch

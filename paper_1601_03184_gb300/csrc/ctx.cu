@@ -147,14 +147,26 @@ __global__ void k_tables_canon(GeomArgs g, const int* nbr, const int* perm, cons
 
 // gauge field: canonical sites s0.. of [V][4][9] complex128 (staging) ->
 // device order, f64 + f32 copies
-__global__ void k_gauge_in(int s0, int ns, const int* perm, const double* Uc, double* U64, float* U32) {
+// U20[x][mu] = (1/2) sgn(x, mu) U_mu(x) in FP32, padded to 20 floats: the hop
+// factor 1/2 and the antiperiodic sign of a hop across the t boundary belong
+// to the link (the forward hop from x and the backward hop from x+mu cross the
+// boundary together)
+__global__ void k_gauge_in(int s0, int ns, const int* perm, const double* Uc, double* U64, float* U32, float* U20,
+                           int Lt_last_start) {
   size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (t >= (size_t)ns * 72) return;
-  size_t s = t / 72, e = t % 72;
-  size_t o = (size_t)perm[s0 + s] * 72 + e;
-  double v = Uc[t];
-  U64[o] = v;
-  U32[o] = (float)v;
+  if (t >= (size_t)ns * 80) return;
+  size_t s = t / 80, e = t % 80;
+  size_t sd = (size_t)perm[s0 + s];
+  size_t mu = e / 20, k = e % 20;
+  if (k < 18) {
+    double v = Uc[s * 72 + mu * 18 + k];
+    U64[sd * 72 + mu * 18 + k] = v;
+    U32[sd * 72 + mu * 18 + k] = (float)v;
+    const bool flip = mu == 3 && (size_t)(s0 + s) >= (size_t)Lt_last_start;
+    U20[sd * 80 + e] = (float)(flip ? -0.5 * v : 0.5 * v);
+  } else {
+    U20[sd * 80 + e] = 0.f;
+  }
 }
 
 // ------------------------------------------------------------ clover ------
@@ -357,7 +369,7 @@ __global__ void k_unpack_c(HT* st, const S* dev, size_t rows, int nrhs) {
 template <class SI, class SO>
 __global__ void k_convert(const SI* x, SO* y, size_t n) {
   size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (t < n) y[t] = from_r<SO>((double)to_r(x[t]));
+  if (t < n) y[t] = from_r<SO>(to_r(x[t]));
 }
 
 void check_host_dtype(int hd) {
@@ -490,6 +502,7 @@ int mrhs_create(const int dims[4], const int agg[4], int ntv, int prec, void* st
       c->aggnbr = (int*)dalloc(c, sizeof(int) * 8 * (size_t)na);
       c->blocks_col = (int*)dalloc(c, sizeof(int) * (size_t)na);
       c->dflag = (int*)dalloc(c, sizeof(int) * 16);
+      c->coef32 = (float*)dalloc(c, sizeof(float) * 65 * 256 * 2);
       MRHS_CUDA(cudaMallocHost((void**)&c->hflag, sizeof(int) * 16));
       GeomArgs ga = geom_args(g);
       k_tables<<<grid_for(V, 256), 256, 0, c->stream>>>(ga, c->nbr, c->perm, c->iperm);
@@ -586,6 +599,7 @@ int mrhs_set_gauge(mrhs_ctx c, const double* U) {
     if (!c->U64) {
       c->U64 = (double*)dalloc(c, n * sizeof(double));
       c->U32 = (float*)dalloc(c, n * sizeof(float));
+      c->U20 = (float*)dalloc(c, (size_t)c->g.V * 80 * sizeof(float));
     }
     // chunks of sites through the staging buffer bound the extra device memory
     const size_t per_site = 72 * sizeof(double);
@@ -594,7 +608,9 @@ int mrhs_set_gauge(mrhs_ctx c, const double* U) {
     for (size_t s0 = 0; s0 < (size_t)c->g.V; s0 += chunk) {
       int ns = (int)std::min(chunk, (size_t)c->g.V - s0);
       MRHS_CUDA(cudaMemcpyAsync(st, U + s0 * 72, ns * per_site, cudaMemcpyHostToDevice, c->stream));
-      k_gauge_in<<<grid_for((size_t)ns * 72, 256), 256, 0, c->stream>>>((int)s0, ns, c->perm, st, c->U64, c->U32);
+      const int lt_last = c->g.L[0] * c->g.L[1] * c->g.L[2] * (c->g.L[3] - 1);  // first canonical site with t = Lt-1
+      k_gauge_in<<<grid_for((size_t)ns * 80, 256), 256, 0, c->stream>>>((int)s0, ns, c->perm, st, c->U64, c->U32, c->U20,
+                                                                       lt_last);
       MRHS_LAUNCH_CHECK("gauge_in");
     }
     MRHS_CUDA(cudaStreamSynchronize(c->stream));

@@ -1,5 +1,7 @@
 // Multi-right-hand-side Wilson-clover stencil (full, block-restricted and
 // residual forms) and the SAP smoother built on it.
+#include <cstdlib>
+
 #include "stencil.cuh"
 
 namespace mrhs {
@@ -104,6 +106,241 @@ __global__ void k_block_mr(S* x, S* rho, S* q, const cx<R>* __restrict__ U, cons
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 full operator with G right-hand sides per thread (N % G == 0), vector
+// loads of the G interleaved right-hand sides, links padded to 20 floats
+// (one float4-aligned record per link, loaded once per thread and applied to
+// all G right-hand sides) and the clover term read as float4.
+template <int G>
+struct VecT;
+template <>
+struct VecT<2> {
+  using T = float2;
+};
+template <>
+struct VecT<4> {
+  using T = float4;
+};
+
+template <int G>
+__device__ __forceinline__ void ldv(const float* p, float v[G]) {
+  if constexpr (G == 2) {
+    float2 t = *reinterpret_cast<const float2*>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+  } else {
+    float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+    v[2] = t.z;
+    v[3] = t.w;
+  }
+}
+template <int G>
+__device__ __forceinline__ void stv(float* p, const float v[G]) {
+  if constexpr (G == 2) {
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+  } else {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+}
+
+// one hop for G right-hand sides: neighbour rows at xn (row base n*12, column
+// offset r0), link record Ul = (1/2) sgn U (20 floats: 9 complex + padding)
+template <int MU, int DIR, int G, int NC>
+__device__ __forceinline__ void hop_vec(float ore[12][G], float oim[12][G], const float* __restrict__ xn, int Nrt,
+                                        const float* __restrict__ Ul) {
+  const int N = NC > 0 ? NC : Nrt;
+  float hre[2][3][G], him[2][3][G];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float pr[4][G], pi[4][G];
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp) {
+      ldv<G>(xn + ((3 * sp + c) * 2 + 0) * N, pr[sp]);
+      ldv<G>(xn + ((3 * sp + c) * 2 + 1) * N, pi[sp]);
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      cx<float> p2 = mk(pr[2][g], pi[2][g]), p3 = mk(pr[3][g], pi[3][g]);
+      cx<float> b0, b1;
+      b_low<MU>(p2, p3, b0, b1);
+      cx<float> h0 = DIR > 0 ? mk(pr[0][g], pi[0][g]) - b0 : mk(pr[0][g], pi[0][g]) + b0;
+      cx<float> h1 = DIR > 0 ? mk(pr[1][g], pi[1][g]) - b1 : mk(pr[1][g], pi[1][g]) + b1;
+      hre[0][c][g] = h0.re;
+      him[0][c][g] = h0.im;
+      hre[1][c][g] = h1.re;
+      him[1][c][g] = h1.im;
+    }
+  }
+  float u[20];
+  const float4* U4 = reinterpret_cast<const float4*>(Ul);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    float4 t = __ldg(U4 + k);
+    u[4 * k] = t.x;
+    u[4 * k + 1] = t.y;
+    u[4 * k + 2] = t.z;
+    u[4 * k + 3] = t.w;
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      cx<float> ch[2];
+#pragma unroll
+      for (int sp = 0; sp < 2; ++sp) {
+        cx<float> acc = mk(0.f, 0.f);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          cx<float> hv = mk(hre[sp][b][g], him[sp][b][g]);
+          if (DIR > 0) fma_(acc, mk(u[2 * (a * 3 + b)], u[2 * (a * 3 + b) + 1]), hv);
+          else fmac_(acc, mk(u[2 * (b * 3 + a)], u[2 * (b * 3 + a) + 1]), hv);
+        }
+        ch[sp] = acc;
+      }
+      cx<float> l0, l1;
+      bdag<MU>(ch[0], ch[1], l0, l1);
+      ore[a][g] -= ch[0].re;
+      oim[a][g] -= ch[0].im;
+      ore[3 + a][g] -= ch[1].re;
+      oim[3 + a][g] -= ch[1].im;
+      if (DIR > 0) {
+        ore[6 + a][g] += l0.re;
+        oim[6 + a][g] += l0.im;
+        ore[9 + a][g] += l1.re;
+        oim[9 + a][g] += l1.im;
+      } else {
+        ore[6 + a][g] -= l0.re;
+        oim[6 + a][g] -= l0.im;
+        ore[9 + a][g] -= l1.re;
+        oim[9 + a][g] -= l1.im;
+      }
+    }
+  }
+}
+
+// y = D x, FP32: one thread per (site, group of G right-hand sides), threads
+// in site order so that the CTAs running at one time cover a compact range of
+// aggregates; output stores are streaming (evict-first) so that L2 keeps the
+// input field.
+template <int G, int NC>
+__global__ void __launch_bounds__(128, G == 2 ? 3 : 2) k_dslash_vec(const float* __restrict__ x, float* __restrict__ y,
+                                                                    const float* __restrict__ U20,
+                                                                    const float* __restrict__ Acl,
+                                                                    const int* __restrict__ nbr, int Nrt, int q0, int nq,
+                                                                    size_t nwork) {
+  const int N = NC > 0 ? NC : Nrt;
+  const int ng = nq / G;  // right-hand sides q0 .. q0+nq-1 of this pass
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= nwork) return;
+  const int r0 = q0 + (int)(t % ng) * G;
+  const size_t s = t / ng;
+  float ore[12][G], oim[12][G];
+  {
+    const float4* A4 = reinterpret_cast<const float4*>(Acl + s * 72);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float q[36];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        float4 v = __ldg(A4 + 9 * h + k);
+        q[4 * k] = v.x;
+        q[4 * k + 1] = v.y;
+        q[4 * k + 2] = v.z;
+        q[4 * k + 3] = v.w;
+      }
+      float pr[6][G], pi[6][G];
+#pragma unroll
+      for (int a = 0; a < 6; ++a) {
+        ldv<G>(x + ((s * 12 + 6 * h + a) * 2 + 0) * N + r0, pr[a]);
+        ldv<G>(x + ((s * 12 + 6 * h + a) * 2 + 1) * N + r0, pi[a]);
+      }
+#pragma unroll
+      for (int a = 0; a < 6; ++a)
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          cx<float> acc = scale(mk(pr[a][g], pi[a][g]), q[a]);
+#pragma unroll
+          for (int b2 = 0; b2 < 6; ++b2) {
+            if (b2 == a) continue;
+            cx<float> m = b2 > a ? mk(q[herm_idx(a, b2)], q[herm_idx(a, b2) + 1])
+                                 : mk(q[herm_idx(b2, a)], -q[herm_idx(b2, a) + 1]);
+            fma_(acc, m, mk(pr[b2][g], pi[b2][g]));
+          }
+          ore[6 * h + a][g] = acc.re;
+          oim[6 * h + a][g] = acc.im;
+        }
+    }
+  }
+#pragma unroll
+  for (int d = 0; d < 2; ++d) {
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      const size_t n = (size_t)(__ldg(nbr + s * 8 + d * 4 + mu) & 0x3fffffff);
+      const float* xn = x + n * 24 * N + r0;
+      const float* Ul = U20 + ((d == 0 ? s : n) * 4 + mu) * 20;
+      if (d == 0) {
+        if (mu == 0) hop_vec<0, +1, G, NC>(ore, oim, xn, Nrt, Ul);
+        if (mu == 1) hop_vec<1, +1, G, NC>(ore, oim, xn, Nrt, Ul);
+        if (mu == 2) hop_vec<2, +1, G, NC>(ore, oim, xn, Nrt, Ul);
+        if (mu == 3) hop_vec<3, +1, G, NC>(ore, oim, xn, Nrt, Ul);
+      } else {
+        if (mu == 0) hop_vec<0, -1, G, NC>(ore, oim, xn, Nrt, Ul);
+        if (mu == 1) hop_vec<1, -1, G, NC>(ore, oim, xn, Nrt, Ul);
+        if (mu == 2) hop_vec<2, -1, G, NC>(ore, oim, xn, Nrt, Ul);
+        if (mu == 3) hop_vec<3, -1, G, NC>(ore, oim, xn, Nrt, Ul);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 12; ++c) {
+    float* yr = y + ((s * 12 + c) * 2 + 0) * N + r0;
+    float* yi = y + ((s * 12 + c) * 2 + 1) * N + r0;
+    if constexpr (G == 2) {
+      __stcs(reinterpret_cast<float2*>(yr), make_float2(ore[c][0], ore[c][1]));
+      __stcs(reinterpret_cast<float2*>(yi), make_float2(oim[c][0], oim[c][1]));
+    } else {
+      __stcs(reinterpret_cast<float4*>(yr), make_float4(ore[c][0], ore[c][1], ore[c][2], ore[c][3]));
+      __stcs(reinterpret_cast<float4*>(yi), make_float4(oim[c][0], oim[c][1], oim[c][2], oim[c][3]));
+    }
+  }
+}
+
+// The right-hand sides are processed in `passes` sweeps over the lattice (a
+// sweep over fewer right-hand sides keeps a larger part of the lattice in L2,
+// at the price of reading links and clover once per sweep).
+static int stencil_passes(int N, int G) {
+  static int forced = [] {
+    const char* e = getenv("MRHS_STENCIL_PASSES");
+    return e ? atoi(e) : 0;
+  }();
+  int p = forced > 0 ? forced : (N >= 16 ? 2 : 1);
+  while (p > 1 && (N % p != 0 || (N / p) % G != 0)) --p;
+  return p;
+}
+
+template <int G, int NC>
+void launch_dslash_vec(mrhs_ctx c, const float* x, float* y, int N) {
+  const int passes = stencil_passes(N, G);
+  const int nq = N / passes;
+  const size_t work = (size_t)c->g.V * (nq / G);
+  for (int p = 0; p < passes; ++p)
+    k_dslash_vec<G, NC><<<grid_for(work, 128), 128, 0, c->stream>>>(x, y, c->U20, c->A32, c->nbr, N, p * nq, nq, work);
+}
+
+template <int G>
+void dslash_vec(mrhs_ctx c, const float* x, float* y, int N) {
+  switch (N) {
+    case 8: launch_dslash_vec<G, 8>(c, x, y, N); break;
+    case 16: launch_dslash_vec<G, 16>(c, x, y, N); break;
+    case 20: launch_dslash_vec<G, 20>(c, x, y, N); break;
+    case 24: launch_dslash_vec<G, 24>(c, x, y, N); break;
+    case 32: launch_dslash_vec<G, 32>(c, x, y, N); break;
+    default: launch_dslash_vec<G, 0>(c, x, y, N); break;
+  }
+}
+
 template <class S, class SB>
 void dslash_t(mrhs_ctx c, const S* x, S* y, const SB* b, int N, int mode, const int* blist, int nblk) {
   using R = typename Real<S>::type;
@@ -157,9 +394,29 @@ void block_mr_t(mrhs_ctx c, S* x, S* rho, S* q, int N, const int* blist, int nbl
 
 }  // namespace
 
+// right-hand sides per thread of the FP32 stencil: MRHS_STENCIL_VEC = 1 (one
+// per thread), 2 or 4; default 4 when nrhs % 4 == 0, else 2 when even
+static int stencil_vec_width() {
+  static int w = [] {
+    const char* e = getenv("MRHS_STENCIL_VEC");
+    int v = e ? atoi(e) : 0;
+    return (v == 1 || v == 2 || v == 4) ? v : 0;
+  }();
+  return w;
+}
+
 void dslash(mrhs_ctx c, const void* x, void* y, const void* b, int nrhs, int dtype, int mode, int colour) {
   MRHS_REQUIRE(c->have_clover, MRHS_ERR_STATE, "operator used before mrhs_build_clover");
   MRHS_REQUIRE(nrhs >= 1, MRHS_ERR_ARG, "nrhs must be >= 1");
+  const int vw = stencil_vec_width();
+  if (dtype == MRHS_F32 && mode == DS_FULL && colour < 0 && c->U20 && nrhs % 2 == 0 && vw != 1) {
+    int G = (nrhs % 4 == 0 && vw != 2) ? 4 : 2;
+    Prof pr(c, "dslash_full");
+    if (G == 4) dslash_vec<4>(c, (const float*)x, (float*)y, nrhs);
+    else dslash_vec<2>(c, (const float*)x, (float*)y, nrhs);
+    MRHS_LAUNCH_CHECK("dslash_vec");
+    return;
+  }
   const int* blist = nullptr;
   int nblk = 0;
   if (colour >= 0) {

@@ -149,9 +149,12 @@ __device__ __forceinline__ void apply_local(cx<float> out[G][12], const SapSmem&
 #undef MRHS_SAP_HOP
 }
 
-// block-wide sum of NV doubles per thread, fixed order; result in red[0..NV)
+// Block-wide sums of NV per-thread partials, fixed order: warp sums in FP32
+// (each thread's partial already covers 12 components), the cross-warp sum in
+// double by one thread per value. FP64 is slow on this GPU, so no thread does
+// more than a handful of double operations. Result in red[0..NV).
 template <int NV>
-__device__ __forceinline__ void block_sum(double v[NV], double* red) {
+__device__ __forceinline__ void block_sum(float v[NV], double* red) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int k = 0; k < NV; ++k)
@@ -159,7 +162,7 @@ __device__ __forceinline__ void block_sum(double v[NV], double* red) {
     for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
   if (lane == 0)
 #pragma unroll
-    for (int k = 0; k < NV; ++k) red[NV + w * NV + k] = v[k];
+    for (int k = 0; k < NV; ++k) red[NV + w * NV + k] = (double)v[k];
   __syncthreads();
   if (threadIdx.x < NV) {
     double a = 0;
@@ -218,8 +221,9 @@ __global__ void k_sap_fused(const SB* __restrict__ b, float* x, const float* __r
     __syncthreads();
     if (act) store_rho<G>(q, sm.R, Va, l);
     __syncthreads();
+    float* salpha = (float*)(sm.red + 3 * G + (blockDim.x >> 5) * 3 * G);  // [G][2]
     for (int it = 0; it < n_mr; ++it) {
-      double v[3 * G];
+      float v[3 * G];
 #pragma unroll
       for (int k = 0; k < 3 * G; ++k) v[k] = 0;
       if (act) {
@@ -241,13 +245,19 @@ __global__ void k_sap_fused(const SB* __restrict__ b, float* x, const float* __r
         }
       }
       block_sum<3 * G>(v, sm.red);  // contains the barrier after all reads of rho
+      if (threadIdx.x < G) {
+        const int g = threadIdx.x;
+        double qq = sm.red[3 * g + 2];
+        salpha[2 * g] = qq > 0 ? (float)(sm.red[3 * g] / qq) : 0.f;
+        salpha[2 * g + 1] = qq > 0 ? (float)(sm.red[3 * g + 1] / qq) : 0.f;
+      }
+      __syncthreads();
       if (act) {
         cx<float> rho[G][12];
         load_rho<G>(rho, sm.R, Va, l);
 #pragma unroll
         for (int g = 0; g < G; ++g) {
-          double qq = sm.red[3 * g + 2];
-          cx<float> al = qq > 0 ? mk((float)(sm.red[3 * g] / qq), (float)(sm.red[3 * g + 1] / qq)) : mk(0.f, 0.f);
+          const cx<float> al = mk(salpha[2 * g], salpha[2 * g + 1]);
 #pragma unroll
           for (int c = 0; c < 12; ++c) {
             fma_(xr[g][c], al, rho[g][c]);
@@ -272,13 +282,204 @@ __global__ void k_sap_fused(const SB* __restrict__ b, float* x, const float* __r
   }
 }
 
+// ---------------------------------------------------------------------------
+// 8-RHS form (N % 8 == 0): one chunk of 8 right-hand sides is exactly one
+// 32-byte sector of every spin-colour row, so every global access of x, b and
+// q moves whole sectors. rho of the chunk lives in shared memory (all Va sites);
+// q and x are updated in place in global memory (the chunk of one domain stays
+// in L2 while its CTA runs); links and clover come through L1, shared by the 8
+// threads of a site. Items (site l, rhs g) = 8*l + g; a thread keeps one g.
+constexpr int kG8 = 8;
+constexpr int kThreads8 = 512;
+
+__device__ __forceinline__ void load_rho8(cx<float> psi[12], const float* sR, int Va, int n, int g) {
+#pragma unroll
+  for (int c = 0; c < 12; ++c)
+    psi[c] = mk(sR[((size_t)(c * 2 + 0) * Va + n) * kG8 + g], sR[((size_t)(c * 2 + 1) * Va + n) * kG8 + g]);
+}
+
+__device__ __forceinline__ size_t gidx(size_t s, int c, int reim, int N, int r) {
+  return ((s * 12 + c) * 2 + reim) * (size_t)N + r;
+}
+
+// D (RESID: all hops; neighbours outside the domain from global x) or D_B at
+// site l of the domain for right-hand side g of the chunk starting at r0
+template <bool RESID>
+__device__ __forceinline__ void apply8(cx<float> out[12], const float* sR, int Va, int l, int s, int blk, int g,
+                                       const int* __restrict__ nbr, const float* x, const float* __restrict__ U,
+                                       const float* __restrict__ Acl, int N, int r0) {
+  cx<float> psi[12];
+  load_rho8(psi, sR, Va, l, g);
+  clover_apply_reg<float>(out, psi, Acl + (size_t)s * 72);
+  const cx<float>* Uc = reinterpret_cast<const cx<float>*>(U);
+#pragma unroll 1
+  for (int d = 0; d < 2; ++d) {
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      const int e = nbr[(size_t)s * 8 + d * 4 + mu];
+      const int n = e & 0x3fffffff;
+      const float sg = (e & 0x40000000) ? -1.f : 1.f;
+      const bool inside = n / Va == blk;
+      if (!inside && !RESID) continue;
+      if (inside) {
+        load_rho8(psi, sR, Va, n - blk * Va, g);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 12; ++c) psi[c] = mk(x[gidx(n, c, 0, N, r0 + g)], x[gidx(n, c, 1, N, r0 + g)]);
+      }
+      const cx<float>* Ul = d == 0 ? Uc + (size_t)s * 36 + mu * 9 : Uc + (size_t)n * 36 + mu * 9;
+      if (d == 0) {
+        switch (mu) {
+          case 0: hop_reg<0, +1, float>(out, psi, Ul, sg); break;
+          case 1: hop_reg<1, +1, float>(out, psi, Ul, sg); break;
+          case 2: hop_reg<2, +1, float>(out, psi, Ul, sg); break;
+          default: hop_reg<3, +1, float>(out, psi, Ul, sg); break;
+        }
+      } else {
+        switch (mu) {
+          case 0: hop_reg<0, -1, float>(out, psi, Ul, sg); break;
+          case 1: hop_reg<1, -1, float>(out, psi, Ul, sg); break;
+          case 2: hop_reg<2, -1, float>(out, psi, Ul, sg); break;
+          default: hop_reg<3, -1, float>(out, psi, Ul, sg); break;
+        }
+      }
+    }
+  }
+}
+
+template <class SB>
+__global__ void __launch_bounds__(kThreads8) k_sap_fused8(const SB* __restrict__ b, float* x, float* qbuf,
+                                                          const float* __restrict__ U, const float* __restrict__ Acl,
+                                                          const int* __restrict__ nbr, int N, int Va,
+                                                          const int* __restrict__ blist, int n_mr) {
+  extern __shared__ double smem_d[];
+  float* sR = (float*)smem_d;                                  // [12][2][Va][8]
+  float* sred = sR + (size_t)24 * Va * kG8;                    // [warps][8][3]
+  double* salpha_d = (double*)(sred + (kThreads8 / 32) * kG8 * 3 + 8);
+  float* salpha = (float*)(salpha_d + 0);                      // [8][2]
+  const int blk = blist[blockIdx.x];
+  const int g = threadIdx.x % kG8;
+  const int items = Va * kG8;
+  float* q = qbuf + (size_t)blockIdx.x * Va * 24 * kG8;        // this CTA's q: [Va][12][2][8]
+  for (int r0 = 0; r0 < N; r0 += kG8) {
+    // stage x of the chunk
+    for (int it = threadIdx.x; it < items; it += kThreads8) {
+      const int l = it / kG8;
+      const size_t s = (size_t)blk * Va + l;
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        sR[((size_t)(c * 2 + 0) * Va + l) * kG8 + g] = x[gidx(s, c, 0, N, r0 + g)];
+        sR[((size_t)(c * 2 + 1) * Va + l) * kG8 + g] = x[gidx(s, c, 1, N, r0 + g)];
+      }
+    }
+    __syncthreads();
+    // r = b - D x into q (global), then into shared memory
+    for (int it = threadIdx.x; it < items; it += kThreads8) {
+      const int l = it / kG8;
+      const int s = blk * Va + l;
+      cx<float> out[12];
+      apply8<true>(out, sR, Va, l, s, blk, g, nbr, x, U, Acl, N, r0);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        q[((size_t)l * 24 + c * 2 + 0) * kG8 + g] = (float)to_r(b[gidx(s, c, 0, N, r0 + g)]) - out[c].re;
+        q[((size_t)l * 24 + c * 2 + 1) * kG8 + g] = (float)to_r(b[gidx(s, c, 1, N, r0 + g)]) - out[c].im;
+      }
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < items; it += kThreads8) {
+      const int l = it / kG8;
+#pragma unroll
+      for (int k = 0; k < 24; ++k) sR[((size_t)k * Va + l) * kG8 + g] = q[((size_t)l * 24 + k) * kG8 + g];
+    }
+    __syncthreads();
+    for (int step = 0; step < n_mr; ++step) {
+      float pr = 0, pi = 0, pq = 0;
+      for (int it = threadIdx.x; it < items; it += kThreads8) {
+        const int l = it / kG8;
+        const int s = blk * Va + l;
+        cx<float> out[12], rho[12];
+        apply8<false>(out, sR, Va, l, s, blk, g, nbr, x, U, Acl, N, r0);
+        load_rho8(rho, sR, Va, l, g);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+          q[((size_t)l * 24 + c * 2 + 0) * kG8 + g] = out[c].re;
+          q[((size_t)l * 24 + c * 2 + 1) * kG8 + g] = out[c].im;
+          pr = fmaf(out[c].re, rho[c].re, fmaf(out[c].im, rho[c].im, pr));
+          pi = fmaf(out[c].re, rho[c].im, fmaf(-out[c].im, rho[c].re, pi));
+          pq = fmaf(out[c].re, out[c].re, fmaf(out[c].im, out[c].im, pq));
+        }
+      }
+      // sums over the lanes that share g (lane % 8 == g), then over warps
+#pragma unroll
+      for (int o = 8; o < 32; o <<= 1) {
+        pr += __shfl_xor_sync(0xffffffffu, pr, o);
+        pi += __shfl_xor_sync(0xffffffffu, pi, o);
+        pq += __shfl_xor_sync(0xffffffffu, pq, o);
+      }
+      const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+      if (lane < kG8) {
+        sred[(w * kG8 + lane) * 3 + 0] = pr;
+        sred[(w * kG8 + lane) * 3 + 1] = pi;
+        sred[(w * kG8 + lane) * 3 + 2] = pq;
+      }
+      __syncthreads();
+      if (threadIdx.x < kG8) {
+        double a = 0, bb = 0, cc = 0;
+        for (int i = 0; i < kThreads8 / 32; ++i) {
+          a += sred[(i * kG8 + threadIdx.x) * 3 + 0];
+          bb += sred[(i * kG8 + threadIdx.x) * 3 + 1];
+          cc += sred[(i * kG8 + threadIdx.x) * 3 + 2];
+        }
+        salpha[2 * threadIdx.x] = cc > 0 ? (float)(a / cc) : 0.f;
+        salpha[2 * threadIdx.x + 1] = cc > 0 ? (float)(bb / cc) : 0.f;
+      }
+      __syncthreads();
+      const cx<float> al = mk(salpha[2 * g], salpha[2 * g + 1]);
+      for (int it = threadIdx.x; it < items; it += kThreads8) {
+        const int l = it / kG8;
+        const size_t s = (size_t)blk * Va + l;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+          const size_t i0 = ((size_t)(c * 2 + 0) * Va + l) * kG8 + g, i1 = ((size_t)(c * 2 + 1) * Va + l) * kG8 + g;
+          cx<float> rv = mk(sR[i0], sR[i1]);
+          cx<float> qv = mk(q[((size_t)l * 24 + c * 2 + 0) * kG8 + g], q[((size_t)l * 24 + c * 2 + 1) * kG8 + g]);
+          const size_t x0 = gidx(s, c, 0, N, r0 + g), x1 = gidx(s, c, 1, N, r0 + g);
+          cx<float> xv = mk(x[x0], x[x1]);
+          fma_(xv, al, rv);
+          x[x0] = xv.re;
+          x[x1] = xv.im;
+          cx<float> t = mk(-qv.re, -qv.im);
+          fma_(rv, al, t);
+          sR[i0] = rv.re;
+          sR[i1] = rv.im;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <class SB>
+void launch_fused8(mrhs_ctx c, const SB* b, float* x, int N, int colour, int n_mr) {
+  const int Va = c->g.Va;
+  size_t smem = sizeof(float) * ((size_t)24 * Va * kG8 + (kThreads8 / 32) * kG8 * 3 + 8) + sizeof(float) * 2 * kG8 + 16;
+  auto kern = k_sap_fused8<SB>;
+  MRHS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int nblk = c->ncol[colour];
+  float* qbuf = (float*)scratch(c, SC_Q, sizeof(float) * (size_t)nblk * Va * 24 * kG8);
+  const int* blist = c->blocks_col + (colour ? c->ncol[0] : 0);
+  Prof pr(c, "sap_fused8");
+  kern<<<nblk, kThreads8, smem, c->stream>>>(b, x, qbuf, c->U32, c->A32, c->nbr, N, Va, blist, n_mr);
+  MRHS_LAUNCH_CHECK("sap_fused8");
+}
+
 template <class SB, int G>
 void launch_fused(mrhs_ctx c, const SB* b, float* x, int N, int colour, int n_mr) {
   const int Va = c->g.Va;
   const int threads = (Va + 31) / 32 * 32;
   const int LS = Va + 1;
   size_t smem = sizeof(float) * (144 * (size_t)LS + ((24 * (size_t)Va * G + 1) & ~(size_t)1)) +
-                sizeof(double) * (3 * G + (threads / 32) * 3 * G);
+                sizeof(double) * (3 * G + (threads / 32) * 3 * G) + sizeof(float) * 2 * G;
   auto kern = k_sap_fused<SB, G>;
   MRHS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int* blist = c->blocks_col + (colour ? c->ncol[0] : 0);
@@ -300,9 +501,17 @@ bool sap_fused_ok(mrhs_ctx c, int dtype) {
 }
 
 void sap_fused(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int n_sweeps, int n_mr) {
+  const bool g8 = nrhs % kG8 == 0 &&
+                  sizeof(float) * ((size_t)24 * c->g.Va * kG8 + 1024) <= (size_t)[&] {
+                    int m = 0;
+                    cudaDeviceGetAttribute(&m, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+                    return m;
+                  }();
   for (int sw = 0; sw < n_sweeps; ++sw)
     for (int col = 0; col < 2; ++col) {
-      if (nrhs % 2 == 0) {
+      if (g8) {
+        MRHS_DISPATCH(bdtype, SB, (launch_fused8<SB>(c, (const SB*)b, (float*)x, nrhs, col, n_mr)));
+      } else if (nrhs % 2 == 0) {
         MRHS_DISPATCH(bdtype, SB, (launch_fused<SB, 2>(c, (const SB*)b, (float*)x, nrhs, col, n_mr)));
       } else {
         MRHS_DISPATCH(bdtype, SB, (launch_fused<SB, 1>(c, (const SB*)b, (float*)x, nrhs, col, n_mr)));

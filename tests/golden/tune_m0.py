@@ -38,15 +38,17 @@ def tune(dims, eps, csw, seed):
     A0 = oracle.clover(dims, U, 0.0, csw)
     n = int(np.prod(dims)) * 12
     count = [0]
+    t = time.time()
 
     def mv(v):
         count[0] += 1
+        if count[0] % 200 == 0:
+            print("  matvecs", count[0], round(time.time() - t, 1), "s", flush=True)
         return oracle.apply_D(dims, U, A0, v.reshape(-1, 12)).reshape(-1)
 
     op = LinearOperator((n, n), matvec=mv, dtype=np.complex128)
-    t = time.time()
     lmax = eigs(op, k=1, which="LM", tol=1e-4, return_eigenvectors=False)
-    low = eigs(op, k=8, which="SR", tol=1e-6, ncv=48, maxiter=20000, return_eigenvectors=False)
+    low = eigs(op, k=4, which="SR", tol=1e-4, ncv=40, maxiter=4000, return_eigenvectors=False)
     low = low[np.argsort(low.real)]
     lam_c = low[0]
     # m0 with |lambda_c + m0| = RATIO * |lambda_max + m0| (leftmost eigenvalue put at +RATIO*|lmax|)

@@ -88,6 +88,17 @@ def test_apply_D_ragged_fp64_and_fp32(ragged):
         assert rel(lat.to_host(yd, nrhs, dt), ref) < tol
 
 
+@pytest.mark.parametrize("nrhs", [6, 8, 12])
+def test_apply_D_fp32_multi_rhs_per_thread(ragged, nrhs):
+    """FP32 stencil with 2 or 4 right-hand sides per thread (nrhs even)."""
+    lat, U, A = ragged
+    x = inputs.gaussian_field((nrhs, lat.V, 12), 620 + nrhs)
+    xd = lat.to_device(x, MRHS_F32)
+    yd = lat.field(nrhs, MRHS_F32)
+    lat.apply_D(xd, yd, nrhs, MRHS_F32)
+    assert rel(lat.to_host(yd, nrhs, MRHS_F32), oracle.apply_D(lat.dims, U, A, x)) < 1e-5
+
+
 def test_apply_D_block_fp64(c1, ragged):
     for lat, U, A in (c1, ragged):
         x = inputs.gaussian_field((4, lat.V, 12), 611)
