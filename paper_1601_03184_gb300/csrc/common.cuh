@@ -193,6 +193,10 @@ struct mrhs_ctx_s {
   void* P = nullptr;    // same
   void* Dc = nullptr;   // [nagg][9][2ntv][2ntv] complex in work dtype
   bool have_tv = false, have_P = false, have_Dc = false;
+  // the setup stores its (unit-norm) test vectors multiplied by tv_scale:
+  // sqrt(12 V) for fp16 storage (entries of order 1, inside the fp16 range),
+  // 1 otherwise; every use of the stored vectors is invariant under scaling
+  double tv_scale = 1.0;
 
   float* coef32 = nullptr;   // [65][256][2] float copy of BLAS coefficients
   int* dflag = nullptr;      // device error flag
@@ -264,6 +268,7 @@ void multi_dot(mrhs_ctx c, const void* X, size_t stride, int K, const void* Y, s
                double* out /* device [K][N][2] */);
 void norms(mrhs_ctx c, const void* X, size_t rows, int N, int dtype, double* out /* device [N] (squared) */);
 void convert(mrhs_ctx c, const void* x, int dx, void* y, int dy, size_t n);
+void convert_scaled(mrhs_ctx c, const void* x, int dx, void* y, int dy, size_t n, float scale);
 void sap_mixed(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int dtype, int n_sweeps, int n_mr);
 // sap.cu: the on-chip SAP (FP32 work fields)
 bool sap_fused_ok(mrhs_ctx c, int dtype);

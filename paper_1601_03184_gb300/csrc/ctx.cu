@@ -372,6 +372,13 @@ __global__ void k_convert(const SI* x, SO* y, size_t n) {
   if (t < n) y[t] = from_r<SO>(to_r(x[t]));
 }
 
+template <class SI, class SO>
+__global__ void k_convert_scaled(const SI* x, SO* y, size_t n, float scale) {
+  using R = typename Real<SI>::type;  // double data stays double
+  size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t < n) y[t] = from_r<SO>(to_r(x[t]) * (R)scale);
+}
+
 void check_host_dtype(int hd) {
   MRHS_REQUIRE(hd == MRHS_F64 || hd == MRHS_F32, MRHS_ERR_ARG, "host dtype must be MRHS_F64 or MRHS_F32");
 }
@@ -455,6 +462,11 @@ void convert(mrhs_ctx c, const void* x, int dx, void* y, int dy, size_t n) {
   Prof pr(c, "convert");
   MRHS_DISPATCH(dx, SI, MRHS_DISPATCH(dy, SO, (k_convert<SI, SO><<<grid_for(n, 256), 256, 0, c->stream>>>((const SI*)x, (SO*)y, n))));
   MRHS_LAUNCH_CHECK("convert");
+}
+void convert_scaled(mrhs_ctx c, const void* x, int dx, void* y, int dy, size_t n, float scale) {
+  Prof pr(c, "convert");
+  MRHS_DISPATCH(dx, SI, MRHS_DISPATCH(dy, SO, (k_convert_scaled<SI, SO><<<grid_for(n, 256), 256, 0, c->stream>>>((const SI*)x, (SO*)y, n, scale))));
+  MRHS_LAUNCH_CHECK("convert_scaled");
 }
 }  // namespace mrhs
 
@@ -682,6 +694,7 @@ int mrhs_set_tv(mrhs_ctx c, const void* tv, int dtype) {
     size_t n = fine_elems(c, c->ntv);
     if (!c->tv) c->tv = dalloc(c, n * dtype_size(c->tv_dtype));
     convert(c, tv, dtype, c->tv, c->tv_dtype, n);
+    c->tv_scale = 1.0;
     c->have_tv = true;
     c->have_P = c->have_Dc = false;
   });
@@ -691,7 +704,14 @@ int mrhs_get_tv(mrhs_ctx c, void* host, int hd) {
   return guarded(c, [&] {
     MRHS_REQUIRE(c && host, MRHS_ERR_ARG, "null argument");
     MRHS_REQUIRE(c->have_tv, MRHS_ERR_STATE, "no test vectors yet");
-    transfer_fine(c, nullptr, host, hd, c->tv, nullptr, c->tv_dtype, c->ntv);
+    if (c->tv_scale != 1.0) {
+      const size_t n = fine_elems(c, c->ntv);
+      void* tmp = scratch(c, SC_FINE1, n * sizeof(float));
+      convert_scaled(c, c->tv, c->tv_dtype, tmp, MRHS_F32, n, (float)(1.0 / c->tv_scale));
+      transfer_fine(c, nullptr, host, hd, tmp, nullptr, MRHS_F32, c->ntv);
+    } else {
+      transfer_fine(c, nullptr, host, hd, c->tv, nullptr, c->tv_dtype, c->ntv);
+    }
   });
 }
 

@@ -1,6 +1,7 @@
 // The setup phase (Sec. 2 and Algorithm 2 of the paper with block length
 // N_b = ntv: the V-cycle is applied to all test vectors at once) and the
 // two-level FGMRES solve used to judge a setup.
+#include <cmath>
 #include <complex>
 #include <vector>
 
@@ -35,7 +36,8 @@ void setup_init(mrhs_ctx c, const void* tv0, int dtype, int init_mode, int n_swe
     }
   }
   normalise_rhs(c, x, (size_t)c->g.V * 12, N, c->work_dtype);
-  convert(c, x, c->work_dtype, c->tv, c->tv_dtype, n);
+  c->tv_scale = c->tv_dtype == MRHS_F16 ? std::sqrt(12.0 * c->g.V) : 1.0;
+  convert_scaled(c, x, c->work_dtype, c->tv, c->tv_dtype, n, (float)c->tv_scale);
   build_P(c);
   build_Dc(c);
 }
@@ -61,7 +63,8 @@ void setup_refine(mrhs_ctx c, int n_iter, int n_sweeps, int n_mr, double ctol, i
     sap_mixed(c, c->tv, c->tv_dtype, x, N, wd, n_sweeps, n_mr);
     // replace the test vectors by the result, then rebuild R = P^dag and D_c
     normalise_rhs(c, x, (size_t)c->g.V * 12, N, wd);
-    convert(c, x, wd, c->tv, c->tv_dtype, n);
+    c->tv_scale = c->tv_dtype == MRHS_F16 ? std::sqrt(12.0 * c->g.V) : 1.0;
+    convert_scaled(c, x, wd, c->tv, c->tv_dtype, n, (float)c->tv_scale);
     build_P(c);
     build_Dc(c);
   }
