@@ -235,3 +235,45 @@ def fgmres(dims, agg, U, A, P, Dc, b, tol=1e-10, restart=25, maxit=500, coarse_t
 
 def relres(dims, U, A, b, x):
     return lib().ora_relres(_i4(dims), _p(_c(U)), _p(_c(A)), _p(_c(b)), _p(_c(x)))
+
+
+# ------------------------------------------------------ learned generator --
+def nn_sizes(widths):
+    c0, c1, c2, c3 = widths
+    return 9 * (c1 * c0 + c2 * c1 + c3 * c2), c1 + c2
+
+
+def nn_forward(dims, U, widths, W, bias, x, linear=False):
+    """x: [nrhs, V, c0*3] complex -> [nrhs, V, c3*3]."""
+    c0, c1, c2, c3 = widths
+    U, W, x = _c(U), _c(W), _c(x)
+    bias = np.ascontiguousarray(bias, dtype=np.float64)
+    nrhs = x.shape[0]
+    out = np.zeros((nrhs, _vol(dims), c3 * 3), np.complex128)
+    _check(lib().ora_nn_forward(_i4(dims), _p(U), c0, c1, c2, c3, _p(W), _p(bias), int(linear), _p(x), _p(out),
+                                nrhs), "nn_forward")
+    return out
+
+
+def nn_backward(dims, U, widths, W, bias, x, dout, linear=False, want_din=False):
+    """Returns (gW, gb, din) with g = dL/dRe + i dL/dIm for complex parameters."""
+    c0, c1, c2, c3 = widths
+    U, W, x, dout = _c(U), _c(W), _c(x), _c(dout)
+    bias = np.ascontiguousarray(bias, dtype=np.float64)
+    nw, nb = nn_sizes(widths)
+    gW = np.zeros(nw, np.complex128)
+    gb = np.zeros(nb, np.float64)
+    din = np.zeros_like(x) if want_din else None
+    _check(lib().ora_nn_backward(_i4(dims), _p(U), c0, c1, c2, c3, _p(W), _p(bias), int(linear), _p(x), _p(dout),
+                                 x.shape[0], _p(gW), _p(gb), _p(din) if want_din else None), "nn_backward")
+    return gW, gb, din
+
+
+def nn_loss(dims, agg, U, A, P, v, lam):
+    """(loss, dv) of sum_r |D v_r|^2/|v_r|^2 + lam |(1 - P P^dag) v_r|^2/|v_r|^2."""
+    U, A, P, v = _c(U), _c(A), _c(P), _c(v)
+    dv = np.zeros_like(v)
+    loss = ctypes.c_double(0)
+    _check(lib().ora_nn_loss(_i4(dims), _i4(agg), P.shape[0], _p(U), _p(A), _p(P), _p(v), v.shape[0],
+                             ctypes.c_double(lam), ctypes.byref(loss), _p(dv)), "nn_loss")
+    return loss.value, dv

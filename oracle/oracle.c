@@ -980,3 +980,317 @@ double ora_relres(const int* dims, const cplx* U, const cplx* A, const cplx* b, 
   free(r);
   return sqrt(rr / bb);
 }
+
+/* ------------------------------------------------------------------ */
+/* learned test-vector generator: gauge-covariant convolution network   */
+/* ------------------------------------------------------------------ */
+/* Channels are colour triplets: a field of C channels is h[s][c][a],
+ * a = colour. One layer maps C_in -> C_out channels:
+ *   z(x)[c] = sum_{k=0..8} sum_c' W[k][c][c'] T_k(x) h(x + k)[c']
+ * with k = 0 the site itself (T_0 = 1), k = 1+mu the +mu neighbour
+ * (T = U_mu(x)), k = 5+mu the -mu neighbour (T = U_mu(x-mu)^dag) and the
+ * fermion sign -1 on hops across the t boundary. W acts on the channel
+ * index only, so the layer is gauge covariant. Between layers the
+ * nonlinearity acts on every channel triplet:
+ *   modrelu(z; b)[c] = z[c] * max(0, |z[c]| + b[c]) / |z[c]|  (0 if z[c] = 0),
+ * which depends on |z[c]| only and is therefore gauge invariant.
+ * The network is 3 layers, C0 -> C1 -> C2 -> C3, modrelu after layers 1 and 2
+ * (skipped when linear != 0). Spinors enter as 4 channels (spin) x 3 colours.
+ * Weights: W_l[9][C_{l+1}][C_l] complex for l = 0, 1, 2, then biases
+ * b_1[C1], b_2[C2] (real), packed in that order in one array.
+ * Gradients use G = dL/dRe(p) + i dL/dIm(p) for complex parameters p and
+ * dL/db for the biases. */
+
+static void covconv(const geom_t* g, const cplx* U, int cin, int cout, const cplx* W, const cplx* h, cplx* z) {
+#pragma omp parallel for schedule(static)
+  for (int s = 0; s < g->V; ++s) {
+    cplx* zs = z + (size_t)s * cout * 3;
+    for (int i = 0; i < cout * 3; ++i) zs[i] = 0;
+    for (int k = 0; k < 9; ++k) {
+      int n = s, flip = 0;
+      su3 T;
+      if (k == 0) {
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) T.m[a][b] = (a == b);
+      } else if (k <= 4) {
+        n = neighbour(g, s, k - 1, +1, &flip);
+        T = link_of(U, s, k - 1);
+      } else {
+        n = neighbour(g, s, k - 5, -1, &flip);
+        T = dag(link_of(U, n, k - 5));
+      }
+      double sg = flip ? -1.0 : 1.0;
+      const cplx* hn = h + (size_t)n * cin * 3;
+      for (int cp = 0; cp < cin; ++cp) {
+        cplx t[3];
+        for (int a = 0; a < 3; ++a) {
+          t[a] = 0;
+          for (int b = 0; b < 3; ++b) t[a] += T.m[a][b] * hn[cp * 3 + b];
+          t[a] *= sg;
+        }
+        for (int c = 0; c < cout; ++c) {
+          cplx w = W[((size_t)k * cout + c) * cin + cp];
+          for (int a = 0; a < 3; ++a) zs[c * 3 + a] += w * t[a];
+        }
+      }
+    }
+  }
+}
+
+static void modrelu(int V, int C, const double* bias, const cplx* z, cplx* h) {
+  for (int s = 0; s < V; ++s)
+    for (int c = 0; c < C; ++c) {
+      const cplx* zc = z + ((size_t)s * C + c) * 3;
+      cplx* hc = h + ((size_t)s * C + c) * 3;
+      double n = sqrt(norm2(zc, 3));
+      double f = (n > 0 && n + bias[c] > 0) ? (n + bias[c]) / n : 0.0;
+      for (int a = 0; a < 3; ++a) hc[a] = zc[a] * f;
+    }
+}
+
+static size_t nn_wsize(int c0, int c1, int c2, int c3) {
+  return (size_t)9 * ((size_t)c1 * c0 + (size_t)c2 * c1 + (size_t)c3 * c2);
+}
+
+/* out = net(in) for nrhs right-hand sides; in [nrhs][V][c0*3], out [nrhs][V][c3*3] */
+int ora_nn_forward(const int* dims, const cplx* U, int c0, int c1, int c2, int c3, const cplx* W,
+                   const double* bias, int linear, const cplx* in, cplx* out, int nrhs) {
+  geom_t g;
+  const int one[4] = {1, 1, 1, 1};
+  if (geom_init(&g, dims, one)) return -1;
+  const cplx* W0 = W;
+  const cplx* W1 = W0 + (size_t)9 * c1 * c0;
+  const cplx* W2 = W1 + (size_t)9 * c2 * c1;
+  const double* b1 = bias;
+  const double* b2 = bias + c1;
+  size_t V = g.V;
+  cplx* z1 = (cplx*)malloc(sizeof(cplx) * V * c1 * 3);
+  cplx* h1 = (cplx*)malloc(sizeof(cplx) * V * c1 * 3);
+  cplx* z2 = (cplx*)malloc(sizeof(cplx) * V * c2 * 3);
+  cplx* h2 = (cplx*)malloc(sizeof(cplx) * V * c2 * 3);
+  for (int r = 0; r < nrhs; ++r) {
+    covconv(&g, U, c0, c1, W0, in + (size_t)r * V * c0 * 3, z1);
+    if (linear) memcpy(h1, z1, sizeof(cplx) * V * c1 * 3);
+    else modrelu(g.V, c1, b1, z1, h1);
+    covconv(&g, U, c1, c2, W1, h1, z2);
+    if (linear) memcpy(h2, z2, sizeof(cplx) * V * c2 * 3);
+    else modrelu(g.V, c2, b2, z2, h2);
+    covconv(&g, U, c2, c3, W2, h2, out + (size_t)r * V * c3 * 3);
+  }
+  free(z1);
+  free(h1);
+  free(z2);
+  free(h2);
+  return 0;
+}
+
+/* dz = adjoint of covconv applied to dz_out (gradient with respect to h):
+ * dh(y)[c'] = sum_k sum_c conj(W[k][c][c']) T_k(x)^dag dz(x)[c], x = y - k */
+static void covconv_adjoint(const geom_t* g, const cplx* U, int cin, int cout, const cplx* W, const cplx* dz,
+                            cplx* dh) {
+  memset(dh, 0, sizeof(cplx) * (size_t)g->V * cin * 3);
+  for (int s = 0; s < g->V; ++s) {
+    const cplx* dzs = dz + (size_t)s * cout * 3;
+    for (int k = 0; k < 9; ++k) {
+      int n = s, flip = 0;
+      su3 T;
+      if (k == 0) {
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) T.m[a][b] = (a == b);
+      } else if (k <= 4) {
+        n = neighbour(g, s, k - 1, +1, &flip);
+        T = link_of(U, s, k - 1);
+      } else {
+        n = neighbour(g, s, k - 5, -1, &flip);
+        T = dag(link_of(U, n, k - 5));
+      }
+      double sg = flip ? -1.0 : 1.0;
+      cplx* dhn = dh + (size_t)n * cin * 3;
+      for (int cp = 0; cp < cin; ++cp) {
+        cplx u[3] = {0, 0, 0};
+        for (int c = 0; c < cout; ++c) {
+          cplx w = conj(W[((size_t)k * cout + c) * cin + cp]);
+          for (int a = 0; a < 3; ++a) u[a] += w * dzs[c * 3 + a];
+        }
+        for (int b = 0; b < 3; ++b) {
+          cplx acc = 0;
+          for (int a = 0; a < 3; ++a) acc += conj(T.m[a][b]) * u[a];
+          dhn[cp * 3 + b] += sg * acc;
+        }
+      }
+    }
+  }
+}
+
+/* gW[k][c][c'] += sum_{x,a} dz(x)[c][a] conj((T_k h(x+k))[c'][a]) */
+static void covconv_wgrad(const geom_t* g, const cplx* U, int cin, int cout, const cplx* dz, const cplx* h,
+                          cplx* gW) {
+  for (int s = 0; s < g->V; ++s) {
+    const cplx* dzs = dz + (size_t)s * cout * 3;
+    for (int k = 0; k < 9; ++k) {
+      int n = s, flip = 0;
+      su3 T;
+      if (k == 0) {
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) T.m[a][b] = (a == b);
+      } else if (k <= 4) {
+        n = neighbour(g, s, k - 1, +1, &flip);
+        T = link_of(U, s, k - 1);
+      } else {
+        n = neighbour(g, s, k - 5, -1, &flip);
+        T = dag(link_of(U, n, k - 5));
+      }
+      double sg = flip ? -1.0 : 1.0;
+      const cplx* hn = h + (size_t)n * cin * 3;
+      for (int cp = 0; cp < cin; ++cp) {
+        cplx t[3];
+        for (int a = 0; a < 3; ++a) {
+          t[a] = 0;
+          for (int b = 0; b < 3; ++b) t[a] += T.m[a][b] * hn[cp * 3 + b];
+          t[a] *= sg;
+        }
+        for (int c = 0; c < cout; ++c) {
+          cplx acc = 0;
+          for (int a = 0; a < 3; ++a) acc += dzs[c * 3 + a] * conj(t[a]);
+          gW[((size_t)k * cout + c) * cin + cp] += acc;
+        }
+      }
+    }
+  }
+}
+
+/* backward of modrelu: given z, b and dh, returns dz and accumulates db */
+static void modrelu_backward(int V, int C, const double* bias, const cplx* z, const cplx* dh, cplx* dz, double* db) {
+  for (int s = 0; s < V; ++s)
+    for (int c = 0; c < C; ++c) {
+      const cplx* zc = z + ((size_t)s * C + c) * 3;
+      const cplx* dhc = dh + ((size_t)s * C + c) * 3;
+      cplx* dzc = dz + ((size_t)s * C + c) * 3;
+      double n = sqrt(norm2(zc, 3));
+      if (!(n > 0) || n + bias[c] <= 0) {
+        for (int a = 0; a < 3; ++a) dzc[a] = 0;
+        continue;
+      }
+      double zd = 0; /* real dot of z and dh */
+      for (int a = 0; a < 3; ++a) zd += creal(zc[a]) * creal(dhc[a]) + cimag(zc[a]) * cimag(dhc[a]);
+      double f = 1.0 + bias[c] / n;
+      for (int a = 0; a < 3; ++a) dzc[a] = f * dhc[a] - bias[c] / (n * n * n) * zd * zc[a];
+      db[c] += zd / n;
+    }
+}
+
+/* Gradient of a real loss through the network: given dout = dL/dRe(out) +
+ * i dL/dIm(out) [nrhs][V][c3*3], returns the weight gradients gW (same
+ * packing as W), the bias gradients gb [c1 + c2] and (if din != NULL) the
+ * gradient with respect to the input [nrhs][V][c0*3]. */
+int ora_nn_backward(const int* dims, const cplx* U, int c0, int c1, int c2, int c3, const cplx* W,
+                    const double* bias, int linear, const cplx* in, const cplx* dout, int nrhs, cplx* gW, double* gb,
+                    cplx* din) {
+  geom_t g;
+  const int one[4] = {1, 1, 1, 1};
+  if (geom_init(&g, dims, one)) return -1;
+  const cplx* W0 = W;
+  const cplx* W1 = W0 + (size_t)9 * c1 * c0;
+  const cplx* W2 = W1 + (size_t)9 * c2 * c1;
+  cplx* gW0 = gW;
+  cplx* gW1 = gW0 + (size_t)9 * c1 * c0;
+  cplx* gW2 = gW1 + (size_t)9 * c2 * c1;
+  const double* b1 = bias;
+  const double* b2 = bias + c1;
+  memset(gW, 0, sizeof(cplx) * nn_wsize(c0, c1, c2, c3));
+  memset(gb, 0, sizeof(double) * (size_t)(c1 + c2));
+  size_t V = g.V;
+  cplx* z1 = (cplx*)malloc(sizeof(cplx) * V * c1 * 3);
+  cplx* h1 = (cplx*)malloc(sizeof(cplx) * V * c1 * 3);
+  cplx* z2 = (cplx*)malloc(sizeof(cplx) * V * c2 * 3);
+  cplx* h2 = (cplx*)malloc(sizeof(cplx) * V * c2 * 3);
+  cplx* dh2 = (cplx*)malloc(sizeof(cplx) * V * c2 * 3);
+  cplx* dz2 = (cplx*)malloc(sizeof(cplx) * V * c2 * 3);
+  cplx* dh1 = (cplx*)malloc(sizeof(cplx) * V * c1 * 3);
+  cplx* dz1 = (cplx*)malloc(sizeof(cplx) * V * c1 * 3);
+  cplx* dh0 = (cplx*)malloc(sizeof(cplx) * V * c0 * 3);
+  for (int r = 0; r < nrhs; ++r) {
+    const cplx* h0 = in + (size_t)r * V * c0 * 3;
+    const cplx* d3 = dout + (size_t)r * V * c3 * 3;
+    covconv(&g, U, c0, c1, W0, h0, z1);
+    if (linear) memcpy(h1, z1, sizeof(cplx) * V * c1 * 3);
+    else modrelu(g.V, c1, b1, z1, h1);
+    covconv(&g, U, c1, c2, W1, h1, z2);
+    if (linear) memcpy(h2, z2, sizeof(cplx) * V * c2 * 3);
+    else modrelu(g.V, c2, b2, z2, h2);
+    /* layer 2 */
+    covconv_wgrad(&g, U, c2, c3, d3, h2, gW2);
+    covconv_adjoint(&g, U, c2, c3, W2, d3, dh2);
+    if (linear) memcpy(dz2, dh2, sizeof(cplx) * V * c2 * 3);
+    else modrelu_backward(g.V, c2, b2, z2, dh2, dz2, gb + c1);
+    /* layer 1 */
+    covconv_wgrad(&g, U, c1, c2, dz2, h1, gW1);
+    covconv_adjoint(&g, U, c1, c2, W1, dz2, dh1);
+    if (linear) memcpy(dz1, dh1, sizeof(cplx) * V * c1 * 3);
+    else modrelu_backward(g.V, c1, b1, z1, dh1, dz1, gb);
+    /* layer 0 */
+    covconv_wgrad(&g, U, c0, c1, dz1, h0, gW0);
+    if (din) {
+      covconv_adjoint(&g, U, c0, c1, W0, dz1, dh0);
+      memcpy(din + (size_t)r * V * c0 * 3, dh0, sizeof(cplx) * V * c0 * 3);
+    }
+  }
+  free(z1);
+  free(h1);
+  free(z2);
+  free(h2);
+  free(dh2);
+  free(dz2);
+  free(dh1);
+  free(dz1);
+  free(dh0);
+  return 0;
+}
+
+/* Training loss of the learned test vectors v (nrhs of them) and its
+ * gradient dv = dL/dRe(v) + i dL/dIm(v):
+ *   L = sum_r |D v_r|^2/|v_r|^2 + lambda |v_r - P P^dag v_r|^2/|v_r|^2
+ * with P the prolongation of a plain setup (columns orthonormal per
+ * aggregate and chirality, [ntv][V][12]). D^dag = gamma_5 D gamma_5. */
+int ora_nn_loss(const int* dims, const int* agg, int ntv, const cplx* U, const cplx* A, const cplx* P,
+                const cplx* v, int nrhs, double lambda, double* loss, cplx* dv) {
+  geom_t g;
+  if (geom_init(&g, dims, agg)) return -1;
+  init_gammas();
+  size_t n = (size_t)g.V * 12;
+  size_t nc = (size_t)g.nagg * 2 * ntv;
+  cplx* Dv = (cplx*)malloc(sizeof(cplx) * n);
+  cplx* DDv = (cplx*)malloc(sizeof(cplx) * n);
+  cplx* vc = (cplx*)malloc(sizeof(cplx) * nc);
+  cplx* pv = (cplx*)malloc(sizeof(cplx) * n);
+  double total = 0;
+  for (int r = 0; r < nrhs; ++r) {
+    const cplx* vr = v + r * n;
+    cplx* dvr = dv ? dv + r * n : NULL;
+    double vv = norm2(vr, n);
+#pragma omp parallel for schedule(static)
+    for (int s = 0; s < g.V; ++s) apply_D_site(&g, U, A, vr, Dv, s, -1);
+    double dd = norm2(Dv, n);
+    /* gamma_5 D gamma_5 (D v) */
+    for (size_t i = 0; i < n; ++i) DDv[i] = (i % 12) < 6 ? Dv[i] : -Dv[i];
+    cplx* tmp = pv;
+#pragma omp parallel for schedule(static)
+    for (int s = 0; s < g.V; ++s) apply_D_site(&g, U, A, DDv, tmp, s, -1);
+    for (size_t i = 0; i < n; ++i) DDv[i] = (i % 12) < 6 ? tmp[i] : -tmp[i];
+    /* q = v - P P^dag v */
+    restrict_one(&g, ntv, P, vr, vc);
+    prolong_one(&g, ntv, P, vc, pv);
+    for (size_t i = 0; i < n; ++i) pv[i] = vr[i] - pv[i];
+    double qq = norm2(pv, n);
+    total += dd / vv + lambda * qq / vv;
+    if (dvr)
+      for (size_t i = 0; i < n; ++i)
+        dvr[i] = 2.0 * (DDv[i] / vv - dd * vr[i] / (vv * vv)) + 2.0 * lambda * (pv[i] / vv - qq * vr[i] / (vv * vv));
+  }
+  *loss = total;
+  free(Dv);
+  free(DDv);
+  free(vc);
+  free(pv);
+  return 0;
+}

@@ -1,0 +1,117 @@
+"""Pins of the oracle's learned test-vector generator (gauge-covariant
+convolution network) and of its training loss: central finite differences of
+every parameter class and of the input, gauge covariance, and the identity
+network."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1601_03184_gb300 import inputs
+from lattice_helpers import colour_rotate, gauge_transform, vol
+
+DIMS = (2, 2, 2, 4)
+WIDTHS = (4, 3, 2, 4)
+
+
+def params(seed, widths=WIDTHS, scale=0.3):
+    nw, nb = oracle.nn_sizes(widths)
+    rng = np.random.default_rng(seed)
+    W = scale * (rng.standard_normal(nw) + 1j * rng.standard_normal(nw))
+    b = 0.2 * rng.standard_normal(nb)
+    return W, b
+
+
+def net_loss(U, W, b, x, dout_weights, linear=False):
+    out = oracle.nn_forward(DIMS, U, WIDTHS, W, b, x, linear)
+    # a real loss with a known gradient: L = sum Re(conj(c) out) + |out|^2
+    return float(np.sum((np.conj(dout_weights) * out).real) + np.sum(np.abs(out) ** 2)), out
+
+
+@pytest.mark.parametrize("linear", [False, True])
+def test_nn_gradients_by_central_differences(linear):
+    U = inputs.gauge_field(DIMS, 0.5, 11)
+    W, b = params(12)
+    x = inputs.gaussian_field((2, vol(DIMS), 12), 13)
+    cw = inputs.gaussian_field((2, vol(DIMS), 12), 14)
+    L0, out = net_loss(U, W, b, x, cw, linear)
+    dout = cw + 2 * out  # dL/dRe(out) + i dL/dIm(out)
+    gW, gb, din = oracle.nn_backward(DIMS, U, WIDTHS, W, b, x, dout, linear, want_din=True)
+    h = 1e-6
+    rng = np.random.default_rng(15)
+    for i in rng.choice(len(W), 12, replace=False):
+        for part, unit in ((gW[i].real, 1.0), (gW[i].imag, 1j)):
+            Wp, Wm = W.copy(), W.copy()
+            Wp[i] += h * unit
+            Wm[i] -= h * unit
+            fd = (net_loss(U, Wp, b, x, cw, linear)[0] - net_loss(U, Wm, b, x, cw, linear)[0]) / (2 * h)
+            assert abs(fd - part) <= 1e-6 * max(1.0, abs(fd))
+    if not linear:
+        for i in range(len(b)):
+            bp, bm = b.copy(), b.copy()
+            bp[i] += h
+            bm[i] -= h
+            fd = (net_loss(U, W, bp, x, cw)[0] - net_loss(U, W, bm, x, cw)[0]) / (2 * h)
+            assert abs(fd - gb[i]) <= 1e-6 * max(1.0, abs(fd))
+    for (r, s, c) in [(0, 0, 0), (1, 7, 5), (0, 15, 11)]:
+        for unit, part in ((1.0, din[r, s, c].real), (1j, din[r, s, c].imag)):
+            xp, xm = x.copy(), x.copy()
+            xp[r, s, c] += h * unit
+            xm[r, s, c] -= h * unit
+            fd = (net_loss(U, W, b, xp, cw, linear)[0] - net_loss(U, W, b, xm, cw, linear)[0]) / (2 * h)
+            assert abs(fd - part) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_nn_is_gauge_covariant():
+    dims = (4, 4, 4, 4)
+    U = inputs.gauge_field(dims, 0.5, 21)
+    widths = (4, 5, 5, 4)
+    W, b = params(22, widths)
+    x = inputs.gaussian_field((1, vol(dims), 12), 23)
+    Om = inputs.random_su3(vol(dims), 24)
+    y = oracle.nn_forward(dims, U, widths, W, b, x)
+    yt = oracle.nn_forward(dims, gauge_transform(dims, U, Om), widths, W, b, colour_rotate(Om, x))
+    assert np.abs(yt - colour_rotate(Om, y)).max() < 1e-12 * np.abs(y).max()
+
+
+def test_identity_network():
+    """Linear net with W_0 = identity on channels at k = 0 and every other
+    weight zero returns its input."""
+    widths = (4, 4, 4, 4)
+    nw, nb = oracle.nn_sizes(widths)
+    W = np.zeros(nw, np.complex128)
+    for layer in range(3):
+        off = layer * 9 * 16
+        for c in range(4):
+            W[off + c * 4 + c] = 1.0  # k = 0 block of layer `layer`
+    U = inputs.gauge_field(DIMS, 0.5, 31)
+    x = inputs.gaussian_field((2, vol(DIMS), 12), 32)
+    y = oracle.nn_forward(DIMS, U, widths, W, np.zeros(nb), x, linear=True)
+    assert np.abs(y - x).max() < 1e-15
+
+
+def test_loss_gradient_by_central_differences():
+    dims, agg, ntv = (4, 4, 4, 4), (2, 2, 2, 2), 4
+    U = inputs.gauge_field(dims, 0.3, 41)
+    A = oracle.clover(dims, U, -0.2, 1.0)
+    P = oracle.gram_schmidt(dims, agg, inputs.test_vectors(ntv, dims, 42))
+    v = inputs.gaussian_field((2, vol(dims), 12), 43)
+    lam = 0.7
+    L, dv = oracle.nn_loss(dims, agg, U, A, P, v, lam)
+    # the loss itself from its definition with dense operators
+    from lattice_helpers import dense_D, dense_P
+    Dm = dense_D(dims, U, A)
+    Pm = dense_P(dims, agg, P)
+    ref = 0.0
+    for r in range(2):
+        vr = v[r].reshape(-1)
+        q = vr - Pm @ (Pm.conj().T @ vr)
+        ref += np.linalg.norm(Dm @ vr) ** 2 / np.linalg.norm(vr) ** 2 + lam * np.linalg.norm(q) ** 2 / np.linalg.norm(vr) ** 2
+    assert abs(L - ref) < 1e-12 * ref
+    h = 1e-6
+    for (r, s, c) in [(0, 3, 2), (1, 100, 7), (1, 255, 11)]:
+        for unit, part in ((1.0, dv[r, s, c].real), (1j, dv[r, s, c].imag)):
+            vp, vm = v.copy(), v.copy()
+            vp[r, s, c] += h * unit
+            vm[r, s, c] -= h * unit
+            fd = (oracle.nn_loss(dims, agg, U, A, P, vp, lam)[0] - oracle.nn_loss(dims, agg, U, A, P, vm, lam)[0]) / (2 * h)
+            assert abs(fd - part) <= 1e-6 * max(1.0, abs(fd))
