@@ -233,6 +233,46 @@ int mrhs_setup_init(mrhs_ctx ctx, const void* tv0, int dtype, int init_mode, int
 int mrhs_setup_refine(mrhs_ctx ctx, int n_iter, int n_sweeps, int n_mr, double coarse_tol, int coarse_restart,
                       int coarse_maxit, int* coarse_iters);
 
+/* ------------------------------------------------- learned generator */
+
+/* A gauge-covariant nearest-neighbour convolution network that maps test
+ * vectors after one SAP sweep to near-null vectors (a project form beside the
+ * paper's method; the paper itself has none). Channels are colour triplets;
+ * widths = {4, C1, C2, 4}, C1, C2 <= 32 (a spinor is 4 spin channels x 3
+ * colours). Layer: z(x)[c] = sum_{k=0..8} sum_c' W[k][c][c'] s_k T_k(x)
+ * h(n_k(x))[c'] with k = 0 the site (T = 1), k = 1+mu the +mu neighbour
+ * (T = U_mu(x)), k = 5+mu the -mu neighbour (T = U_mu(x-mu)^dag), s_k = -1 on
+ * hops across the t boundary; modReLU h[c] = z[c] max(0,|z[c]|+b[c])/|z[c]|
+ * after layers 1 and 2. Parameters (host float arrays): complex W of the three
+ * layers ([9][C_out][C_in], (re, im) pairs) then the real biases b1[C1],
+ * b2[C2]. bf16_weights != 0: forward and backward use the weights rounded to
+ * bf16 (master copy and Adam state stay FP32). Fields are FP32 device fields
+ * of the context. Gradients are dL/dRe + i dL/dIm. */
+int mrhs_nn_create(mrhs_ctx ctx, const int widths[4], int bf16_weights);
+int mrhs_nn_num_params(mrhs_ctx ctx, long long* n_complex, long long* n_real);
+int mrhs_nn_set_weights(mrhs_ctx ctx, const float* host);
+/* compute_copy != 0: the weights the kernels use (bf16-rounded if enabled) */
+int mrhs_nn_get_weights(mrhs_ctx ctx, float* host, int compute_copy);
+int mrhs_nn_get_grads(mrhs_ctx ctx, float* host);
+int mrhs_nn_zero_grads(mrhs_ctx ctx);
+/* out = net(in); keeps the activations for mrhs_nn_backward */
+int mrhs_nn_forward(mrhs_ctx ctx, const void* in, void* out, int nrhs);
+/* accumulates the parameter gradients of a real loss with dL/dout given in
+ * grad_out; grad_in (may be NULL) receives dL/din */
+int mrhs_nn_backward(mrhs_ctx ctx, const void* grad_out, void* grad_in, int nrhs);
+/* training loss L = sum_r |D v_r|^2/|v_r|^2 + lambda |v_r - P P^dag v_r|^2/|v_r|^2
+ * with P the context's current prolongation (a plain setup of this gauge
+ * field); grad_v (may be NULL) receives dL/dv; per_rhs (host, may be NULL)
+ * the terms of every right-hand side */
+int mrhs_nn_loss(mrhs_ctx ctx, const void* v, void* grad_v, int nrhs, double lambda, double* loss, double* per_rhs);
+/* one Adam step (step counts from 1) on the accumulated gradients */
+int mrhs_nn_adam(mrhs_ctx ctx, float lr, float beta1, float beta2, float eps, int step);
+/* forward + loss + backward + Adam (beta 0.9, 0.999, eps 1e-8) on v_in */
+int mrhs_nn_train_step(mrhs_ctx ctx, const void* v_in, int nrhs, double lambda, float lr, int step, double* loss);
+/* learned initial phase: x = SAP^n_sweeps(b = tv0, x0 = 0), v = net(x)
+ * normalised, then P and D_c (replaces the initial phase's SAP sweeps) */
+int mrhs_setup_init_learned(mrhs_ctx ctx, const void* tv0, int dtype, int n_sweeps, int n_mr);
+
 /* copy the test vectors / P out: host canonical [ntv][V][12] (complex128
  * for MRHS_F64, complex64 for MRHS_F32). Column j of P is the orthonormalised
  * v_j; its chirality-h part is the prolongation column (h, j). */

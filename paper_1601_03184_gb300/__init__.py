@@ -64,6 +64,18 @@ _SIGS = {
     "mrhs_get_Dc": (_I, [_VP, _VP, _I]),
     "mrhs_profile": (_I, [_VP, _I]),
     "mrhs_profile_read": (_I, [_VP, _I, ctypes.c_char_p, _I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D)]),
+    "mrhs_nn_create": (_I, [_VP, ctypes.POINTER(_I), _I]),
+    "mrhs_nn_num_params": (_I, [_VP, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
+    "mrhs_nn_set_weights": (_I, [_VP, _VP]),
+    "mrhs_nn_get_weights": (_I, [_VP, _VP, _I]),
+    "mrhs_nn_get_grads": (_I, [_VP, _VP]),
+    "mrhs_nn_zero_grads": (_I, [_VP]),
+    "mrhs_nn_forward": (_I, [_VP, _VP, _VP, _I]),
+    "mrhs_nn_backward": (_I, [_VP, _VP, _VP, _I]),
+    "mrhs_nn_loss": (_I, [_VP, _VP, _VP, _I, _D, ctypes.POINTER(_D), _VP]),
+    "mrhs_nn_adam": (_I, [_VP, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _I]),
+    "mrhs_nn_train_step": (_I, [_VP, _VP, _I, _D, ctypes.c_float, _I, ctypes.POINTER(_D)]),
+    "mrhs_setup_init_learned": (_I, [_VP, _VP, _I, _I, _I]),
     "mrhs_solve_fgmres": (_I, [_VP, _VP, _VP, _D, _I, _I, _D, _I, _I, _I, _I, _VP, _VP]),
 }
 
@@ -273,6 +285,68 @@ def mrhs_profile_read(ctx):
         out[name.value.decode()] = (n.value, ms.value)
         i += 1
     return out
+
+
+def mrhs_nn_create(ctx, widths, bf16_weights=1):
+    return _check(ctx, lib().mrhs_nn_create(ctx, _i4(widths), int(bf16_weights)))
+
+
+def mrhs_nn_num_params(ctx):
+    a, b = ctypes.c_longlong(0), ctypes.c_longlong(0)
+    _check(ctx, lib().mrhs_nn_num_params(ctx, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def mrhs_nn_set_weights(ctx, host):
+    return _check(ctx, lib().mrhs_nn_set_weights(ctx, _ptr(np.ascontiguousarray(host, dtype=np.float32))))
+
+
+def mrhs_nn_get_weights(ctx, compute_copy=0):
+    nc, nr = mrhs_nn_num_params(ctx)
+    out = np.zeros(2 * nc + nr, np.float32)
+    _check(ctx, lib().mrhs_nn_get_weights(ctx, _ptr(out), int(compute_copy)))
+    return out
+
+
+def mrhs_nn_get_grads(ctx):
+    nc, nr = mrhs_nn_num_params(ctx)
+    out = np.zeros(2 * nc + nr, np.float32)
+    _check(ctx, lib().mrhs_nn_get_grads(ctx, _ptr(out)))
+    return out
+
+
+def mrhs_nn_zero_grads(ctx):
+    return _check(ctx, lib().mrhs_nn_zero_grads(ctx))
+
+
+def mrhs_nn_forward(ctx, x, y, nrhs):
+    return _check(ctx, lib().mrhs_nn_forward(ctx, _ptr(x), _ptr(y), int(nrhs)))
+
+
+def mrhs_nn_backward(ctx, gout, gin, nrhs):
+    return _check(ctx, lib().mrhs_nn_backward(ctx, _ptr(gout), _ptr(gin), int(nrhs)))
+
+
+def mrhs_nn_loss(ctx, v, gv, nrhs, lam):
+    loss = ctypes.c_double(0)
+    per = np.zeros(int(nrhs), np.float64)
+    _check(ctx, lib().mrhs_nn_loss(ctx, _ptr(v), _ptr(gv), int(nrhs), float(lam), ctypes.byref(loss), _ptr(per)))
+    return loss.value, per
+
+
+def mrhs_nn_adam(ctx, lr, beta1, beta2, eps, step):
+    return _check(ctx, lib().mrhs_nn_adam(ctx, float(lr), float(beta1), float(beta2), float(eps), int(step)))
+
+
+def mrhs_nn_train_step(ctx, v_in, nrhs, lam, lr, step):
+    loss = ctypes.c_double(0)
+    _check(ctx, lib().mrhs_nn_train_step(ctx, _ptr(v_in), int(nrhs), float(lam), float(lr), int(step),
+                                         ctypes.byref(loss)))
+    return loss.value
+
+
+def mrhs_setup_init_learned(ctx, tv0, dtype, n_sweeps, n_mr):
+    return _check(ctx, lib().mrhs_setup_init_learned(ctx, _ptr(tv0), int(dtype), int(n_sweeps), int(n_mr)))
 
 
 def mrhs_solve_fgmres(ctx, b, x, tol, restart, maxit, coarse_tol, coarse_restart, coarse_maxit, n_sweeps, n_mr,

@@ -159,6 +159,8 @@ struct Geometry {
   int V, Va, nagg;
 };
 
+struct NNState;  // nn.cu
+
 }  // namespace mrhs
 
 struct mrhs_ctx_s {
@@ -206,6 +208,8 @@ struct mrhs_ctx_s {
 
   // named scratch buffers, grown on demand
   mrhs::DevBuf scratch[16];
+
+  mrhs::NNState* nn = nullptr;  // learned test-vector generator (nn.cu)
 
   // per-kernel CUDA-event timing (off unless enabled through mrhs_profile)
   bool prof = false;
@@ -292,6 +296,10 @@ struct Prof {
   Prof(mrhs_ctx ctx, const char* name);
   ~Prof();
 };
+
+// nn.cu
+void nn_forward(mrhs_ctx c, const float* in, float* out, int N);
+void nn_destroy(mrhs_ctx c);
 
 // every extern "C" entry point runs its body through this guard
 std::string& create_error_slot();

@@ -555,6 +555,7 @@ void mrhs_destroy(mrhs_ctx c) {
   if (c->hflag) cudaFreeHost(c->hflag);
   if (c->hbuf) cudaFreeHost(c->hbuf);
   for (cudaEvent_t e : c->prof_events) cudaEventDestroy(e);
+  if (c->nn) nn_destroy(c);
   delete c;
 }
 

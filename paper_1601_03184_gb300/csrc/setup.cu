@@ -42,6 +42,34 @@ void setup_init(mrhs_ctx c, const void* tv0, int dtype, int init_mode, int n_swe
   build_Dc(c);
 }
 
+// learned initial phase: x = SAP^n_sweeps(b = v, x0 = 0), v <- net(x),
+// normalised, then P and D_c
+void setup_init_learned(mrhs_ctx c, const void* tv0, int dtype, int n_sweeps, int n_mr) {
+  MRHS_REQUIRE(c->have_clover, MRHS_ERR_STATE, "mrhs_setup_init_learned before mrhs_build_clover");
+  MRHS_REQUIRE(c->nn, MRHS_ERR_STATE, "mrhs_setup_init_learned before mrhs_nn_create");
+  MRHS_REQUIRE(c->work_dtype == MRHS_F32, MRHS_ERR_ARG, "the learned initial phase runs on FP32 work fields");
+  MRHS_REQUIRE(n_sweeps >= 0 && n_mr >= 0, MRHS_ERR_ARG, "bad smoother parameters");
+  const int N = c->ntv;
+  const size_t n = fine_elems(c, N);
+  if (!c->tv) c->tv = dalloc(c, n * dtype_size(c->tv_dtype));
+  void* x = scratch(c, SC_X, n * sizeof(float));
+  void* y = scratch(c, SC_R, n * sizeof(float));
+  convert(c, tv0, dtype, y, MRHS_F32, n);
+  if (n_sweeps > 0) {
+    MRHS_CUDA(cudaMemsetAsync(x, 0, n * sizeof(float), c->stream));
+    sap_mixed(c, y, MRHS_F32, x, N, MRHS_F32, n_sweeps, n_mr);
+  } else {
+    MRHS_CUDA(cudaMemcpyAsync(x, y, n * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+  }
+  nn_forward(c, (const float*)x, (float*)y, N);
+  normalise_rhs(c, y, (size_t)c->g.V * 12, N, MRHS_F32);
+  c->tv_scale = c->tv_dtype == MRHS_F16 ? std::sqrt(12.0 * c->g.V) : 1.0;
+  convert_scaled(c, y, MRHS_F32, c->tv, c->tv_dtype, n, (float)c->tv_scale);
+  c->have_tv = true;
+  build_P(c);
+  build_Dc(c);
+}
+
 void setup_refine(mrhs_ctx c, int n_iter, int n_sweeps, int n_mr, double ctol, int crestart, int cmaxit,
                   int* coarse_iters) {
   MRHS_REQUIRE(c->have_Dc, MRHS_ERR_STATE, "mrhs_setup_refine before mrhs_setup_init");
@@ -225,6 +253,13 @@ int mrhs_setup_init(mrhs_ctx c, const void* tv0, int dtype, int init_mode, int n
   return guarded(c, [&] {
     MRHS_REQUIRE(c && tv0, MRHS_ERR_ARG, "null argument");
     setup_init(c, tv0, dtype, init_mode, n_sweeps, n_mr);
+  });
+}
+
+int mrhs_setup_init_learned(mrhs_ctx c, const void* tv0, int dtype, int n_sweeps, int n_mr) {
+  return guarded(c, [&] {
+    MRHS_REQUIRE(c && tv0, MRHS_ERR_ARG, "null argument");
+    setup_init_learned(c, tv0, dtype, n_sweeps, n_mr);
   });
 }
 
