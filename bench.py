@@ -37,11 +37,14 @@ METRIC = "MRHS setup wall time (s) at Ntv; stencil HBM GB/s % peak; learned/mixe
 # workloads: lattice, aggregate (= Schwarz domain), N_tv, roughness, csw, seeds, setup schedule
 CONFIGS = {
     "48x48x48x96_ntv32": dict(dims=(48, 48, 48, 96), agg=(4, 4, 4, 4), ntv=32, eps=0.6, csw=1.7, gseed=1005,
-                              tvseed=2005, m0_key="c5proxy_16x16x16x32_eps0.6_csw1.7_seed1005"),
+                              tvseed=2005, m0_keys=["c5proxy_16x16x16x32_eps0.6_csw1.7_seed1005",
+                                                    "proxy_12x12x12x12_eps0.6_csw1.7_seed1005"]),
     "32x32x32x64_ntv24": dict(dims=(32, 32, 32, 64), agg=(4, 4, 4, 4), ntv=24, eps=0.6, csw=1.5, gseed=1003,
-                              tvseed=2003, m0_key="c3_32x32x32x64_eps0.6_csw1.5_seed1003"),
+                              tvseed=2003, m0_keys=["c3_32x32x32x64_eps0.6_csw1.5_seed1003",
+                                                    "proxy_12x12x12x12_eps0.6_csw1.5_seed1002"]),
     "16x16x16x32_ntv20": dict(dims=(16, 16, 16, 32), agg=(4, 4, 4, 4), ntv=20, eps=0.6, csw=1.5, gseed=1002,
-                              tvseed=2002, m0_key="c2_16x16x16x32_eps0.6_csw1.5_seed1002"),
+                              tvseed=2002, m0_keys=["c2_16x16x16x32_eps0.6_csw1.5_seed1002",
+                                                    "proxy_12x12x12x12_eps0.6_csw1.5_seed1002"]),
 }
 DEFAULT_CONFIG = "48x48x48x96_ntv32"
 SCHEDULE = dict(init_sweeps=5, init_mr=4, n_refine=3, smooth_sweeps=4, smooth_mr=4, coarse_tol=0.05,
@@ -51,12 +54,15 @@ M0_FALLBACK = -0.45
 CPU_SAMPLE_DIMS = (8, 8, 8, 8)
 
 
-def load_m0(key):
+def load_m0(keys):
+    """m0 from tests/golden/m0.json (written by tests/golden/tune_m0.py from the
+    oracle), first key present wins."""
     p = os.path.join(ROOT, "tests", "golden", "m0.json")
     if os.path.exists(p):
         d = json.load(open(p))
-        if key in d:
-            return float(d[key]["m0"]), "tuned"
+        for key in keys:
+            if key in d:
+                return float(d[key]["m0"]), "tuned: " + key
     return M0_FALLBACK, "fallback"
 
 
@@ -428,7 +434,7 @@ def main():
         world = 1
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     cfg = CONFIGS[args.config]
-    m0, m0_src = load_m0(cfg["m0_key"])
+    m0, m0_src = load_m0(cfg["m0_keys"])
     if args.impl == "reference":
         run_reference(args, cfg, args.config, m0, m0_src, rank, world)
     else:

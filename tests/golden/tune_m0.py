@@ -29,6 +29,10 @@ CASES = {
     "c2_16x16x16x32_eps0.6_csw1.5_seed1002": ((16, 16, 16, 32), 0.6, 1.5, 1002),
     "c3_32x32x32x64_eps0.6_csw1.5_seed1003": ((32, 32, 32, 64), 0.6, 1.5, 1003),
     "c5proxy_16x16x16x32_eps0.6_csw1.7_seed1005": ((16, 16, 16, 32), 0.6, 1.7, 1005),
+    # small-volume proxies (same roughness and c_sw), used while the full-size
+    # solves above are not available
+    "proxy_12x12x12x12_eps0.6_csw1.5_seed1002": ((12, 12, 12, 12), 0.6, 1.5, 1002),
+    "proxy_12x12x12x12_eps0.6_csw1.7_seed1005": ((12, 12, 12, 12), 0.6, 1.7, 1005),
 }
 RATIO = 1e-3
 
@@ -64,9 +68,9 @@ def tune(dims, eps, csw, seed):
 
 if __name__ == "__main__":
     names = sys.argv[1:] or list(CASES)
-    res = json.load(open(OUT)) if os.path.exists(OUT) else {}
     for nm in names:
         r = tune(*CASES[nm])
+        res = json.load(open(OUT)) if os.path.exists(OUT) else {}
         res[nm] = r
         print(nm, json.dumps(r), flush=True)
         json.dump(res, open(OUT, "w"), indent=1, sort_keys=True)
