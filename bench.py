@@ -341,6 +341,11 @@ def run_ours(args, cfg, cfg_name, m0, m0_src, rank, world, local_rank):
     if not args.no_e2e:
         e2e = run_e2e(args, lat, U, tv0, cfg, m0, stream)
 
+    # ---- the judge of the plain setup: two-level FGMRES to 1e-10
+    fg_plain = None
+    if not args.no_fgmres:
+        pkg.mrhs_trim(lat.ctx)
+        fg_plain = fgmres_judge(lat, cfg)
     gpu_launches = int(sum(v[0] for v in prof.values()) / args.steps)
     line = {
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -362,11 +367,99 @@ def run_ours(args, cfg, cfg_name, m0, m0_src, rank, world, local_rank):
     if rank == 0 and not args.no_cpu_baseline:
         dt, scaled, threads, desc = cpu_sample(cfg, m0)
         line["cpu_baseline"] = {"value": scaled, "unit": "s", "cores": threads, "kind": "oracle", "sample": desc}
+    line["fgmres_plain"] = fg_plain
+    # ---- learned + mixed-precision setup, wall-time ratio against the plain one
+    if not args.no_learned:
+        lat.close()
+        del tv0
+        torch.cuda.empty_cache()
+        line["learned_mixed"] = run_learned_mixed(args, cfg, U, m0, stream, ms, barrier)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    lat.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def fgmres_judge(lat, cfg, seed=3005):
+    """Two-level FGMRES (FP64 outer, restart 10) on a Gaussian right-hand side to
+    relative residual 1e-10 with the context's current setup."""
+    b = None
+    from paper_1601_03184_gb300 import inputs
+
+    b = inputs.gaussian_field((lat.V, 12), seed)
+    t0 = time.perf_counter()
+    x, it, rr = lat.solve_fgmres(b, tol=1e-10, restart=10, maxit=300, coarse_tol=SCHEDULE["coarse_tol"],
+                                 coarse_restart=SCHEDULE["coarse_restart"], coarse_maxit=SCHEDULE["coarse_maxit"],
+                                 n_sweeps=SCHEDULE["smooth_sweeps"], n_mr=SCHEDULE["smooth_mr"], allow_noconv=True)
+    return {"iterations": int(it), "relres": float(rr), "seconds": round(time.perf_counter() - t0, 2),
+            "tol": 1e-10, "restart": 10}
+
+
+def run_learned_mixed(args, cfg, U, m0, stream, plain_ms, barrier):
+    """Train the network on small seeded lattices of the same roughness and
+    csw (16^4, 8 fields x 50 Adam steps on 8 vectors), then time the learned
+    initial phase (1 SAP sweep + network) and the refinement with bf16 test
+    vectors on the benchmark lattice."""
+    import torch
+
+    import paper_1601_03184_gb300 as pkg
+    from paper_1601_03184_gb300 import (MRHS_F32, MRHS_PREC_FP32, MRHS_PREC_MIX_BF16, Lattice, inputs, learned)
+
+    t0 = time.perf_counter()
+    small = Lattice((16, 16, 16, 16), cfg["agg"], 8, MRHS_PREC_FP32, stream.cuda_stream)
+    learned.attach(small, learned.WIDTHS, seed=17, noise=0.01, bf16=True)
+    sched = dict(init_sweeps=SCHEDULE["init_sweeps"], init_mr=SCHEDULE["init_mr"], n_refine=1,
+                 sweeps=SCHEDULE["smooth_sweeps"], mr=SCHEDULE["smooth_mr"], ctol=SCHEDULE["coarse_tol"],
+                 crestart=SCHEDULE["coarse_restart"], cmaxit=SCHEDULE["coarse_maxit"])
+    step = 1
+    losses = []
+    for f in range(8):
+        small.set_gauge(inputs.gauge_field((16, 16, 16, 16), cfg["eps"], 6000 + f, device="cuda"))
+        small.build_clover(m0, cfg["csw"])
+        ls = learned.train_on_field(small, sched, 50, seed=6100 + f, lr=3e-3, first_step=step)
+        step += len(ls)
+        losses += ls
+    weights = pkg.mrhs_nn_get_weights(small.ctx, 0)
+    small.close()
+    train_s = time.perf_counter() - t0
+    dims, N = cfg["dims"], cfg["ntv"]
+    lat = Lattice(dims, cfg["agg"], N, MRHS_PREC_MIX_BF16, stream.cuda_stream)
+    lat.set_gauge(U)
+    lat.build_clover(m0, cfg["csw"])
+    pkg.mrhs_nn_create(lat.ctx, learned.WIDTHS, 1)
+    pkg.mrhs_nn_set_weights(lat.ctx, weights)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(cfg["tvseed"])
+    tv0 = torch.randn(pkg.mrhs_field_bytes(lat.ctx, N, MRHS_F32) // 4, generator=gen, device="cuda",
+                      dtype=torch.float32)
+
+    def step_fn():
+        pkg.mrhs_setup_init_learned(lat.ctx, tv0, MRHS_F32, 1, SCHEDULE["init_mr"])
+        lat.setup_refine(SCHEDULE["n_refine"], SCHEDULE["smooth_sweeps"], SCHEDULE["smooth_mr"],
+                         SCHEDULE["coarse_tol"], SCHEDULE["coarse_restart"], SCHEDULE["coarse_maxit"])
+
+    for _ in range(args.warmup):
+        step_fn()
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step_fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    lm_ms = e0.elapsed_time(e1) / args.steps
+    fg = None
+    if not args.no_fgmres:
+        pkg.mrhs_trim(lat.ctx)
+        fg = fgmres_judge(lat, cfg)
+    lat.close()
+    return {"value": lm_ms / 1000.0, "unit": "s", "ratio_vs_plain": lm_ms / plain_ms,
+            "form": "1 SAP sweep + network (widths %s, bf16 weights) for the initial phase, bf16 test vectors and P, "
+                    "FP32 smoother and D_c, then the same refinement" % (list(learned.WIDTHS),),
+            "training": {"lattice": [16, 16, 16, 16], "fields": 8, "steps": step - 1, "loss_first": losses[0],
+                         "loss_last": losses[-1], "seconds": round(train_s, 1)},
+            "fgmres": fg}
 
 
 def run_e2e(args, lat, U, tv0, cfg, m0, stream):
@@ -427,6 +520,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fgmres", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", args.gpus if args.gpus else 1))

@@ -89,6 +89,11 @@ int mrhs_sync(mrhs_ctx ctx);
  * the library, number of SMs, 0 */
 int mrhs_info(mrhs_ctx ctx, long long out[8]);
 
+/* release the context's scratch buffers (work fields, Krylov bases, staging);
+ * they are allocated again when a later call needs them. The setup state
+ * (test vectors, P, D_c, gauge field, clover) is kept. */
+int mrhs_trim(mrhs_ctx ctx);
+
 /* bytes of a device field of nrhs right-hand sides (coarse != 0: coarse
  * field) in storage type dtype */
 size_t mrhs_field_bytes(mrhs_ctx ctx, int nrhs, int dtype, int coarse);

@@ -37,6 +37,7 @@ _SIGS = {
     "mrhs_last_error": (ctypes.c_char_p, [_VP]),
     "mrhs_sync": (_I, [_VP]),
     "mrhs_info": (_I, [_VP, ctypes.POINTER(ctypes.c_longlong)]),
+    "mrhs_trim": (_I, [_VP]),
     "mrhs_field_bytes": (ctypes.c_size_t, [_VP, _I, _I, _I]),
     "mrhs_get_tables": (_I, [_VP, _VP, _VP, _VP]),
     "mrhs_set_gauge": (_I, [_VP, _VP]),
@@ -152,6 +153,10 @@ def mrhs_last_error(ctx):
 
 def mrhs_sync(ctx):
     return _check(ctx, lib().mrhs_sync(ctx))
+
+
+def mrhs_trim(ctx):
+    return _check(ctx, lib().mrhs_trim(ctx))
 
 
 def mrhs_info(ctx):

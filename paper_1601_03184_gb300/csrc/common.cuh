@@ -299,6 +299,7 @@ struct Prof {
 
 // nn.cu
 void nn_forward(mrhs_ctx c, const float* in, float* out, int N);
+void nn_infer(mrhs_ctx c, const float* in, float* out, int N);
 void nn_destroy(mrhs_ctx c);
 
 // every extern "C" entry point runs its body through this guard

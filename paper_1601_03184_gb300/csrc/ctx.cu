@@ -568,6 +568,20 @@ int mrhs_sync(mrhs_ctx c) {
   });
 }
 
+int mrhs_trim(mrhs_ctx c) {
+  return guarded(c, [&] {
+    MRHS_REQUIRE(c, MRHS_ERR_ARG, "null context");
+    MRHS_CUDA(cudaStreamSynchronize(c->stream));
+    for (auto& b : c->scratch)
+      if (b.p) {
+        MRHS_CUDA(cudaFree(b.p));
+        c->held_bytes -= b.bytes;
+        b.p = nullptr;
+        b.bytes = 0;
+      }
+  });
+}
+
 int mrhs_info(mrhs_ctx c, long long out[8]) {
   return guarded(c, [&] {
     MRHS_REQUIRE(c && out, MRHS_ERR_ARG, "null argument");

@@ -315,7 +315,7 @@ static int stencil_passes(int N, int G) {
     const char* e = getenv("MRHS_STENCIL_PASSES");
     return e ? atoi(e) : 0;
   }();
-  int p = forced > 0 ? forced : (N >= 16 ? 2 : 1);
+  int p = forced > 0 ? forced : 1;
   while (p > 1 && (N % p != 0 || (N / p) % G != 0)) --p;
   return p;
 }
@@ -395,7 +395,7 @@ void block_mr_t(mrhs_ctx c, S* x, S* rho, S* q, int N, const int* blist, int nbl
 }  // namespace
 
 // right-hand sides per thread of the FP32 stencil: MRHS_STENCIL_VEC = 1 (one
-// per thread), 2 or 4; default 4 when nrhs % 4 == 0, else 2 when even
+// per thread), 2 or 4; default 2 when nrhs is even (measured fastest)
 static int stencil_vec_width() {
   static int w = [] {
     const char* e = getenv("MRHS_STENCIL_VEC");
@@ -410,7 +410,7 @@ void dslash(mrhs_ctx c, const void* x, void* y, const void* b, int nrhs, int dty
   MRHS_REQUIRE(nrhs >= 1, MRHS_ERR_ARG, "nrhs must be >= 1");
   const int vw = stencil_vec_width();
   if (dtype == MRHS_F32 && mode == DS_FULL && colour < 0 && c->U20 && nrhs % 2 == 0 && vw != 1) {
-    int G = (nrhs % 4 == 0 && vw != 2) ? 4 : 2;
+    int G = (nrhs % 4 == 0 && vw == 4) ? 4 : 2;
     Prof pr(c, "dslash_full");
     if (G == 4) dslash_vec<4>(c, (const float*)x, (float*)y, nrhs);
     else dslash_vec<2>(c, (const float*)x, (float*)y, nrhs);

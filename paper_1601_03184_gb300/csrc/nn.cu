@@ -351,6 +351,22 @@ __global__ void k_gamma5(const float* x, float* y, int N, size_t nwork) {
   y[t] = ((row % 12) < 6) ? x[t] : -x[t];
 }
 
+// y (N_y = nr right-hand sides) <- x (right-hand sides r0 .. r0+nr-1 of N_x)
+__global__ void k_gather_rhs(const float* x, int Nx, int r0, float* y, int nr, size_t rows) {
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= rows * 2 * nr) return;
+  const int r = (int)(t % nr);
+  const size_t q = t / nr;  // row*2 + reim
+  y[t] = x[q * Nx + r0 + r];
+}
+__global__ void k_scatter_rhs(const float* y, int nr, float* x, int Nx, int r0, size_t rows) {
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= rows * 2 * nr) return;
+  const int r = (int)(t % nr);
+  const size_t q = t / nr;
+  x[q * Nx + r0 + r] = y[t];
+}
+
 __global__ void k_sub(const float* a, const float* b, float* c, size_t n) {
   const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (t < n) c[t] = a[t] - b[t];
@@ -513,8 +529,39 @@ void refresh_compute_weights(mrhs_ctx c, NNState& s) {
 
 }  // namespace
 
+// inference only (no activations kept): right-hand sides in chunks, two
+// ping-pong buffers for the hidden layers
+void nn_infer_chunked(mrhs_ctx c, const float* in, float* out, int N, int chunk) {
+  NNState& s = nn_of(c);
+  const size_t V = c->g.V;
+  const int hid = std::max(s.C[1], s.C[2]);
+  const int cs = std::min(N, chunk);
+  float* a = (float*)scratch(c, SC_FINE1, sizeof(float) * V * hid * 6 * cs);
+  float* b = (float*)scratch(c, SC_FINE2, sizeof(float) * V * hid * 6 * cs);
+  float* io = (float*)scratch(c, SC_FINE3, sizeof(float) * V * 24 * cs * 2);
+  float* xin = io;
+  float* xout = io + V * 24 * cs;
+  const float* bias = s.Wc + 2 * s.nw;
+  for (int r0 = 0; r0 < N; r0 += cs) {
+    const int nr = std::min(cs, N - r0);
+    k_gather_rhs<<<grid_for(V * 12 * 2 * nr, 256), 256, 0, c->stream>>>(in, N, r0, xin, nr, V * 12);
+    MRHS_LAUNCH_CHECK("gather_rhs");
+    covconv(c, xin, a, s.Wc + 2 * layer_off(s, 0), s.C[0], s.C[1], nr);
+    k_modrelu<<<grid_for(V * s.C[1] * nr, 256), 256, 0, c->stream>>>(a, a, bias, s.C[1], nr, V * s.C[1] * nr);
+    MRHS_LAUNCH_CHECK("modrelu");
+    covconv(c, a, b, s.Wc + 2 * layer_off(s, 1), s.C[1], s.C[2], nr);
+    k_modrelu<<<grid_for(V * s.C[2] * nr, 256), 256, 0, c->stream>>>(b, b, bias + s.C[1], s.C[2], nr,
+                                                                     V * s.C[2] * nr);
+    MRHS_LAUNCH_CHECK("modrelu");
+    covconv(c, b, xout, s.Wc + 2 * layer_off(s, 2), s.C[2], s.C[3], nr);
+    k_scatter_rhs<<<grid_for(V * 12 * 2 * nr, 256), 256, 0, c->stream>>>(xout, nr, out, N, r0, V * 12);
+    MRHS_LAUNCH_CHECK("scatter_rhs");
+  }
+}
+
 namespace mrhs {
 void nn_forward(mrhs_ctx c, const float* in, float* out, int N) { nn_forward_impl(c, in, out, N); }
+void nn_infer(mrhs_ctx c, const float* in, float* out, int N) { nn_infer_chunked(c, in, out, N, 4); }
 }  // namespace mrhs
 
 using namespace mrhs;

@@ -61,7 +61,7 @@ void setup_init_learned(mrhs_ctx c, const void* tv0, int dtype, int n_sweeps, in
   } else {
     MRHS_CUDA(cudaMemcpyAsync(x, y, n * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
   }
-  nn_forward(c, (const float*)x, (float*)y, N);
+  nn_infer(c, (const float*)x, (float*)y, N);
   normalise_rhs(c, y, (size_t)c->g.V * 12, N, MRHS_F32);
   c->tv_scale = c->tv_dtype == MRHS_F16 ? std::sqrt(12.0 * c->g.V) : 1.0;
   convert_scaled(c, y, MRHS_F32, c->tv, c->tv_dtype, n, (float)c->tv_scale);

@@ -12,7 +12,9 @@ import numpy as np
 from . import (MRHS_F32, mrhs_nn_create, mrhs_nn_num_params, mrhs_nn_set_weights, mrhs_nn_train_step,
                mrhs_sap, mrhs_setup_init, mrhs_setup_init_learned, mrhs_setup_refine)
 
-WIDTHS = (4, 32, 32, 4)
+# 4 -> 11 -> 11 -> 4 colour triplets: 12 -> 33 -> 33 -> 12 complex channels
+# per site, the gauge-covariant width closest to 32 complex channels
+WIDTHS = (4, 11, 11, 4)
 
 
 def initial_weights(widths=WIDTHS, seed=7, noise=0.01):
