@@ -142,7 +142,7 @@ def kernel_work(name, cfg, launches_per_step, bytes_f=4):
         return V * (link4 + clov + 2 * N * spin), V * N * flop_site_rhs
     if name == "dslash_resid":  # one colour: r = b - D x on half of the sites
         return V / 2 * (link4 + clov + 3 * N * spin), V / 2 * N * flop_site_rhs
-    if name in ("sap_fused8", "sap_fused"):  # one colour: residual + n_mr MR steps, on chip
+    if name in ("sap_tm", "sap_fused8", "sap_fused"):  # one colour: residual + n_mr MR steps, on chip
         nmr = SCHEDULE["smooth_mr"]
         flops = V / 2 * N * (flop_site_rhs + nmr * (flop_site_rhs + 336))
         byt = V / 2 * (link4 + clov + 3 * N * spin)  # b in, x in and out, links and clover once
@@ -152,7 +152,13 @@ def kernel_work(name, cfg, launches_per_step, bytes_f=4):
         flops = V / 2 * N * nmr * (flop_site_rhs + 4 * 96)
         byt = V / 2 * (link4 + clov + 3 * N * spin)  # x, rho in and out once, links once
         return byt, flops
-    if name == "coarse_op":  # P read once, U, A once, D_c written once
+    if name == "apply_dc_tc" or name == "apply_dc":  # D_c read once, x_c of 9 neighbours (L2), y_c written
+        nagg = V // Va
+        nc = 2 * N
+        byt = nagg * (9 * nc * nc * 2 * bytes_f + 2 * nc * 2 * N * bytes_f)
+        fl = nagg * 9 * nc * nc * 8 * N
+        return byt, fl
+    if name in ("coarse_op", "coarse_op_tc"):  # P read once, U, A once, D_c written once
         nagg = V // Va
         nc = 2 * N
         byt = V * (N * spin + link4 + clov) + nagg * 9 * nc * nc * 2 * bytes_f

@@ -58,7 +58,7 @@ typedef enum {
   MRHS_ERR_NOCONV = -5,    /* an iterative solve hit maxit before its tolerance */
   MRHS_ERR_NONFINITE = -6, /* NaN/Inf or a linearly dependent test vector */
   MRHS_ERR_STATE = -7,     /* call made before the state it needs exists */
-  MRHS_ERR_TIMEOUT = -8    /* reserved: a bounded device wait ran out */
+  MRHS_ERR_TIMEOUT = -8    /* a bounded device wait (tensor-core pipeline) ran out */
 } mrhs_status;
 
 /* storage type of a field (device) or of a host array */
@@ -83,7 +83,8 @@ typedef enum { MRHS_PREC_FP64 = 0, MRHS_PREC_FP32 = 1, MRHS_PREC_MIX_BF16 = 2, M
 int mrhs_create(const int dims[4], const int agg[4], int ntv, int prec, void* stream, mrhs_ctx* out);
 void mrhs_destroy(mrhs_ctx ctx);
 const char* mrhs_last_error(mrhs_ctx ctx);
-/* wait for all work of the context's stream */
+/* wait for all work of the context's stream; MRHS_ERR_TIMEOUT if a bounded
+ * wait of a tensor-core coarse-stencil launch ran out since the last check */
 int mrhs_sync(mrhs_ctx ctx);
 /* out[0..7] = V, nagg, sites per aggregate, ntv, prec, device bytes held by
  * the library, number of SMs, 0 */
@@ -178,6 +179,25 @@ int mrhs_build_P(mrhs_ctx ctx);
  * A+mu == A-mu). MRHS_ERR_STATE before mrhs_build_P. */
 int mrhs_build_Dc(mrhs_ctx ctx);
 
+/* Engine of the contraction P^dag (D P) inside mrhs_build_Dc (the dense
+ * 2ntv x 2ntv coarse-link products). AUTO: FP32/FP64 CUDA cores for the
+ * FP64 and FP32 contexts; tensor cores (tcgen05, FP32 accumulation) for the
+ * mixed contexts: bf16 operands for MIX_BF16, tf32 for MIX_FP16. ALU: always
+ * the CUDA cores. TC_BF16 / TC_F16 / TC_TF32: the tensor cores with that
+ * operand type (P and D P rounded to it). The tensor-core forms need FP32
+ * work fields (prec FP32 or mixed) and 2*ntv <= 64; mrhs_build_Dc returns
+ * MRHS_ERR_SHAPE otherwise, MRHS_ERR_TIMEOUT if a bounded wait of the
+ * tensor-core pipeline ran out. The backward blocks always follow from
+ * gamma_5-hermiticity. */
+typedef enum {
+  MRHS_DC_AUTO = 0,
+  MRHS_DC_ALU = 1,
+  MRHS_DC_TC_BF16 = 2,
+  MRHS_DC_TC_F16 = 3,
+  MRHS_DC_TC_TF32 = 4
+} mrhs_dc_engine;
+int mrhs_set_dc_engine(mrhs_ctx ctx, int engine);
+
 /* restriction vc = R v = P^dag v (Algorithm 3 of the paper, all nrhs at
  * once): vc[A][h*ntv+j] = sum_{x in A, c in h} conj(P_j(x,c)) v(x,c).
  * v: fine device field, vc: coarse device field, both of storage dtype
@@ -186,7 +206,11 @@ int mrhs_restrict(mrhs_ctx ctx, const void* v, void* vc, int nrhs, int dtype);
 /* prolongation u = P uc (Sec. 2, Algorithm 1) */
 int mrhs_prolong(mrhs_ctx ctx, const void* uc, void* u, int nrhs, int dtype);
 /* yc = D_c xc on nrhs coarse right-hand sides (Sec. 5: D_c applied with the
- * same broadcast scheme as the restriction) */
+ * same broadcast scheme as the restriction). With F32 coarse fields, nrhs a
+ * multiple of 16 up to 64, 2*ntv a multiple of 8 up to 64 and an engine other
+ * than MRHS_DC_ALU the products run on the tensor cores (tcgen05, FP32
+ * accumulation): split tf32 (hi*hi + hi*lo + lo*hi, FP32 accuracy) for FP32
+ * contexts, single tf32 for the mixed ones; otherwise on the CUDA cores. */
 int mrhs_apply_Dc(mrhs_ctx ctx, const void* xc, void* yc, int nrhs, int dtype);
 
 /* Coarse solve "to low accuracy" (Algorithm 1/2, tolerance 0.05 in Sec. 6):

@@ -24,6 +24,7 @@ MRHS_ERR_ARG, MRHS_ERR_SHAPE, MRHS_ERR_OOM, MRHS_ERR_CUDA = -1, -2, -3, -4
 MRHS_ERR_NOCONV, MRHS_ERR_NONFINITE, MRHS_ERR_STATE, MRHS_ERR_TIMEOUT = -5, -6, -7, -8
 MRHS_F64, MRHS_F32, MRHS_BF16, MRHS_F16 = 0, 1, 2, 3
 MRHS_PREC_FP64, MRHS_PREC_FP32, MRHS_PREC_MIX_BF16, MRHS_PREC_MIX_FP16 = 0, 1, 2, 3
+MRHS_DC_AUTO, MRHS_DC_ALU, MRHS_DC_TC_BF16, MRHS_DC_TC_F16, MRHS_DC_TC_TF32 = 0, 1, 2, 3, 4
 
 _VP = ctypes.c_void_p
 _I = ctypes.c_int
@@ -53,6 +54,7 @@ _SIGS = {
     "mrhs_set_tv": (_I, [_VP, _VP, _I]),
     "mrhs_build_P": (_I, [_VP]),
     "mrhs_build_Dc": (_I, [_VP]),
+    "mrhs_set_dc_engine": (_I, [_VP, _I]),
     "mrhs_restrict": (_I, [_VP, _VP, _VP, _I, _I]),
     "mrhs_prolong": (_I, [_VP, _VP, _VP, _I, _I]),
     "mrhs_apply_Dc": (_I, [_VP, _VP, _VP, _I, _I]),
@@ -223,6 +225,10 @@ def mrhs_build_P(ctx):
 
 def mrhs_build_Dc(ctx):
     return _check(ctx, lib().mrhs_build_Dc(ctx))
+
+
+def mrhs_set_dc_engine(ctx, engine):
+    return _check(ctx, lib().mrhs_set_dc_engine(ctx, engine))
 
 
 def mrhs_restrict(ctx, v, vc, nrhs, dtype):

@@ -19,47 +19,62 @@ int n_chunks(size_t rows, int N) {
   return (int)ch;
 }
 
-// partial[k][chunk][r] = sum over the chunk's rows of conj(X_k) * Y
+// partial[k][chunk][r] = sum over the chunk's rows of conj(X_k) * Y, for the
+// group of up to kKG vectors k = kKG*blockIdx.y + j: every element of Y read
+// serves the whole group
+constexpr int kKG = 8;
+
 template <class S>
-__global__ void k_multi_dot(const S* X, size_t stride, const S* Y, size_t rows, int N, int nchunk, double* part) {
+__global__ void __launch_bounds__(kBlock) k_multi_dot(const S* X, size_t stride, int K, const S* Y, size_t rows, int N,
+                                                      int nchunk, double* part) {
   using R = typename Real<S>::type;
   __shared__ double sre[kBlock], sim[kBlock];
-  const int k = blockIdx.y, ch = blockIdx.x;
+  const int k0 = blockIdx.y * kKG, ch = blockIdx.x;
+  const int nk = min(kKG, K - k0);
   const size_t r0 = rows * ch / nchunk, r1 = rows * (ch + 1) / nchunk;
-  const S* Xk = X + (size_t)k * stride;
   const int lanes = blockDim.x / N;
   const int tid = threadIdx.x, r = tid % N, lane = tid / N;
-  double are = 0, aim = 0;
+  double are[kKG], aim[kKG];
+  R pre[kKG], pim[kKG];
+#pragma unroll
+  for (int j = 0; j < kKG; ++j) are[j] = aim[j] = 0, pre[j] = pim[j] = 0;
   if (lane < lanes) {
-    R pre = 0, pim = 0;
     int cnt = 0;
     for (size_t row = r0 + lane; row < r1; row += lanes) {
-      R xr = to_r(Xk[fidx(row, 0, N, r)]), xi = to_r(Xk[fidx(row, 1, N, r)]);
-      R yr = to_r(Y[fidx(row, 0, N, r)]), yi = to_r(Y[fidx(row, 1, N, r)]);
-      pre = fma(xr, yr, fma(xi, yi, pre));
-      pim = fma(xr, yi, fma(-xi, yr, pim));
+      const R yr = to_r(Y[fidx(row, 0, N, r)]), yi = to_r(Y[fidx(row, 1, N, r)]);
+#pragma unroll
+      for (int j = 0; j < kKG; ++j) {
+        if (j < nk) {
+          const S* Xk = X + (size_t)(k0 + j) * stride;
+          const R xr = to_r(Xk[fidx(row, 0, N, r)]), xi = to_r(Xk[fidx(row, 1, N, r)]);
+          pre[j] = fma(xr, yr, fma(xi, yi, pre[j]));
+          pim[j] = fma(xr, yi, fma(-xi, yr, pim[j]));
+        }
+      }
       if (++cnt == 32) {
-        are += pre;
-        aim += pim;
-        pre = pim = 0;
+#pragma unroll
+        for (int j = 0; j < kKG; ++j) are[j] += pre[j], aim[j] += pim[j], pre[j] = pim[j] = 0;
         cnt = 0;
       }
     }
-    are += pre;
-    aim += pim;
+#pragma unroll
+    for (int j = 0; j < kKG; ++j) are[j] += pre[j], aim[j] += pim[j];
   }
-  sre[tid] = are;
-  sim[tid] = aim;
-  __syncthreads();
-  if (tid < N) {
-    double a = 0, b = 0;
-    for (int l = 0; l < lanes; ++l) {
-      a += sre[l * N + tid];
-      b += sim[l * N + tid];
+  for (int j = 0; j < nk; ++j) {
+    sre[tid] = are[j];
+    sim[tid] = aim[j];
+    __syncthreads();
+    if (tid < N) {
+      double a = 0, b = 0;
+      for (int l = 0; l < lanes; ++l) {
+        a += sre[l * N + tid];
+        b += sim[l * N + tid];
+      }
+      double* o = part + (((size_t)(k0 + j) * nchunk + ch) * N + tid) * 2;
+      o[0] = a;
+      o[1] = b;
     }
-    double* o = part + (((size_t)k * nchunk + ch) * N + tid) * 2;
-    o[0] = a;
-    o[1] = b;
+    __syncthreads();
   }
 }
 
@@ -129,9 +144,9 @@ void multi_dot(mrhs_ctx c, const void* X, size_t stride, int K, const void* Y, s
   MRHS_REQUIRE(N >= 1 && N <= kBlock && K >= 1, MRHS_ERR_ARG, "multi_dot: bad sizes");
   int nch = n_chunks(rows, N);
   double* part = (double*)scratch(c, SC_RED, sizeof(double) * 2 * (size_t)K * nch * N);
-  dim3 grid(nch, K);
+  dim3 grid(nch, (K + kKG - 1) / kKG);
   Prof pr(c, "multi_dot");
-  MRHS_DISPATCH(dtype, S, (k_multi_dot<S><<<grid, kBlock, 0, c->stream>>>((const S*)X, stride, (const S*)Y, rows, N, nch, part)));
+  MRHS_DISPATCH(dtype, S, (k_multi_dot<S><<<grid, kBlock, 0, c->stream>>>((const S*)X, stride, K, (const S*)Y, rows, N, nch, part)));
   MRHS_LAUNCH_CHECK("multi_dot");
   k_sum_chunks<<<grid_for((size_t)K * N, 128), 128, 0, c->stream>>>(part, K, nch, N, out);
   MRHS_LAUNCH_CHECK("sum_chunks");
@@ -147,9 +162,9 @@ void multi_dot_ws(mrhs_ctx c, const void* X, size_t stride, int K, const void* Y
                   double* out, double* part) {
   MRHS_REQUIRE(N >= 1 && N <= kBlock && K >= 1, MRHS_ERR_ARG, "multi_dot: bad sizes");
   int nch = n_chunks(rows, N);
-  dim3 grid(nch, K);
+  dim3 grid(nch, (K + kKG - 1) / kKG);
   Prof pr(c, "multi_dot");
-  MRHS_DISPATCH(dtype, S, (k_multi_dot<S><<<grid, kBlock, 0, c->stream>>>((const S*)X, stride, (const S*)Y, rows, N, nch, part)));
+  MRHS_DISPATCH(dtype, S, (k_multi_dot<S><<<grid, kBlock, 0, c->stream>>>((const S*)X, stride, K, (const S*)Y, rows, N, nch, part)));
   MRHS_LAUNCH_CHECK("multi_dot");
   k_sum_chunks<<<grid_for((size_t)K * N, 128), 128, 0, c->stream>>>(part, K, nch, N, out);
   MRHS_LAUNCH_CHECK("sum_chunks");

@@ -1,53 +1,12 @@
 // Coarse grid: D_c = P^dag D P assembly, restriction R = P^dag (Algorithm 3
 // of the paper, all right-hand sides at once), prolongation, the coarse
 // 9-point stencil and the multi-RHS coarse GMRES.
-#include "stencil.cuh"
+#include "coarse_common.cuh"
 
 namespace mrhs {
 namespace {
 
 constexpr int kSites = 8;  // sites staged per chunk in the contractions
-
-struct Agg4 {
-  int a[4];
-};
-
-// local site index of face site f of an aggregate: l_mu fixed to lmu, the
-// other three coordinates enumerated lexicographically
-__device__ __forceinline__ int face_site(const Agg4& g, int mu, int lmu, int f) {
-  int l[4];
-  for (int m = 0; m < 4; ++m) {
-    if (m == mu) {
-      l[m] = lmu;
-    } else {
-      l[m] = f % g.a[m];
-      f /= g.a[m];
-    }
-  }
-  return l[0] + g.a[0] * (l[1] + g.a[1] * (l[2] + g.a[2] * l[3]));
-}
-
-// column col = (h', j) of P: P_j restricted to chirality h', at site n
-template <class SP, class R>
-__device__ __forceinline__ void load_pcol(cx<R> psi[12], const SP* P, int n, int Nt, int col) {
-  const int hp = col / Nt, j = col % Nt;
-#pragma unroll
-  for (int c = 0; c < 12; ++c)
-    psi[c] = (c / 6 == hp) ? ld<SP, R>(P, (size_t)n * 12 + c, Nt, j) : mk<R>(0, 0);
-}
-
-template <int MU, class SP, class R>
-__device__ __forceinline__ void hop_pcol(cx<R> out[12], const SP* P, const cx<R>* U, const int* nbr, int s, int dir,
-                                         int Nt, int col, bool only_same_block, int Va) {
-  int e = nbr[s * 8 + (dir > 0 ? 0 : 4) + MU];
-  int n = e & 0x3fffffff;
-  if (only_same_block && n / Va != s / Va) return;
-  R sg = (e & 0x40000000) ? (R)-1 : (R)1;
-  cx<R> psi[12];
-  load_pcol<SP, R>(psi, P, n, Nt, col);
-  if (dir > 0) hop_reg<MU, +1, R>(out, psi, U + (size_t)s * 36 + MU * 9, sg);
-  else hop_reg<MU, -1, R>(out, psi, U + (size_t)n * 36 + MU * 9, sg);
-}
 
 // One CTA per (aggregate A, stencil entry k). Columns (h', j), rows (h, i):
 //   k = 0:      sum_{x in A} P_(h,i)(x)^dag [A(x) + hops inside A] P_(h',j)
@@ -599,6 +558,27 @@ void build_Dc(mrhs_ctx c) {
   Agg4 ag;
   for (int m = 0; m < 4; ++m) ag.a[m] = c->g.a[m];
   const bool tiled = Nt % 4 == 0 && nc <= 64;
+  // tensor-core contraction: chosen explicitly, or by default for the mixed setups
+  int fmt = -1;
+  switch (c->dc_engine) {
+    case MRHS_DC_TC_BF16: fmt = tc_fmt_bf16; break;
+    case MRHS_DC_TC_F16: fmt = tc_fmt_f16; break;
+    case MRHS_DC_TC_TF32: fmt = tc_fmt_tf32; break;
+    case MRHS_DC_AUTO:
+      if (c->prec == MRHS_PREC_MIX_BF16) fmt = tc_fmt_bf16;
+      if (c->prec == MRHS_PREC_MIX_FP16) fmt = tc_fmt_tf32;
+      break;
+    default: break;
+  }
+  if (fmt >= 0 && build_Dc_tc(c, fmt)) {
+    size_t tot = (size_t)c->g.nagg * 4 * nc * nc;
+    k_coarse_backward<float><<<grid_for(tot, 256), 256, 0, c->stream>>>((cx<float>*)c->Dc, c->aggnbr, c->g.nagg, Nt);
+    MRHS_LAUNCH_CHECK("coarse_backward");
+    c->have_Dc = true;
+    return;
+  }
+  MRHS_REQUIRE(c->dc_engine == MRHS_DC_AUTO || c->dc_engine == MRHS_DC_ALU, MRHS_ERR_SHAPE,
+               "tensor-core D_c contraction needs FP32 work fields and 2*ntv <= 64");
   Prof pr(c, "coarse_op");
   MRHS_DISPATCH(c->tv_dtype, SP, {
     using R = typename Real<SP>::type;
@@ -693,6 +673,12 @@ void apply_Dc(mrhs_ctx c, const void* xc, void* yc, int nrhs, int dtype) {
   MRHS_REQUIRE(c->have_Dc, MRHS_ERR_STATE, "D_c used before mrhs_build_Dc");
   MRHS_REQUIRE(dtype == c->work_dtype, MRHS_ERR_ARG, "D_c apply: dtype must be the context's work type");
   const int nc = 2 * c->ntv;
+  // tensor cores unless the CUDA-core engine is chosen: split tf32 (FP32
+  // accuracy) for the FP32 setup, single tf32 for the mixed ones
+  if (c->dc_engine != MRHS_DC_ALU && dtype == MRHS_F32) {
+    const bool split = c->prec == MRHS_PREC_FP32;
+    if (apply_Dc_tc(c, xc, yc, nrhs, split)) return;
+  }
   Prof pr(c, "apply_dc");
   if (nc % 8 == 0) {
     size_t work = (size_t)c->g.nagg * (nc / 8) * nrhs;
@@ -790,6 +776,7 @@ void coarse_solve(mrhs_ctx c, const void* bc, void* xc, int N, int dtype, double
     MRHS_CUDA(cudaMemcpyAsync(iters, st.its, sizeof(int) * N, cudaMemcpyDeviceToHost, c->stream));
     MRHS_CUDA(cudaStreamSynchronize(c->stream));
   }
+  check_tc_timeout(c);
 }
 
 // ------------------------------------------------------------------------
@@ -905,6 +892,7 @@ void coarse_solve_ws(mrhs_ctx c, const void* bc, void* xc, int N, int dtype, dou
     MRHS_CUDA(cudaMemcpyAsync(iters, st.its, sizeof(int) * N, cudaMemcpyDeviceToHost, c->stream));
     MRHS_CUDA(cudaStreamSynchronize(c->stream));
   }
+  check_tc_timeout(c);
 }
 
 }  // namespace mrhs
@@ -917,6 +905,14 @@ int mrhs_build_Dc(mrhs_ctx c) {
   return guarded(c, [&] {
     MRHS_REQUIRE(c, MRHS_ERR_ARG, "null context");
     build_Dc(c);
+  });
+}
+
+int mrhs_set_dc_engine(mrhs_ctx c, int engine) {
+  return guarded(c, [&] {
+    MRHS_REQUIRE(c, MRHS_ERR_ARG, "null context");
+    MRHS_REQUIRE(engine >= MRHS_DC_AUTO && engine <= MRHS_DC_TC_TF32, MRHS_ERR_ARG, "unknown D_c engine");
+    c->dc_engine = engine;
   });
 }
 

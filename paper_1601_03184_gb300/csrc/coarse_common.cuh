@@ -1,0 +1,49 @@
+// Helpers shared by the coarse-operator kernels (ALU and tensor-core forms):
+// aggregate face enumeration and the hop of one column of P.
+#pragma once
+#include "stencil.cuh"
+
+namespace mrhs {
+
+struct Agg4 {
+  int a[4];
+};
+
+// local site index of face site f of an aggregate: l_mu fixed to lmu, the
+// other three coordinates enumerated lexicographically
+static __device__ __forceinline__ int face_site(const Agg4& g, int mu, int lmu, int f) {
+  int l[4];
+  for (int m = 0; m < 4; ++m) {
+    if (m == mu) {
+      l[m] = lmu;
+    } else {
+      l[m] = f % g.a[m];
+      f /= g.a[m];
+    }
+  }
+  return l[0] + g.a[0] * (l[1] + g.a[1] * (l[2] + g.a[2] * l[3]));
+}
+
+// column col = (h', j) of P: P_j restricted to chirality h', at site n
+template <class SP, class R>
+static __device__ __forceinline__ void load_pcol(cx<R> psi[12], const SP* P, int n, int Nt, int col) {
+  const int hp = col / Nt, j = col % Nt;
+#pragma unroll
+  for (int c = 0; c < 12; ++c)
+    psi[c] = (c / 6 == hp) ? ld<SP, R>(P, (size_t)n * 12 + c, Nt, j) : mk<R>(0, 0);
+}
+
+template <int MU, class SP, class R>
+static __device__ __forceinline__ void hop_pcol(cx<R> out[12], const SP* P, const cx<R>* U, const int* nbr, int s, int dir,
+                                         int Nt, int col, bool only_same_block, int Va) {
+  int e = nbr[s * 8 + (dir > 0 ? 0 : 4) + MU];
+  int n = e & 0x3fffffff;
+  if (only_same_block && n / Va != s / Va) return;
+  R sg = (e & 0x40000000) ? (R)-1 : (R)1;
+  cx<R> psi[12];
+  load_pcol<SP, R>(psi, P, n, Nt, col);
+  if (dir > 0) hop_reg<MU, +1, R>(out, psi, U + (size_t)s * 36 + MU * 9, sg);
+  else hop_reg<MU, -1, R>(out, psi, U + (size_t)n * 36 + MU * 9, sg);
+}
+
+}  // namespace mrhs

@@ -166,6 +166,7 @@ struct NNState;  // nn.cu
 struct mrhs_ctx_s {
   mrhs::Geometry g;
   int ntv = 0, prec = 0;
+  int dc_engine = 0;    // mrhs_dc_engine
   int tv_dtype = 0;     // storage of test vectors and P
   int work_dtype = 0;   // storage/compute of smoother work fields, D_c, coarse fields (F64 or F32)
   cudaStream_t stream = nullptr;
@@ -261,6 +262,12 @@ void sap(mrhs_ctx c, const void* b, void* x, int nrhs, int dtype, int n_sweeps, 
 void build_P(mrhs_ctx c);
 // coarse.cu
 void build_Dc(mrhs_ctx c);
+// operand formats of the tensor-core contraction (tcgen05 instruction-descriptor codes)
+constexpr int tc_fmt_f16 = 0, tc_fmt_bf16 = 1, tc_fmt_tf32 = 2;
+bool build_Dc_tc(mrhs_ctx c, int fmt);
+// coarse stencil on the tensor cores; sets dflag[3] if a pipeline wait ran out
+bool apply_Dc_tc(mrhs_ctx c, const void* xc, void* yc, int nrhs, bool split);
+void check_tc_timeout(mrhs_ctx c);
 void restrict_(mrhs_ctx c, const void* v, void* vc, int nrhs, int dtype);
 void prolong(mrhs_ctx c, const void* uc, void* u, int nrhs, int dtype);
 void apply_Dc(mrhs_ctx c, const void* xc, void* yc, int nrhs, int dtype);
@@ -277,6 +284,8 @@ void sap_mixed(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int dty
 // sap.cu: the on-chip SAP (FP32 work fields)
 bool sap_fused_ok(mrhs_ctx c, int dtype);
 void sap_fused(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int n_sweeps, int n_mr);
+bool sap_tm_ok(mrhs_ctx c, int nrhs);
+void sap_tm(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int n_sweeps, int n_mr);
 // blas.cu: y[row][r] += sign * sum_k coef[k][r] * X_k[row][r], X_k = X + k*stride elements
 void multi_axpy(mrhs_ctx c, const void* X, size_t stride, int K, void* Y, size_t rows, int N, int dtype,
                 const double* coef /* device [K][N][2] */, double sign);

@@ -565,6 +565,7 @@ int mrhs_sync(mrhs_ctx c) {
   return guarded(c, [&] {
     MRHS_REQUIRE(c, MRHS_ERR_ARG, "null context");
     MRHS_CUDA(cudaStreamSynchronize(c->stream));
+    check_tc_timeout(c);
   });
 }
 

@@ -12,6 +12,8 @@
 //      x += alpha rho, rho -= alpha q,
 //   4. x is written back.
 // Only b and x of the colour's sites (and the face neighbours of x) touch HBM.
+#include <cstdlib>
+
 #include "stencil.cuh"
 
 namespace mrhs {
@@ -501,6 +503,16 @@ bool sap_fused_ok(mrhs_ctx c, int dtype) {
 }
 
 void sap_fused(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int n_sweeps, int n_mr) {
+  // the on-chip form (tensor memory for the running solution) unless
+  // MRHS_SAP_KERNEL=smem asks for the shared-memory/global forms below
+  static const bool tm_off = [] {
+    const char* e = std::getenv("MRHS_SAP_KERNEL");
+    return e && std::string(e) == "smem";
+  }();
+  if (!tm_off && sap_tm_ok(c, nrhs)) {
+    sap_tm(c, b, bdtype, x, nrhs, n_sweeps, n_mr);
+    return;
+  }
   const bool g8 = nrhs % kG8 == 0 &&
                   sizeof(float) * ((size_t)24 * c->g.Va * kG8 + 1024) <= (size_t)[&] {
                     int m = 0;

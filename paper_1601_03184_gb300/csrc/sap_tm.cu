@@ -1,0 +1,437 @@
+// SAP sweep (Sec. 3.1 of the paper; red-black multiplicative Schwarz with
+// minimal-residual block solves) with the whole state of a domain on chip.
+//
+// One CTA per domain of the colour, right-hand sides in chunks of four. Per
+// chunk:
+//   shared memory  rho [24][Va][4] (the block residual of the MR iteration)
+//                  and the domain's links (1/2) sgn U [4][5][Va+1] float4,
+//                  staged once per CTA;
+//   tensor memory  the running solution x_B = x0 + sum_k alpha_k rho_k of the
+//                  thread's own items (tcgen05.st / tcgen05.ld, 24 columns per
+//                  item), so x is read once and written once per chunk;
+//   registers      q = D_B rho of the thread's items between the reduction
+//                  for alpha and the update.
+// Items (site l, rhs g) = 4*l + g; thread t owns items t and t + T (T threads).
+// Per colour: r = b - D x on the domain (neighbours outside it from x in
+// global memory, which the other colour owns and nobody writes during the
+// launch), then n_mr MR steps e += alpha rho, rho -= alpha q with
+// alpha = <q, rho> / <q, q>, then x_B += e.
+#include "stencil.cuh"
+#include "tc.cuh"
+
+namespace mrhs {
+namespace {
+
+constexpr int kG = 4;            // right-hand sides per chunk
+constexpr int kMaxT = 512;       // threads for a 256-site domain
+constexpr int kColsItem = 24;    // tensor-memory columns per item
+
+// one hop for one right-hand side: pr/pi the neighbour spinor, u the halved
+// link (9 complex, row-major, sign of the time boundary folded in)
+template <int MU, int DIR>
+__device__ __forceinline__ void hop1(float ore[12], float oim[12], const float pr[12], const float pi[12],
+                                     const float u[18]) {
+  float hre[2][3], him[2][3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    cx<float> p2 = mk(pr[6 + c], pi[6 + c]), p3 = mk(pr[9 + c], pi[9 + c]);
+    cx<float> b0, b1;
+    b_low<MU>(p2, p3, b0, b1);
+    cx<float> h0 = DIR > 0 ? mk(pr[c], pi[c]) - b0 : mk(pr[c], pi[c]) + b0;
+    cx<float> h1 = DIR > 0 ? mk(pr[3 + c], pi[3 + c]) - b1 : mk(pr[3 + c], pi[3 + c]) + b1;
+    hre[0][c] = h0.re;
+    him[0][c] = h0.im;
+    hre[1][c] = h1.re;
+    him[1][c] = h1.im;
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    cx<float> ch[2];
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp) {
+      cx<float> acc = mk(0.f, 0.f);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        cx<float> hv = mk(hre[sp][b], him[sp][b]);
+        if (DIR > 0) fma_(acc, mk(u[2 * (a * 3 + b)], u[2 * (a * 3 + b) + 1]), hv);
+        else fmac_(acc, mk(u[2 * (b * 3 + a)], u[2 * (b * 3 + a) + 1]), hv);
+      }
+      ch[sp] = acc;
+    }
+    cx<float> l0, l1;
+    bdag<MU>(ch[0], ch[1], l0, l1);
+    ore[a] -= ch[0].re;
+    oim[a] -= ch[0].im;
+    ore[3 + a] -= ch[1].re;
+    oim[3 + a] -= ch[1].im;
+    if (DIR > 0) {
+      ore[6 + a] += l0.re;
+      oim[6 + a] += l0.im;
+      ore[9 + a] += l1.re;
+      oim[9 + a] += l1.im;
+    } else {
+      ore[6 + a] -= l0.re;
+      oim[6 + a] -= l0.im;
+      ore[9 + a] -= l1.re;
+      oim[9 + a] -= l1.im;
+    }
+  }
+}
+
+struct Dom {
+  const float* sR;   // [24][Va][4]
+  const float4* sU;  // [20][Va+1]
+  int Va, l, g;
+  size_t s0;         // first device site of the domain
+};
+
+__device__ __forceinline__ void load_rho(const Dom& d, int n, float pr[12], float pi[12]) {
+#pragma unroll
+  for (int c = 0; c < 12; ++c) {
+    pr[c] = d.sR[((2 * c) * d.Va + n) * kG + d.g];
+    pi[c] = d.sR[((2 * c + 1) * d.Va + n) * kG + d.g];
+  }
+}
+
+__device__ __forceinline__ void load_u_smem(const Dom& d, int site, int mu, float u[18]) {
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const float4 t = d.sU[(mu * 5 + k) * (d.Va + 1) + site];
+    u[4 * k] = t.x;
+    u[4 * k + 1] = t.y;
+    if (4 * k + 2 < 18) u[4 * k + 2] = t.z;
+    if (4 * k + 3 < 18) u[4 * k + 3] = t.w;
+  }
+}
+
+__device__ __forceinline__ void load_u_glob(const float* __restrict__ U20, size_t site, int mu, float u[18]) {
+  const float4* p = reinterpret_cast<const float4*>(U20 + (site * 4 + mu) * 20);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const float4 t = __ldg(p + k);
+    u[4 * k] = t.x;
+    u[4 * k + 1] = t.y;
+    if (4 * k + 2 < 18) u[4 * k + 2] = t.z;
+    if (4 * k + 3 < 18) u[4 * k + 3] = t.w;
+  }
+}
+
+// hop (MU, DIR) at the item's site: inside the domain from shared memory;
+// outside (RESID only) from x and the links in global memory
+template <int MU, int DIR, bool RESID>
+__device__ __forceinline__ void hop_dom(const Dom& d, float ore[12], float oim[12], const int* __restrict__ nbr,
+                                        const float* __restrict__ x, const float* __restrict__ U20, int N, int r0) {
+  const int e = __ldg(nbr + (d.s0 + d.l) * 8 + (DIR > 0 ? 0 : 4) + MU);
+  const int n = e & 0x3fffffff;
+  const unsigned nl = (unsigned)(n - (int)d.s0);
+  float pr[12], pi[12], u[18];
+  if (nl < (unsigned)d.Va) {
+    load_rho(d, (int)nl, pr, pi);
+    load_u_smem(d, DIR > 0 ? d.l : (int)nl, MU, u);
+  } else {
+    if (!RESID) return;
+    const float* xn = x + (size_t)n * 24 * N + r0 + d.g;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      pr[c] = xn[(2 * c) * N];
+      pi[c] = xn[(2 * c + 1) * N];
+    }
+    if (DIR > 0) load_u_smem(d, d.l, MU, u);
+    else load_u_glob(U20, (size_t)n, MU, u);
+  }
+  hop1<MU, DIR>(ore, oim, pr, pi, u);
+}
+
+// out = D x (RESID) or D_B rho at the item's site
+template <bool RESID>
+__device__ __forceinline__ void apply_dom(const Dom& d, float ore[12], float oim[12], const float* __restrict__ Acl,
+                                          const int* __restrict__ nbr, const float* __restrict__ x,
+                                          const float* __restrict__ U20, int N, int r0) {
+  {
+    float pr[12], pi[12];
+    load_rho(d, d.l, pr, pi);
+    const float4* A4 = reinterpret_cast<const float4*>(Acl + (d.s0 + d.l) * 72);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float q[36];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        const float4 v = __ldg(A4 + 9 * h + k);
+        q[4 * k] = v.x;
+        q[4 * k + 1] = v.y;
+        q[4 * k + 2] = v.z;
+        q[4 * k + 3] = v.w;
+      }
+#pragma unroll
+      for (int a = 0; a < 6; ++a) {
+        cx<float> acc = scale(mk(pr[6 * h + a], pi[6 * h + a]), q[a]);
+#pragma unroll
+        for (int b2 = 0; b2 < 6; ++b2) {
+          if (b2 == a) continue;
+          cx<float> m = b2 > a ? mk(q[herm_idx(a, b2)], q[herm_idx(a, b2) + 1])
+                               : mk(q[herm_idx(b2, a)], -q[herm_idx(b2, a) + 1]);
+          fma_(acc, m, mk(pr[6 * h + b2], pi[6 * h + b2]));
+        }
+        ore[6 * h + a] = acc.re;
+        oim[6 * h + a] = acc.im;
+      }
+    }
+  }
+  hop_dom<0, +1, RESID>(d, ore, oim, nbr, x, U20, N, r0);
+  hop_dom<1, +1, RESID>(d, ore, oim, nbr, x, U20, N, r0);
+  hop_dom<2, +1, RESID>(d, ore, oim, nbr, x, U20, N, r0);
+  hop_dom<3, +1, RESID>(d, ore, oim, nbr, x, U20, N, r0);
+  hop_dom<0, -1, RESID>(d, ore, oim, nbr, x, U20, N, r0);
+  hop_dom<1, -1, RESID>(d, ore, oim, nbr, x, U20, N, r0);
+  hop_dom<2, -1, RESID>(d, ore, oim, nbr, x, U20, N, r0);
+  hop_dom<3, -1, RESID>(d, ore, oim, nbr, x, U20, N, r0);
+}
+
+__device__ __forceinline__ void tm_put(uint32_t ta, const float v[24]) {
+  tc::tmem_st8(ta, v);
+  tc::tmem_st8(ta + 8, v + 8);
+  tc::tmem_st8(ta + 16, v + 16);
+}
+__device__ __forceinline__ void tm_get(uint32_t ta, float v[24]) {
+  tc::tmem_ld8(ta, v);
+  tc::tmem_ld8(ta + 8, v + 8);
+  tc::tmem_ld8(ta + 16, v + 16);
+}
+
+template <class SB>
+__global__ void __launch_bounds__(kMaxT, 1) k_sap_tm(const SB* __restrict__ b, float* __restrict__ x,
+                                                     const float* __restrict__ U20, const float* __restrict__ Acl,
+                                                     const int* __restrict__ nbr, int N, int Va,
+                                                     const int* __restrict__ blist, int n_mr, uint32_t tm_cols) {
+  extern __shared__ float4 smem4[];
+  const int T = blockDim.x;
+  float4* sU = smem4;                                     // [20][Va+1]
+  float* sR = reinterpret_cast<float*>(sU + 20 * (Va + 1));  // [24][Va][4]
+  float* sred = sR + 24 * Va * kG;                        // [T/32][4][3]
+  float* salpha = sred + (T / 32) * kG * 3;               // [4][2]
+  __shared__ uint32_t s_tmem;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nit = kG * Va;
+  Dom d;
+  d.Va = Va;
+  d.g = tid & (kG - 1);
+  d.s0 = (size_t)blist[blockIdx.x] * Va;
+  d.sR = sR;
+  d.sU = sU;
+
+  if (warp == 0) {
+    tc::tmem_alloc(&s_tmem, tm_cols);
+    tc::tmem_relinquish();
+  }
+  {
+    const float4* U4 = reinterpret_cast<const float4*>(U20) + d.s0 * 20;
+    for (int i = tid; i < 20 * Va; i += T) sU[(i % 20) * (Va + 1) + i / 20] = __ldg(U4 + i);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  // lane quarter of the warp; warps w, w+4, w+8, w+12 share it and take
+  // disjoint column ranges
+  const uint32_t tm = s_tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * 2 * kColsItem);
+  const bool v0 = tid < nit, v1 = tid + T < nit;
+
+  for (int r0 = 0; r0 < N; r0 += kG) {
+    // stage x0: shared memory (stencil input) and tensor memory (running solution)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int i = tid + j * T;
+      float v[24];
+      if (i < nit) {
+        const int l = i >> 2;
+        const float* xs = x + (d.s0 + l) * 24 * N + r0 + d.g;
+#pragma unroll
+        for (int k = 0; k < 24; ++k) {
+          v[k] = xs[k * N];
+          sR[(k * Va + l) * kG + d.g] = v[k];
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 24; ++k) v[k] = 0.f;
+      }
+      tm_put(tm + j * kColsItem, v);
+    }
+    tc::tmem_wait_st();
+    __syncthreads();
+    // r = b - D x0 for both items (registers), then rho = r
+    float q0r[12], q0i[12], q1r[12], q1i[12];
+    if (v0) {
+      d.l = tid >> 2;
+      apply_dom<true>(d, q0r, q0i, Acl, nbr, x, U20, N, r0);
+      const SB* bs = b + (d.s0 + d.l) * 24 * N + r0 + d.g;
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        q0r[c] = (float)to_r(bs[(2 * c) * N]) - q0r[c];
+        q0i[c] = (float)to_r(bs[(2 * c + 1) * N]) - q0i[c];
+      }
+    }
+    if (v1) {
+      d.l = (tid + T) >> 2;
+      apply_dom<true>(d, q1r, q1i, Acl, nbr, x, U20, N, r0);
+      const SB* bs = b + (d.s0 + d.l) * 24 * N + r0 + d.g;
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        q1r[c] = (float)to_r(bs[(2 * c) * N]) - q1r[c];
+        q1i[c] = (float)to_r(bs[(2 * c + 1) * N]) - q1i[c];
+      }
+    }
+    __syncthreads();
+    if (v0) {
+      const int l = tid >> 2;
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        sR[((2 * c) * Va + l) * kG + d.g] = q0r[c];
+        sR[((2 * c + 1) * Va + l) * kG + d.g] = q0i[c];
+      }
+    }
+    if (v1) {
+      const int l = (tid + T) >> 2;
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        sR[((2 * c) * Va + l) * kG + d.g] = q1r[c];
+        sR[((2 * c + 1) * Va + l) * kG + d.g] = q1i[c];
+      }
+    }
+    __syncthreads();
+    for (int step = 0; step < n_mr; ++step) {
+      float pr = 0.f, pi = 0.f, pq = 0.f;
+      if (v0) {
+        d.l = tid >> 2;
+        apply_dom<false>(d, q0r, q0i, Acl, nbr, x, U20, N, r0);
+        float rr[12], ri[12];
+        load_rho(d, d.l, rr, ri);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+          pr = fmaf(q0r[c], rr[c], fmaf(q0i[c], ri[c], pr));
+          pi = fmaf(q0r[c], ri[c], fmaf(-q0i[c], rr[c], pi));
+          pq = fmaf(q0r[c], q0r[c], fmaf(q0i[c], q0i[c], pq));
+        }
+      }
+      if (v1) {
+        d.l = (tid + T) >> 2;
+        apply_dom<false>(d, q1r, q1i, Acl, nbr, x, U20, N, r0);
+        float rr[12], ri[12];
+        load_rho(d, d.l, rr, ri);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+          pr = fmaf(q1r[c], rr[c], fmaf(q1i[c], ri[c], pr));
+          pi = fmaf(q1r[c], ri[c], fmaf(-q1i[c], rr[c], pi));
+          pq = fmaf(q1r[c], q1r[c], fmaf(q1i[c], q1i[c], pq));
+        }
+      }
+      // sums over the lanes of the same rhs (lane % 4), then over warps
+#pragma unroll
+      for (int o = kG; o < 32; o <<= 1) {
+        pr += __shfl_xor_sync(0xffffffffu, pr, o);
+        pi += __shfl_xor_sync(0xffffffffu, pi, o);
+        pq += __shfl_xor_sync(0xffffffffu, pq, o);
+      }
+      if (lane < kG) {
+        sred[(warp * kG + lane) * 3 + 0] = pr;
+        sred[(warp * kG + lane) * 3 + 1] = pi;
+        sred[(warp * kG + lane) * 3 + 2] = pq;
+      }
+      __syncthreads();
+      if (tid < kG) {
+        double a = 0, bb = 0, cc = 0;
+        for (int w = 0; w < T / 32; ++w) {
+          a += sred[(w * kG + tid) * 3 + 0];
+          bb += sred[(w * kG + tid) * 3 + 1];
+          cc += sred[(w * kG + tid) * 3 + 2];
+        }
+        salpha[2 * tid] = cc > 0 ? (float)(a / cc) : 0.f;
+        salpha[2 * tid + 1] = cc > 0 ? (float)(bb / cc) : 0.f;
+      }
+      __syncthreads();
+      const cx<float> al = mk(salpha[2 * d.g], salpha[2 * d.g + 1]);
+      // x_B += alpha rho (tensor memory), rho -= alpha q (shared memory)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        float xv[24];
+        tm_get(tm + j * kColsItem, xv);
+        const bool vj = j == 0 ? v0 : v1;
+        if (vj) {
+          const int l = (tid + j * T) >> 2;
+#pragma unroll
+          for (int c = 0; c < 12; ++c) {
+            const int i0 = ((2 * c) * Va + l) * kG + d.g, i1 = ((2 * c + 1) * Va + l) * kG + d.g;
+            cx<float> rv = mk(sR[i0], sR[i1]);
+            cx<float> xc = mk(xv[2 * c], xv[2 * c + 1]);
+            fma_(xc, al, rv);
+            xv[2 * c] = xc.re;
+            xv[2 * c + 1] = xc.im;
+            const cx<float> qv = j == 0 ? mk(-q0r[c], -q0i[c]) : mk(-q1r[c], -q1i[c]);
+            fma_(rv, al, qv);
+            sR[i0] = rv.re;
+            sR[i1] = rv.im;
+          }
+        }
+        tm_put(tm + j * kColsItem, xv);
+      }
+      tc::tmem_wait_st();
+      __syncthreads();
+    }
+    // x = x_B
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      float xv[24];
+      tm_get(tm + j * kColsItem, xv);
+      const int i = tid + j * T;
+      if (i < nit) {
+        float* xs = x + (d.s0 + (i >> 2)) * 24 * N + r0 + d.g;
+#pragma unroll
+        for (int k = 0; k < 24; ++k) xs[k * N] = xv[k];
+      }
+    }
+    __syncthreads();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(s_tmem, tm_cols);
+}
+
+}  // namespace
+
+// threads for a domain of Va sites: four items per site, at most two items
+// per thread, whole warpgroups
+static int sap_tm_threads(int Va) { return 128 * ((kG * Va + 255) / 256); }
+
+static size_t sap_tm_smem(int Va, int T) {
+  return sizeof(float4) * 20 * (size_t)(Va + 1) + sizeof(float) * ((size_t)24 * Va * kG + (T / 32) * kG * 3 + 2 * kG);
+}
+
+bool sap_tm_ok(mrhs_ctx c, int nrhs) {
+  const int Va = c->g.Va;
+  if (nrhs % kG != 0 || Va > 256 || !c->U20) return false;
+  int maxsm = 0;
+  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+  return sap_tm_smem(Va, sap_tm_threads(Va)) <= (size_t)maxsm;
+}
+
+void sap_tm(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int n_sweeps, int n_mr) {
+  const int Va = c->g.Va;
+  const int T = sap_tm_threads(Va);
+  const size_t smem = sap_tm_smem(Va, T);
+  // columns: (T/128) warpgroups x 2 items x 24, rounded up to a power of two >= 32
+  uint32_t cols = 32;
+  while (cols < (uint32_t)(T / 128) * 2 * kColsItem) cols <<= 1;
+  for (int sw = 0; sw < n_sweeps; ++sw)
+    for (int col = 0; col < 2; ++col) {
+      const int* blist = c->blocks_col + (col ? c->ncol[0] : 0);
+      Prof pr(c, "sap_tm");
+      MRHS_DISPATCH(bdtype, SB, {
+        auto kern = k_sap_tm<SB>;
+        MRHS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<c->ncol[col], T, smem, c->stream>>>((const SB*)b, (float*)x, c->U20, c->A32, c->nbr, nrhs, Va, blist,
+                                                   n_mr, cols);
+      });
+      MRHS_LAUNCH_CHECK("sap_tm");
+    }
+}
+
+}  // namespace mrhs

@@ -9,6 +9,7 @@ import numpy as np
 
 from . import (MRHS_F32, MRHS_F64, MRHS_PREC_FP64, mrhs_apply_D, mrhs_apply_D_block, mrhs_apply_Dc,
                mrhs_build_clover, mrhs_build_Dc, mrhs_build_P, mrhs_coarse_solve, mrhs_create, mrhs_destroy,
+               mrhs_set_dc_engine,
                mrhs_field_bytes, mrhs_get_clover, mrhs_get_Dc, mrhs_get_P, mrhs_get_tables, mrhs_get_tv,
                mrhs_info, mrhs_pack, mrhs_pack_coarse, mrhs_prolong, mrhs_restrict, mrhs_sap, mrhs_set_gauge,
                mrhs_set_tv, mrhs_setup_init, mrhs_setup_refine, mrhs_solve_fgmres, mrhs_sync, mrhs_unpack,
@@ -102,6 +103,9 @@ class Lattice:
 
     def build_Dc(self):
         mrhs_build_Dc(self.ctx)
+
+    def set_dc_engine(self, engine):
+        mrhs_set_dc_engine(self.ctx, engine)
 
     def restrict(self, v, vc, nrhs, dtype):
         mrhs_restrict(self.ctx, v, vc, nrhs, dtype)

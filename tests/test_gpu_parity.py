@@ -134,6 +134,24 @@ def test_sap_fp32(c1):
     assert rel(lat32.to_host(xd, nrhs, MRHS_F32), ref) < 1e-5
 
 
+# the paper's 4^4 domains (256 sites: two items per thread in the on-chip
+# SAP kernel) and a ragged 2x3x2x2 domain (24 sites, partial warpgroup), with
+# one and several chunks of four right-hand sides and a nonzero start vector
+P4 = dict(dims=(8, 8, 8, 8), agg=(4, 4, 4, 4), ntv=8, eps=0.4, m0=-0.1, csw=1.2, gseed=1301, tvseed=2301)
+
+
+@pytest.mark.parametrize("cfg,nrhs", [(P4, 4), (P4, 12), (RAGGED, 8)], ids=["4^4-n4", "4^4-n12", "ragged-n8"])
+def test_sap_fp32_domains(cfg, nrhs):
+    lat, U, A = make(cfg, MRHS_PREC_FP32)
+    b = inputs.gaussian_field((nrhs, lat.V, 12), 721)
+    x0 = 0.1 * inputs.gaussian_field((nrhs, lat.V, 12), 722)
+    bd = lat.to_device(b, MRHS_F32)
+    xd = lat.to_device(x0, MRHS_F32)
+    lat.sap(bd, xd, nrhs, MRHS_F32, 2, 4)
+    ref = oracle.sap(cfg["dims"], cfg["agg"], U, A, b, x0, 2, 4)
+    assert rel(lat.to_host(xd, nrhs, MRHS_F32), ref) < 1e-5
+
+
 # ------------------------------------------------------------ GS, Dc, R/P --
 @pytest.mark.parametrize("cfg_name", ["c1", "ragged"])
 def test_gram_schmidt_and_coarse_op_fp64(c1, ragged, cfg_name):
