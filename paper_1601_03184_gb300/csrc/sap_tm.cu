@@ -1,21 +1,25 @@
 // SAP sweep (Sec. 3.1 of the paper; red-black multiplicative Schwarz with
 // minimal-residual block solves) with the whole state of a domain on chip.
 //
-// One CTA per domain of the colour, right-hand sides in chunks of four. Per
-// chunk:
-//   shared memory  rho [24][Va][4] (the block residual of the MR iteration)
-//                  and the domain's links (1/2) sgn U [4][5][Va+1] float4,
-//                  staged once per CTA;
+// Per colour, one CTA per (domain, chunk of G right-hand sides): the CTAs of a
+// domain run side by side, so each 32-byte sector of x and b that they share
+// comes from HBM once. Per chunk:
+//   shared memory  rho [24][Va][G] (the block residual of the MR iteration)
+//                  and the domain's links (1/2) sgn U [4][5][Va+1] float4
+//                  (G = 2 also the clover [18][Va+1] float4 and the
+//                  domain-local neighbour table);
 //   tensor memory  the running solution x_B = x0 + sum_k alpha_k rho_k of the
 //                  thread's own items (tcgen05.st / tcgen05.ld, 24 columns per
 //                  item), so x is read once and written once per chunk;
 //   registers      q = D_B rho of the thread's items between the reduction
 //                  for alpha and the update.
-// Items (site l, rhs g) = 4*l + g; thread t owns items t and t + T (T threads).
-// Per colour: r = b - D x on the domain (neighbours outside it from x in
-// global memory, which the other colour owns and nobody writes during the
-// launch), then n_mr MR steps e += alpha rho, rho -= alpha q with
-// alpha = <q, rho> / <q, q>, then x_B += e.
+// Items (site l, rhs g) = G*l + g. Per colour: r = b - D x on the domain
+// (neighbours outside it from x in global memory, which the other colour owns
+// and nobody writes during the launch), then n_mr MR steps e += alpha rho,
+// rho -= alpha q with alpha = <q, rho> / <q, q>, then x_B += e.
+#include <algorithm>
+#include <cstdlib>
+
 #include "stencil.cuh"
 #include "tc.cuh"
 
@@ -202,7 +206,8 @@ template <class SB>
 __global__ void __launch_bounds__(kMaxT, 1) k_sap_tm(const SB* __restrict__ b, float* __restrict__ x,
                                                      const float* __restrict__ U20, const float* __restrict__ Acl,
                                                      const int* __restrict__ nbr, int N, int Va,
-                                                     const int* __restrict__ blist, int n_mr, uint32_t tm_cols) {
+                                                     const int* __restrict__ blist, int n_mr, uint32_t tm_cols,
+                                                     int cpb) {
   extern __shared__ float4 smem4[];
   const int T = blockDim.x;
   float4* sU = smem4;                                     // [20][Va+1]
@@ -216,7 +221,7 @@ __global__ void __launch_bounds__(kMaxT, 1) k_sap_tm(const SB* __restrict__ b, f
   Dom d;
   d.Va = Va;
   d.g = tid & (kG - 1);
-  d.s0 = (size_t)blist[blockIdx.x] * Va;
+  d.s0 = (size_t)blist[blockIdx.x / cpb] * Va;
   d.sR = sR;
   d.sU = sU;
 
@@ -236,7 +241,7 @@ __global__ void __launch_bounds__(kMaxT, 1) k_sap_tm(const SB* __restrict__ b, f
   const uint32_t tm = s_tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * 2 * kColsItem);
   const bool v0 = tid < nit, v1 = tid + T < nit;
 
-  for (int r0 = 0; r0 < N; r0 += kG) {
+  for (int r0 = (blockIdx.x % cpb) * kG; r0 < N; r0 += cpb * kG) {
     // stage x0: shared memory (stencil input) and tensor memory (running solution)
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
@@ -395,40 +400,333 @@ __global__ void __launch_bounds__(kMaxT, 1) k_sap_tm(const SB* __restrict__ b, f
   if (warp == 0) tc::tmem_dealloc(s_tmem, tm_cols);
 }
 
+// ---------------------------------------------------------------------------
+// Two right-hand sides per chunk, every operand of the MR steps on chip:
+// shared memory holds rho [24][Va][2], the halved links [20][Va+1] float4,
+// the clover [18][Va+1] float4 and the domain-local neighbour table [8][Va]
+// (-1 outside the domain); tensor memory the running solution (24 columns
+// per thread); one item (site l = t/2, rhs g = t%2) per thread, q in
+// registers. Only the residual reads global memory inside the chunk (b and
+// the neighbours outside the domain).
+constexpr int kG2 = 2;
+
+struct Dom2 {
+  const float* sR;   // [24][Va][2]
+  const float4* sU;  // [20][Va+1]
+  const float4* sA;  // [18][Va+1]
+  const int* sN;     // [8][Va]
+  int Va, l, g;
+  size_t s0;
+};
+
+__device__ __forceinline__ void load_rho2(const Dom2& d, int n, float pr[12], float pi[12]) {
+#pragma unroll
+  for (int c = 0; c < 12; ++c) {
+    pr[c] = d.sR[((2 * c) * d.Va + n) * kG2 + d.g];
+    pi[c] = d.sR[((2 * c + 1) * d.Va + n) * kG2 + d.g];
+  }
+}
+
+__device__ __forceinline__ void load_u2(const Dom2& d, int site, int mu, float u[18]) {
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const float4 t = d.sU[(mu * 5 + k) * (d.Va + 1) + site];
+    u[4 * k] = t.x;
+    u[4 * k + 1] = t.y;
+    if (4 * k + 2 < 18) u[4 * k + 2] = t.z;
+    if (4 * k + 3 < 18) u[4 * k + 3] = t.w;
+  }
+}
+
+template <int MU, int DIR, bool RESID>
+__device__ __forceinline__ void hop_dom2(const Dom2& d, float ore[12], float oim[12], const int* __restrict__ nbr,
+                                         const float* __restrict__ x, const float* __restrict__ U20, int N, int r0) {
+  const int nl = d.sN[((DIR > 0 ? 0 : 4) + MU) * d.Va + d.l];
+  float pr[12], pi[12], u[18];
+  if (nl >= 0) {
+    load_rho2(d, nl, pr, pi);
+    load_u2(d, DIR > 0 ? d.l : nl, MU, u);
+  } else {
+    if (!RESID) return;
+    const int n = __ldg(nbr + (d.s0 + d.l) * 8 + (DIR > 0 ? 0 : 4) + MU) & 0x3fffffff;
+    const float* xn = x + (size_t)n * 24 * N + r0 + d.g;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      pr[c] = xn[(2 * c) * N];
+      pi[c] = xn[(2 * c + 1) * N];
+    }
+    if (DIR > 0) load_u2(d, d.l, MU, u);
+    else load_u_glob(U20, (size_t)n, MU, u);
+  }
+  hop1<MU, DIR>(ore, oim, pr, pi, u);
+}
+
+template <bool RESID>
+__device__ __forceinline__ void apply_dom2(const Dom2& d, float ore[12], float oim[12], const int* __restrict__ nbr,
+                                           const float* __restrict__ x, const float* __restrict__ U20, int N, int r0) {
+  {
+    float pr[12], pi[12];
+    load_rho2(d, d.l, pr, pi);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float q[36];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        const float4 v = d.sA[(9 * h + k) * (d.Va + 1) + d.l];
+        q[4 * k] = v.x;
+        q[4 * k + 1] = v.y;
+        q[4 * k + 2] = v.z;
+        q[4 * k + 3] = v.w;
+      }
+#pragma unroll
+      for (int a = 0; a < 6; ++a) {
+        cx<float> acc = scale(mk(pr[6 * h + a], pi[6 * h + a]), q[a]);
+#pragma unroll
+        for (int b2 = 0; b2 < 6; ++b2) {
+          if (b2 == a) continue;
+          cx<float> m = b2 > a ? mk(q[herm_idx(a, b2)], q[herm_idx(a, b2) + 1])
+                               : mk(q[herm_idx(b2, a)], -q[herm_idx(b2, a) + 1]);
+          fma_(acc, m, mk(pr[6 * h + b2], pi[6 * h + b2]));
+        }
+        ore[6 * h + a] = acc.re;
+        oim[6 * h + a] = acc.im;
+      }
+    }
+  }
+  hop_dom2<0, +1, RESID>(d, ore, oim, nbr, x, U20, N, r0);
+  hop_dom2<1, +1, RESID>(d, ore, oim, nbr, x, U20, N, r0);
+  hop_dom2<2, +1, RESID>(d, ore, oim, nbr, x, U20, N, r0);
+  hop_dom2<3, +1, RESID>(d, ore, oim, nbr, x, U20, N, r0);
+  hop_dom2<0, -1, RESID>(d, ore, oim, nbr, x, U20, N, r0);
+  hop_dom2<1, -1, RESID>(d, ore, oim, nbr, x, U20, N, r0);
+  hop_dom2<2, -1, RESID>(d, ore, oim, nbr, x, U20, N, r0);
+  hop_dom2<3, -1, RESID>(d, ore, oim, nbr, x, U20, N, r0);
+}
+
+template <class SB>
+__global__ void __launch_bounds__(kMaxT, 1) k_sap_tm2(const SB* __restrict__ b, float* __restrict__ x,
+                                                      const float* __restrict__ U20, const float* __restrict__ Acl,
+                                                      const int* __restrict__ nbr, int N, int Va,
+                                                      const int* __restrict__ blist, int n_mr, uint32_t tm_cols,
+                                                      int cpb) {
+  extern __shared__ float4 smem4[];
+  const int T = blockDim.x;
+  float4* sU = smem4;                                      // [20][Va+1]
+  float4* sA = sU + 20 * (Va + 1);                         // [18][Va+1]
+  int* sN = reinterpret_cast<int*>(sA + 18 * (Va + 1));    // [8][Va]
+  float* sR = reinterpret_cast<float*>(sN + 8 * Va);       // [24][Va][2]
+  float* sred = sR + 24 * Va * kG2;                        // [T/32][2][3]
+  float* salpha = sred + (T / 32) * kG2 * 3;               // [2][2]
+  __shared__ uint32_t s_tmem;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool valid = tid < kG2 * Va;
+  Dom2 d;
+  d.Va = Va;
+  d.g = tid & 1;
+  d.l = valid ? tid >> 1 : 0;
+  d.s0 = (size_t)blist[blockIdx.x / cpb] * Va;
+  d.sR = sR;
+  d.sU = sU;
+  d.sA = sA;
+  d.sN = sN;
+
+  if (warp == 0) {
+    tc::tmem_alloc(&s_tmem, tm_cols);
+    tc::tmem_relinquish();
+  }
+  {
+    const float4* U4 = reinterpret_cast<const float4*>(U20) + d.s0 * 20;
+    for (int i = tid; i < 20 * Va; i += T) sU[(i % 20) * (Va + 1) + i / 20] = __ldg(U4 + i);
+    const float4* A4 = reinterpret_cast<const float4*>(Acl) + d.s0 * 18;
+    for (int i = tid; i < 18 * Va; i += T) sA[(i % 18) * (Va + 1) + i / 18] = __ldg(A4 + i);
+    for (int i = tid; i < 8 * Va; i += T) {
+      const int l = i >> 3, k = i & 7;
+      const int n = (__ldg(nbr + (d.s0 + l) * 8 + k) & 0x3fffffff) - (int)d.s0;
+      sN[k * Va + l] = (n >= 0 && n < Va) ? n : -1;
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tm = s_tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * kColsItem);
+
+  for (int r0 = (blockIdx.x % cpb) * kG2; r0 < N; r0 += cpb * kG2) {
+    {
+      float v[24];
+      if (valid) {
+        const float* xs = x + (d.s0 + d.l) * 24 * N + r0 + d.g;
+#pragma unroll
+        for (int k = 0; k < 24; ++k) {
+          v[k] = xs[k * N];
+          sR[(k * Va + d.l) * kG2 + d.g] = v[k];
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 24; ++k) v[k] = 0.f;
+      }
+      tm_put(tm, v);
+    }
+    tc::tmem_wait_st();
+    __syncthreads();
+    float qr[12], qi[12];
+    if (valid) {
+      apply_dom2<true>(d, qr, qi, nbr, x, U20, N, r0);
+      const SB* bs = b + (d.s0 + d.l) * 24 * N + r0 + d.g;
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        qr[c] = (float)to_r(bs[(2 * c) * N]) - qr[c];
+        qi[c] = (float)to_r(bs[(2 * c + 1) * N]) - qi[c];
+      }
+    }
+    __syncthreads();
+    if (valid) {
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        sR[((2 * c) * Va + d.l) * kG2 + d.g] = qr[c];
+        sR[((2 * c + 1) * Va + d.l) * kG2 + d.g] = qi[c];
+      }
+    }
+    __syncthreads();
+    for (int step = 0; step < n_mr; ++step) {
+      float pr = 0.f, pi = 0.f, pq = 0.f;
+      if (valid) {
+        apply_dom2<false>(d, qr, qi, nbr, x, U20, N, r0);
+        float rr[12], ri[12];
+        load_rho2(d, d.l, rr, ri);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+          pr = fmaf(qr[c], rr[c], fmaf(qi[c], ri[c], pr));
+          pi = fmaf(qr[c], ri[c], fmaf(-qi[c], rr[c], pi));
+          pq = fmaf(qr[c], qr[c], fmaf(qi[c], qi[c], pq));
+        }
+      }
+#pragma unroll
+      for (int o = kG2; o < 32; o <<= 1) {
+        pr += __shfl_xor_sync(0xffffffffu, pr, o);
+        pi += __shfl_xor_sync(0xffffffffu, pi, o);
+        pq += __shfl_xor_sync(0xffffffffu, pq, o);
+      }
+      if (lane < kG2) {
+        sred[(warp * kG2 + lane) * 3 + 0] = pr;
+        sred[(warp * kG2 + lane) * 3 + 1] = pi;
+        sred[(warp * kG2 + lane) * 3 + 2] = pq;
+      }
+      __syncthreads();
+      if (tid < kG2) {
+        double a = 0, bb = 0, cc = 0;
+        for (int w = 0; w < T / 32; ++w) {
+          a += sred[(w * kG2 + tid) * 3 + 0];
+          bb += sred[(w * kG2 + tid) * 3 + 1];
+          cc += sred[(w * kG2 + tid) * 3 + 2];
+        }
+        salpha[2 * tid] = cc > 0 ? (float)(a / cc) : 0.f;
+        salpha[2 * tid + 1] = cc > 0 ? (float)(bb / cc) : 0.f;
+      }
+      __syncthreads();
+      const cx<float> al = mk(salpha[2 * d.g], salpha[2 * d.g + 1]);
+      {
+        float xv[24];
+        tm_get(tm, xv);
+        if (valid) {
+#pragma unroll
+          for (int c = 0; c < 12; ++c) {
+            const int i0 = ((2 * c) * Va + d.l) * kG2 + d.g, i1 = ((2 * c + 1) * Va + d.l) * kG2 + d.g;
+            cx<float> rv = mk(sR[i0], sR[i1]);
+            cx<float> xc = mk(xv[2 * c], xv[2 * c + 1]);
+            fma_(xc, al, rv);
+            xv[2 * c] = xc.re;
+            xv[2 * c + 1] = xc.im;
+            fma_(rv, al, mk(-qr[c], -qi[c]));
+            sR[i0] = rv.re;
+            sR[i1] = rv.im;
+          }
+        }
+        tm_put(tm, xv);
+      }
+      tc::tmem_wait_st();
+      __syncthreads();
+    }
+    {
+      float xv[24];
+      tm_get(tm, xv);
+      if (valid) {
+        float* xs = x + (d.s0 + d.l) * 24 * N + r0 + d.g;
+#pragma unroll
+        for (int k = 0; k < 24; ++k) xs[k * N] = xv[k];
+      }
+    }
+    __syncthreads();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(s_tmem, tm_cols);
+}
+
 }  // namespace
 
-// threads for a domain of Va sites: four items per site, at most two items
-// per thread, whole warpgroups
-static int sap_tm_threads(int Va) { return 128 * ((kG * Va + 255) / 256); }
+// threads for a domain of Va sites: G items per site, at most two items per
+// thread (G = 4) or one (G = 2), whole warpgroups
+static int sap_tm_threads(int Va, int G) { return G == 4 ? 128 * ((kG * Va + 255) / 256) : 128 * ((2 * Va + 127) / 128); }
 
-static size_t sap_tm_smem(int Va, int T) {
-  return sizeof(float4) * 20 * (size_t)(Va + 1) + sizeof(float) * ((size_t)24 * Va * kG + (T / 32) * kG * 3 + 2 * kG);
+static size_t sap_tm_smem(int Va, int T, int G) {
+  if (G == 4)
+    return sizeof(float4) * 20 * (size_t)(Va + 1) +
+           sizeof(float) * ((size_t)24 * Va * kG + (T / 32) * kG * 3 + 2 * kG);
+  return sizeof(float4) * 38 * (size_t)(Va + 1) + sizeof(int) * 8 * (size_t)Va +
+         sizeof(float) * ((size_t)24 * Va * kG2 + (T / 32) * kG2 * 3 + 2 * kG2);
 }
 
-bool sap_tm_ok(mrhs_ctx c, int nrhs) {
-  const int Va = c->g.Va;
-  if (nrhs % kG != 0 || Va > 256 || !c->U20) return false;
+static int max_smem(mrhs_ctx c) {
   int maxsm = 0;
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
-  return sap_tm_smem(Va, sap_tm_threads(Va)) <= (size_t)maxsm;
+  return maxsm;
 }
+
+// chunk width: 2 (everything on chip) unless MRHS_SAP_CHUNK=4 asks for the
+// four-RHS form (clover through L1) or the 2-wide form does not fit
+static int sap_tm_width(mrhs_ctx c, int nrhs) {
+  static const int forced = [] {
+    const char* e = std::getenv("MRHS_SAP_CHUNK");
+    return e ? std::atoi(e) : 0;
+  }();
+  const int Va = c->g.Va;
+  if (Va > 256 || !c->U20) return 0;
+  const bool ok2 = nrhs % 2 == 0 && sap_tm_smem(Va, sap_tm_threads(Va, 2), 2) <= (size_t)max_smem(c);
+  const bool ok4 = nrhs % 4 == 0 && sap_tm_smem(Va, sap_tm_threads(Va, 4), 4) <= (size_t)max_smem(c);
+  if (forced == 4 && ok4) return 4;
+  if (ok2) return 2;
+  return ok4 ? 4 : 0;
+}
+
+bool sap_tm_ok(mrhs_ctx c, int nrhs) { return sap_tm_width(c, nrhs) > 0; }
 
 void sap_tm(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int n_sweeps, int n_mr) {
   const int Va = c->g.Va;
-  const int T = sap_tm_threads(Va);
-  const size_t smem = sap_tm_smem(Va, T);
-  // columns: (T/128) warpgroups x 2 items x 24, rounded up to a power of two >= 32
+  const int G = sap_tm_width(c, nrhs);
+  const int T = sap_tm_threads(Va, G);
+  const size_t smem = sap_tm_smem(Va, T, G);
+  // columns: (T/128) warpgroups x items per thread x 24, rounded up to a power of two >= 32
   uint32_t cols = 32;
-  while (cols < (uint32_t)(T / 128) * 2 * kColsItem) cols <<= 1;
+  while (cols < (uint32_t)(T / 128) * (G == 4 ? 2 : 1) * kColsItem) cols <<= 1;
+  // CTAs per domain: by default one chunk of G right-hand sides each, so that
+  // the CTAs of a domain run side by side and share every 32-byte sector of
+  // x and b in L2 (MRHS_SAP_CPB overrides, 1 = one CTA loops over the chunks)
+  static const int cpb_env = [] {
+    const char* e = std::getenv("MRHS_SAP_CPB");
+    return e ? std::atoi(e) : 0;
+  }();
+  const int nch = nrhs / G;
+  const int cpb = cpb_env > 0 ? std::min(cpb_env, nch) : nch;
   for (int sw = 0; sw < n_sweeps; ++sw)
     for (int col = 0; col < 2; ++col) {
       const int* blist = c->blocks_col + (col ? c->ncol[0] : 0);
       Prof pr(c, "sap_tm");
       MRHS_DISPATCH(bdtype, SB, {
-        auto kern = k_sap_tm<SB>;
+        auto kern = G == 4 ? k_sap_tm<SB> : k_sap_tm2<SB>;
         MRHS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<c->ncol[col], T, smem, c->stream>>>((const SB*)b, (float*)x, c->U20, c->A32, c->nbr, nrhs, Va, blist,
-                                                   n_mr, cols);
+        kern<<<c->ncol[col] * cpb, T, smem, c->stream>>>((const SB*)b, (float*)x, c->U20, c->A32, c->nbr, nrhs, Va,
+                                                         blist, n_mr, cols, cpb);
       });
       MRHS_LAUNCH_CHECK("sap_tm");
     }
