@@ -83,7 +83,7 @@ __device__ __forceinline__ void hop1(float ore[12], float oim[12], const float p
 }
 
 struct Dom {
-  const float* sR;   // [24][Va][4]
+  const float2* sR;  // [12][Va][4] (re, im)
   const float4* sU;  // [20][Va+1]
   int Va, l, g;
   size_t s0;         // first device site of the domain
@@ -92,8 +92,9 @@ struct Dom {
 __device__ __forceinline__ void load_rho(const Dom& d, int n, float pr[12], float pi[12]) {
 #pragma unroll
   for (int c = 0; c < 12; ++c) {
-    pr[c] = d.sR[((2 * c) * d.Va + n) * kG + d.g];
-    pi[c] = d.sR[((2 * c + 1) * d.Va + n) * kG + d.g];
+    const float2 v = d.sR[(c * d.Va + n) * kG + d.g];
+    pr[c] = v.x;
+    pi[c] = v.y;
   }
 }
 
@@ -191,6 +192,24 @@ __device__ __forceinline__ void apply_dom(const Dom& d, float ore[12], float oim
   hop_dom<3, -1, RESID>(d, ore, oim, nbr, x, U20, N, r0);
 }
 
+// four consecutive right-hand sides of one row of b (16-byte / 8-byte load)
+__device__ __forceinline__ void ld4(const float* p, float v[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double* p, float v[4]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = (float)p[i];
+}
+template <class H>
+__device__ __forceinline__ void ld4(const H* p, float v[4]) {
+  const uint2 t = *reinterpret_cast<const uint2*>(p);
+  H h[4];
+  *reinterpret_cast<uint2*>(h) = t;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = (float)to_r(h[i]);
+}
+
 __device__ __forceinline__ void tm_put(uint32_t ta, const float v[24]) {
   tc::tmem_st8(ta, v);
   tc::tmem_st8(ta + 8, v + 8);
@@ -211,9 +230,9 @@ __global__ void __launch_bounds__(kMaxT, 1) k_sap_tm(const SB* __restrict__ b, f
   extern __shared__ float4 smem4[];
   const int T = blockDim.x;
   float4* sU = smem4;                                     // [20][Va+1]
-  float* sR = reinterpret_cast<float*>(sU + 20 * (Va + 1));  // [24][Va][4]
-  float* sred = sR + 24 * Va * kG;                        // [T/32][4][3]
-  float* salpha = sred + (T / 32) * kG * 3;               // [4][2]
+  float* sR = reinterpret_cast<float*>(sU + 20 * (Va + 1));  // [12][Va][4] x (re, im)
+  float2* sR2 = reinterpret_cast<float2*>(sR);
+  float* sred = sR + 24 * Va * kG;                        // [T/32][4] float4 (pr, pi, pq, -)
   __shared__ uint32_t s_tmem;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -222,7 +241,7 @@ __global__ void __launch_bounds__(kMaxT, 1) k_sap_tm(const SB* __restrict__ b, f
   d.Va = Va;
   d.g = tid & (kG - 1);
   d.s0 = (size_t)blist[blockIdx.x / cpb] * Va;
-  d.sR = sR;
+  d.sR = sR2;
   d.sU = sU;
 
   if (warp == 0) {
@@ -242,18 +261,30 @@ __global__ void __launch_bounds__(kMaxT, 1) k_sap_tm(const SB* __restrict__ b, f
   const bool v0 = tid < nit, v1 = tid + T < nit;
 
   for (int r0 = (blockIdx.x % cpb) * kG; r0 < N; r0 += cpb * kG) {
-    // stage x0: shared memory (stencil input) and tensor memory (running solution)
+    // stage x0 into shared memory, one (component pair c, site l) per unit:
+    // the real and the imaginary row of the chunk's four right-hand sides
+    // (two 16-byte loads) become the four (re, im) pairs of [c][l][g]
+    for (int u = tid; u < 12 * Va; u += T) {
+      const int c = u / Va, l = u % Va;
+      const float* xs = x + ((d.s0 + l) * 24 + 2 * c) * N + r0;
+      const float4 re = *reinterpret_cast<const float4*>(xs);
+      const float4 im = *reinterpret_cast<const float4*>(xs + N);
+      float4* dst = reinterpret_cast<float4*>(sR2 + (c * Va + l) * kG);
+      dst[0] = make_float4(re.x, im.x, re.y, im.y);
+      dst[1] = make_float4(re.z, im.z, re.w, im.w);
+    }
+    __syncthreads();
+    // the thread's items of x0 -> tensor memory (running solution)
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const int i = tid + j * T;
       float v[24];
       if (i < nit) {
-        const int l = i >> 2;
-        const float* xs = x + (d.s0 + l) * 24 * N + r0 + d.g;
 #pragma unroll
-        for (int k = 0; k < 24; ++k) {
-          v[k] = xs[k * N];
-          sR[(k * Va + l) * kG + d.g] = v[k];
+        for (int c = 0; c < 12; ++c) {
+          const float2 t = sR2[(c * Va + (i >> 2)) * kG + d.g];
+          v[2 * c] = t.x;
+          v[2 * c + 1] = t.y;
         }
       } else {
 #pragma unroll
@@ -262,44 +293,45 @@ __global__ void __launch_bounds__(kMaxT, 1) k_sap_tm(const SB* __restrict__ b, f
       tm_put(tm + j * kColsItem, v);
     }
     tc::tmem_wait_st();
-    __syncthreads();
-    // r = b - D x0 for both items (registers), then rho = r
+    // D x0 for both items (registers)
     float q0r[12], q0i[12], q1r[12], q1i[12];
     if (v0) {
       d.l = tid >> 2;
       apply_dom<true>(d, q0r, q0i, Acl, nbr, x, U20, N, r0);
-      const SB* bs = b + (d.s0 + d.l) * 24 * N + r0 + d.g;
-#pragma unroll
-      for (int c = 0; c < 12; ++c) {
-        q0r[c] = (float)to_r(bs[(2 * c) * N]) - q0r[c];
-        q0i[c] = (float)to_r(bs[(2 * c + 1) * N]) - q0i[c];
-      }
     }
     if (v1) {
       d.l = (tid + T) >> 2;
       apply_dom<true>(d, q1r, q1i, Acl, nbr, x, U20, N, r0);
-      const SB* bs = b + (d.s0 + d.l) * 24 * N + r0 + d.g;
-#pragma unroll
-      for (int c = 0; c < 12; ++c) {
-        q1r[c] = (float)to_r(bs[(2 * c) * N]) - q1r[c];
-        q1i[c] = (float)to_r(bs[(2 * c + 1) * N]) - q1i[c];
-      }
+    }
+    __syncthreads();
+    // stage b the same way as x0, then rho = b - D x0 item by item
+    for (int u = tid; u < 12 * Va; u += T) {
+      const int c = u / Va, l = u % Va;
+      const SB* bs = b + ((d.s0 + l) * 24 + 2 * c) * N + r0;
+      float re[4], im[4];
+      ld4(bs, re);
+      ld4(bs + N, im);
+      float4* dst = reinterpret_cast<float4*>(sR2 + (c * Va + l) * kG);
+      dst[0] = make_float4(re[0], im[0], re[1], im[1]);
+      dst[1] = make_float4(re[2], im[2], re[3], im[3]);
     }
     __syncthreads();
     if (v0) {
       const int l = tid >> 2;
 #pragma unroll
       for (int c = 0; c < 12; ++c) {
-        sR[((2 * c) * Va + l) * kG + d.g] = q0r[c];
-        sR[((2 * c + 1) * Va + l) * kG + d.g] = q0i[c];
+        const int ix = (c * Va + l) * kG + d.g;
+        const float2 bv = sR2[ix];
+        sR2[ix] = make_float2(bv.x - q0r[c], bv.y - q0i[c]);
       }
     }
     if (v1) {
       const int l = (tid + T) >> 2;
 #pragma unroll
       for (int c = 0; c < 12; ++c) {
-        sR[((2 * c) * Va + l) * kG + d.g] = q1r[c];
-        sR[((2 * c + 1) * Va + l) * kG + d.g] = q1i[c];
+        const int ix = (c * Va + l) * kG + d.g;
+        const float2 bv = sR2[ix];
+        sR2[ix] = make_float2(bv.x - q1r[c], bv.y - q1i[c]);
       }
     }
     __syncthreads();
@@ -329,31 +361,26 @@ __global__ void __launch_bounds__(kMaxT, 1) k_sap_tm(const SB* __restrict__ b, f
           pq = fmaf(q1r[c], q1r[c], fmaf(q1i[c], q1i[c], pq));
         }
       }
-      // sums over the lanes of the same rhs (lane % 4), then over warps
+      // sums over the lanes of the same rhs (lane % 4), then over warps:
+      // every thread adds the per-warp partials of its rhs in the same order,
+      // so all threads of one rhs hold the same alpha
 #pragma unroll
       for (int o = kG; o < 32; o <<= 1) {
         pr += __shfl_xor_sync(0xffffffffu, pr, o);
         pi += __shfl_xor_sync(0xffffffffu, pi, o);
         pq += __shfl_xor_sync(0xffffffffu, pq, o);
       }
-      if (lane < kG) {
-        sred[(warp * kG + lane) * 3 + 0] = pr;
-        sred[(warp * kG + lane) * 3 + 1] = pi;
-        sred[(warp * kG + lane) * 3 + 2] = pq;
-      }
+      float4* sred4 = reinterpret_cast<float4*>(sred);
+      if (lane < kG) sred4[warp * kG + lane] = make_float4(pr, pi, pq, 0.f);
       __syncthreads();
-      if (tid < kG) {
-        double a = 0, bb = 0, cc = 0;
-        for (int w = 0; w < T / 32; ++w) {
-          a += sred[(w * kG + tid) * 3 + 0];
-          bb += sred[(w * kG + tid) * 3 + 1];
-          cc += sred[(w * kG + tid) * 3 + 2];
-        }
-        salpha[2 * tid] = cc > 0 ? (float)(a / cc) : 0.f;
-        salpha[2 * tid + 1] = cc > 0 ? (float)(bb / cc) : 0.f;
+      float a = 0.f, bb = 0.f, cc = 0.f;
+      for (int w = 0; w < T / 32; ++w) {
+        const float4 t = sred4[w * kG + d.g];
+        a += t.x;
+        bb += t.y;
+        cc += t.z;
       }
-      __syncthreads();
-      const cx<float> al = mk(salpha[2 * d.g], salpha[2 * d.g + 1]);
+      const cx<float> al = cc > 0.f ? mk(a / cc, bb / cc) : mk(0.f, 0.f);
       // x_B += alpha rho (tensor memory), rho -= alpha q (shared memory)
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
@@ -364,16 +391,16 @@ __global__ void __launch_bounds__(kMaxT, 1) k_sap_tm(const SB* __restrict__ b, f
           const int l = (tid + j * T) >> 2;
 #pragma unroll
           for (int c = 0; c < 12; ++c) {
-            const int i0 = ((2 * c) * Va + l) * kG + d.g, i1 = ((2 * c + 1) * Va + l) * kG + d.g;
-            cx<float> rv = mk(sR[i0], sR[i1]);
+            const int i0 = (c * Va + l) * kG + d.g;
+            const float2 r2 = sR2[i0];
+            cx<float> rv = mk(r2.x, r2.y);
             cx<float> xc = mk(xv[2 * c], xv[2 * c + 1]);
             fma_(xc, al, rv);
             xv[2 * c] = xc.re;
             xv[2 * c + 1] = xc.im;
             const cx<float> qv = j == 0 ? mk(-q0r[c], -q0i[c]) : mk(-q1r[c], -q1i[c]);
             fma_(rv, al, qv);
-            sR[i0] = rv.re;
-            sR[i1] = rv.im;
+            sR2[i0] = make_float2(rv.re, rv.im);
           }
         }
         tm_put(tm + j * kColsItem, xv);
@@ -381,17 +408,25 @@ __global__ void __launch_bounds__(kMaxT, 1) k_sap_tm(const SB* __restrict__ b, f
       tc::tmem_wait_st();
       __syncthreads();
     }
-    // x = x_B
+    // x = x_B: items -> shared memory, then 16-byte rows back to x
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       float xv[24];
       tm_get(tm + j * kColsItem, xv);
       const int i = tid + j * T;
       if (i < nit) {
-        float* xs = x + (d.s0 + (i >> 2)) * 24 * N + r0 + d.g;
 #pragma unroll
-        for (int k = 0; k < 24; ++k) xs[k * N] = xv[k];
+        for (int c = 0; c < 12; ++c) sR2[(c * Va + (i >> 2)) * kG + d.g] = make_float2(xv[2 * c], xv[2 * c + 1]);
       }
+    }
+    __syncthreads();
+    for (int u = tid; u < 12 * Va; u += T) {
+      const int c = u / Va, l = u % Va;
+      float* xs = x + ((d.s0 + l) * 24 + 2 * c) * N + r0;
+      const float4* src = reinterpret_cast<const float4*>(sR2 + (c * Va + l) * kG);
+      const float4 p0 = src[0], p1 = src[1];
+      *reinterpret_cast<float4*>(xs) = make_float4(p0.x, p0.z, p1.x, p1.z);
+      *reinterpret_cast<float4*>(xs + N) = make_float4(p0.y, p0.w, p1.y, p1.w);
     }
     __syncthreads();
   }
@@ -671,8 +706,7 @@ static int sap_tm_threads(int Va, int G) { return G == 4 ? 128 * ((kG * Va + 255
 
 static size_t sap_tm_smem(int Va, int T, int G) {
   if (G == 4)
-    return sizeof(float4) * 20 * (size_t)(Va + 1) +
-           sizeof(float) * ((size_t)24 * Va * kG + (T / 32) * kG * 3 + 2 * kG);
+    return sizeof(float4) * 20 * (size_t)(Va + 1) + sizeof(float) * ((size_t)24 * Va * kG + (T / 32) * kG * 4);
   return sizeof(float4) * 38 * (size_t)(Va + 1) + sizeof(int) * 8 * (size_t)Va +
          sizeof(float) * ((size_t)24 * Va * kG2 + (T / 32) * kG2 * 3 + 2 * kG2);
 }
@@ -683,8 +717,8 @@ static int max_smem(mrhs_ctx c) {
   return maxsm;
 }
 
-// chunk width: 2 (everything on chip) unless MRHS_SAP_CHUNK=4 asks for the
-// four-RHS form (clover through L1) or the 2-wide form does not fit
+// chunk width: 4 (clover through L1; measured faster) unless MRHS_SAP_CHUNK=2
+// asks for the two-RHS form (everything on chip) or nrhs is not a multiple of 4
 static int sap_tm_width(mrhs_ctx c, int nrhs) {
   static const int forced = [] {
     const char* e = std::getenv("MRHS_SAP_CHUNK");
@@ -694,9 +728,9 @@ static int sap_tm_width(mrhs_ctx c, int nrhs) {
   if (Va > 256 || !c->U20) return 0;
   const bool ok2 = nrhs % 2 == 0 && sap_tm_smem(Va, sap_tm_threads(Va, 2), 2) <= (size_t)max_smem(c);
   const bool ok4 = nrhs % 4 == 0 && sap_tm_smem(Va, sap_tm_threads(Va, 4), 4) <= (size_t)max_smem(c);
-  if (forced == 4 && ok4) return 4;
-  if (ok2) return 2;
-  return ok4 ? 4 : 0;
+  if (forced == 2 && ok2) return 2;
+  if (ok4) return 4;
+  return ok2 ? 2 : 0;
 }
 
 bool sap_tm_ok(mrhs_ctx c, int nrhs) { return sap_tm_width(c, nrhs) > 0; }
