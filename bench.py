@@ -448,6 +448,8 @@ def run_learned_mixed(args, cfg, U, m0, stream, plain_ms, barrier):
         step_fn()
     torch.cuda.synchronize()
     barrier()
+    pkg.mrhs_profile(lat.ctx, 1)
+    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
@@ -455,6 +457,10 @@ def run_learned_mixed(args, cfg, U, m0, stream, plain_ms, barrier):
     e1.record(stream)
     torch.cuda.synchronize()
     lm_ms = e0.elapsed_time(e1) / args.steps
+    prof = pkg.mrhs_profile_read(lat.ctx)
+    pkg.mrhs_profile(lat.ctx, 0)
+    kernels = {k: {"launches": n // args.steps, "ms_per_step": t / args.steps, "share": t / args.steps / lm_ms}
+               for k, (n, t) in prof.items()}
     fg = None
     if not args.no_fgmres:
         pkg.mrhs_trim(lat.ctx)
@@ -462,7 +468,9 @@ def run_learned_mixed(args, cfg, U, m0, stream, plain_ms, barrier):
     lat.close()
     return {"value": lm_ms / 1000.0, "unit": "s", "ratio_vs_plain": lm_ms / plain_ms,
             "form": "1 SAP sweep + network (widths %s, bf16 weights) for the initial phase, bf16 test vectors and P, "
-                    "FP32 smoother and D_c, then the same refinement" % (list(learned.WIDTHS),),
+                    "FP32 smoother, D_c contraction on bf16 tensor cores with FP32 accumulation (D_c stored FP32), "
+                    "tf32 tensor-core coarse stencil, then the same refinement" % (list(learned.WIDTHS),),
+            "kernels": kernels,
             "training": {"lattice": [16, 16, 16, 16], "fields": 8, "steps": step - 1, "loss_first": losses[0],
                          "loss_last": losses[-1], "seconds": round(train_s, 1)},
             "fgmres": fg}

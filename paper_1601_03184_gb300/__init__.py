@@ -24,7 +24,7 @@ MRHS_ERR_ARG, MRHS_ERR_SHAPE, MRHS_ERR_OOM, MRHS_ERR_CUDA = -1, -2, -3, -4
 MRHS_ERR_NOCONV, MRHS_ERR_NONFINITE, MRHS_ERR_STATE, MRHS_ERR_TIMEOUT = -5, -6, -7, -8
 MRHS_F64, MRHS_F32, MRHS_BF16, MRHS_F16 = 0, 1, 2, 3
 MRHS_PREC_FP64, MRHS_PREC_FP32, MRHS_PREC_MIX_BF16, MRHS_PREC_MIX_FP16 = 0, 1, 2, 3
-MRHS_DC_AUTO, MRHS_DC_ALU, MRHS_DC_TC_BF16, MRHS_DC_TC_F16, MRHS_DC_TC_TF32 = 0, 1, 2, 3, 4
+MRHS_DC_AUTO, MRHS_DC_ALU, MRHS_DC_TC_BF16, MRHS_DC_TC_F16, MRHS_DC_TC_TF32, MRHS_DC_TC_TF32X3 = 0, 1, 2, 3, 4, 5
 
 _VP = ctypes.c_void_p
 _I = ctypes.c_int

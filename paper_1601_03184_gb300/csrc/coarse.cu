@@ -1,6 +1,8 @@
 // Coarse grid: D_c = P^dag D P assembly, restriction R = P^dag (Algorithm 3
 // of the paper, all right-hand sides at once), prolongation, the coarse
 // 9-point stencil and the multi-RHS coarse GMRES.
+#include <cstdlib>
+
 #include "coarse_common.cuh"
 
 namespace mrhs {
@@ -560,17 +562,20 @@ void build_Dc(mrhs_ctx c) {
   const bool tiled = Nt % 4 == 0 && nc <= 64;
   // tensor-core contraction: chosen explicitly, or by default for the mixed setups
   int fmt = -1;
+  bool split = false;
   switch (c->dc_engine) {
     case MRHS_DC_TC_BF16: fmt = tc_fmt_bf16; break;
     case MRHS_DC_TC_F16: fmt = tc_fmt_f16; break;
     case MRHS_DC_TC_TF32: fmt = tc_fmt_tf32; break;
+    case MRHS_DC_TC_TF32X3: fmt = tc_fmt_tf32; split = true; break;
     case MRHS_DC_AUTO:
+      if (c->prec == MRHS_PREC_FP32) fmt = tc_fmt_tf32, split = true;
       if (c->prec == MRHS_PREC_MIX_BF16) fmt = tc_fmt_bf16;
       if (c->prec == MRHS_PREC_MIX_FP16) fmt = tc_fmt_tf32;
       break;
     default: break;
   }
-  if (fmt >= 0 && build_Dc_tc(c, fmt)) {
+  if (fmt >= 0 && build_Dc_tc(c, fmt, split)) {
     size_t tot = (size_t)c->g.nagg * 4 * nc * nc;
     k_coarse_backward<float><<<grid_for(tot, 256), 256, 0, c->stream>>>((cx<float>*)c->Dc, c->aggnbr, c->g.nagg, Nt);
     MRHS_LAUNCH_CHECK("coarse_backward");
@@ -675,7 +680,11 @@ void apply_Dc(mrhs_ctx c, const void* xc, void* yc, int nrhs, int dtype) {
   const int nc = 2 * c->ntv;
   // tensor cores unless the CUDA-core engine is chosen: split tf32 (FP32
   // accuracy) for the FP32 setup, single tf32 for the mixed ones
-  if (c->dc_engine != MRHS_DC_ALU && dtype == MRHS_F32) {
+  static const bool apply_alu = [] {
+    const char* e = std::getenv("MRHS_DC_APPLY");
+    return e && std::string(e) == "alu";
+  }();
+  if (c->dc_engine != MRHS_DC_ALU && dtype == MRHS_F32 && !apply_alu) {
     const bool split = c->prec == MRHS_PREC_FP32;
     if (apply_Dc_tc(c, xc, yc, nrhs, split)) return;
   }
@@ -911,7 +920,7 @@ int mrhs_build_Dc(mrhs_ctx c) {
 int mrhs_set_dc_engine(mrhs_ctx c, int engine) {
   return guarded(c, [&] {
     MRHS_REQUIRE(c, MRHS_ERR_ARG, "null context");
-    MRHS_REQUIRE(engine >= MRHS_DC_AUTO && engine <= MRHS_DC_TC_TF32, MRHS_ERR_ARG, "unknown D_c engine");
+    MRHS_REQUIRE(engine >= MRHS_DC_AUTO && engine <= MRHS_DC_TC_TF32X3, MRHS_ERR_ARG, "unknown D_c engine");
     c->dc_engine = engine;
   });
 }

@@ -65,6 +65,12 @@ struct Elem<tc::kFmtTF32> {
   }
 };
 
+__device__ __forceinline__ void tf32_split(float v, uint32_t& hi, uint32_t& lo) {
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(v));
+  const float r = v - __uint_as_float(hi);
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(r));
+}
+
 // store the pair of elements (row, k), (row, k+1), k even, of a K-major tile
 template <int FMT>
 __device__ __forceinline__ void put2(unsigned char* tile, int row, int k, float a, float b) {
@@ -77,7 +83,17 @@ __device__ __forceinline__ void put2(unsigned char* tile, int row, int k, float 
   }
 }
 
-template <int FMT, class SP>
+// the same for split tf32: v = hi + lo, hi into one tile and lo into the other
+__device__ __forceinline__ void put2_split(unsigned char* thi, unsigned char* tlo, int row, int k, float a, float b) {
+  const uint32_t off = tc::kmajor_offset(row, k, 4, kKG);
+  uint32_t ha, la, hb, lb;
+  tf32_split(a, ha, la);
+  tf32_split(b, hb, lb);
+  *reinterpret_cast<uint2*>(thi + off) = make_uint2(ha, hb);
+  *reinterpret_cast<uint2*>(tlo + off) = make_uint2(la, lb);
+}
+
+template <int FMT, class SP, bool SPLIT>
 __global__ void __launch_bounds__(kThreads) k_coarse_op_tc(const SP* __restrict__ P, const cx<float>* __restrict__ U,
                                                            const float* __restrict__ Acl, const int* __restrict__ nbr,
                                                            int Nt, Agg4 ag, int Va, cx<float>* __restrict__ Dc,
@@ -100,7 +116,8 @@ __global__ void __launch_bounds__(kThreads) k_coarse_op_tc(const SP* __restrict_
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   // zero both stages once: padding rows and off-chirality entries of A stay zero
-  for (int i = threadIdx.x; i < 4 * kTileBytes / 16; i += kThreads)
+  constexpr int NT = SPLIT ? 4 : 2;  // tiles per stage: A, B (and their low parts)
+  for (int i = threadIdx.x; i < 2 * NT * kTileBytes / 16; i += kThreads)
     reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
   if (threadIdx.x == 0) {
     tc::mbar_init(&mbar[0], 1);
@@ -109,26 +126,40 @@ __global__ void __launch_bounds__(kThreads) k_coarse_op_tc(const SP* __restrict_
     s_bad = 0;
   }
   if (warp == 0) {
-    tc::tmem_alloc(&s_tmem, 128);
+    tc::tmem_alloc(&s_tmem, 256);
     tc::tmem_relinquish();
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
+  // R (columns 0..127): the MMAs of one chunk; S (128..255): the sum of the
+  // chunks, kept by the CUDA cores (warp w: lanes 32 (w % 4).., columns
+  // 64 (w / 4)..)
   const uint32_t tbase = s_tmem;
+  const uint32_t t_own = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(64 * (warp >> 2));
+  const int own_cols = max(0, min(64, NN - 64 * (warp >> 2)));
+  {
+    float z[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) z[i] = 0.f;
+    for (int c0 = 0; c0 < own_cols; c0 += 16) tc::tmem_st16(t_own + 128 + c0, z);
+    tc::tmem_wait_st();
+  }
   const uint32_t idesc = tc::instr_desc(FMT, FMT, kRows, NN);
 
   const int nchunk = (nsite + Q - 1) / Q;
   int issued = 0;
   for (int t = 0; t < nchunk; ++t) {
     const int st = t & 1;
-    if (t >= 2 && !tc::mbar_wait(&mbar[st], ((t >> 1) - 1) & 1, kWaitLimit)) s_bad = 1;
-    __syncthreads();
+    // stage st was last read by the MMAs of chunk t-2, complete since the
+    // previous iteration waited for chunk t-1
     if (s_bad) break;
     const int q0 = t * Q;
     const int nq = min(Q, nsite - q0);
-    unsigned char* tA = smem + 2 * st * kTileBytes;
+    unsigned char* tA = smem + NT * st * kTileBytes;
     unsigned char* tB = tA + kTileBytes;
+    unsigned char* tAl = tA + 2 * kTileBytes;  // low parts (SPLIT)
+    unsigned char* tBl = tA + 3 * kTileBytes;
     // B: Y = D_k P for (site q, column col); absent sites of a ragged chunk give zeros
     for (int w = threadIdx.x; w < Q * nc; w += kThreads) {
       const int q = w / nc, col = w % nc;
@@ -159,8 +190,13 @@ __global__ void __launch_bounds__(kThreads) k_coarse_op_tc(const SP* __restrict_
       }
 #pragma unroll
       for (int c = 0; c < 12; c += 2) {
-        put2<FMT>(tB, col, q * 12 + c, out[c].re, out[c + 1].re);
-        put2<FMT>(tB, nc + col, q * 12 + c, out[c].im, out[c + 1].im);
+        if constexpr (SPLIT) {
+          put2_split(tB, tBl, col, q * 12 + c, out[c].re, out[c + 1].re);
+          put2_split(tB, tBl, nc + col, q * 12 + c, out[c].im, out[c + 1].im);
+        } else {
+          put2<FMT>(tB, col, q * 12 + c, out[c].re, out[c + 1].re);
+          put2<FMT>(tB, nc + col, q * 12 + c, out[c].im, out[c + 1].im);
+        }
       }
     }
     // A: P rows (part p, h, j) for the components of chirality h
@@ -178,41 +214,60 @@ __global__ void __launch_bounds__(kThreads) k_coarse_op_tc(const SP* __restrict_
       const size_t s = (size_t)A * Va + l;
       const float a = to_r(P[((s * 12 + c) * 2 + p) * Nt + j]);
       const float b = to_r(P[((s * 12 + c + 1) * 2 + p) * Nt + j]);
-      put2<FMT>(tA, p * nc + h * Nt + j, q * 12 + c, a, b);
+      if constexpr (SPLIT) put2_split(tA, tAl, p * nc + h * Nt + j, q * 12 + c, a, b);
+      else put2<FMT>(tA, p * nc + h * Nt + j, q * 12 + c, a, b);
     }
     tc::fence_async_smem();
+    // chunk t-1 done: fold its partial sum R into S before R is reused
+    if (t >= 1) {
+      if (!tc::mbar_wait(&mbar[0], (t - 1) & 1, kWaitLimit)) s_bad = 1;
+      tc::fence_after_sync();
+      tc::tmem_promote(t_own + 128, t_own, own_cols);
+      tc::tmem_wait_st();
+    }
+    tc::fence_before_sync();
     __syncthreads();
+    if (s_bad) break;
     if (threadIdx.x == 0) {
       tc::fence_after_sync();
       const uint32_t a0 = tc::smem_u32(tA), b0 = tc::smem_u32(tB);
+      const uint32_t a1 = tc::smem_u32(tAl), b1 = tc::smem_u32(tBl);
 #pragma unroll
       for (int ks = 0; ks < kKG / 2; ++ks) {
         const uint64_t ad = tc::smem_desc(a0 + ks * KSTEP_BYTES, 128, kKG * 128);
         const uint64_t bd = tc::smem_desc(b0 + ks * KSTEP_BYTES, 128, kKG * 128);
-        if constexpr (FMT == tc::kFmtTF32)
-          tc::mma_tf32(tbase, ad, bd, idesc, (t > 0 || ks > 0) ? 1u : 0u);
-        else
-          tc::mma_f16(tbase, ad, bd, idesc, (t > 0 || ks > 0) ? 1u : 0u);
+        if constexpr (FMT == tc::kFmtTF32) {
+          tc::mma_tf32(tbase, ad, bd, idesc, ks > 0 ? 1u : 0u);
+          if constexpr (SPLIT) {
+            tc::mma_tf32(tbase, ad, tc::smem_desc(b1 + ks * KSTEP_BYTES, 128, kKG * 128), idesc, 1u);
+            tc::mma_tf32(tbase, tc::smem_desc(a1 + ks * KSTEP_BYTES, 128, kKG * 128), bd, idesc, 1u);
+          }
+        } else {
+          tc::mma_f16(tbase, ad, bd, idesc, ks > 0 ? 1u : 0u);
+        }
       }
-      tc::mma_commit(&mbar[st]);
+      tc::mma_commit(&mbar[0]);
     }
     issued = t + 1;
   }
-  // the last commit covers every MMA issued before it
+  // the last chunk: wait, fold into S
   if (issued > 0) {
-    const int tl = issued - 1;
-    if (!tc::mbar_wait(&mbar[tl & 1], (tl >> 1) & 1, kWaitLimit)) s_bad = 1;
+    if (!tc::mbar_wait(&mbar[0], (issued - 1) & 1, kWaitLimit)) s_bad = 1;
+    tc::fence_after_sync();
+    tc::tmem_promote(t_own + 128, t_own, own_cols);
+    tc::tmem_wait_st();
   }
-  tc::fence_after_sync();
+  tc::fence_before_sync();
   __syncthreads();
+  tc::fence_after_sync();
   const bool ok = !s_bad && issued == nchunk;
   if (ok) {
-    // accumulator rows -> shared memory (stage buffers are free now)
+    // the sum S -> shared memory (stage buffers are free now)
     float* E = reinterpret_cast<float*>(smem);  // [128][NN + 1]
     const int quarter = warp & 3, half = warp >> 2;
     for (int col0 = half * 64; col0 < min(NN, half * 64 + 64); col0 += 16) {
       float v[16];
-      tc::tmem_ld16(tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)col0, v);
+      tc::tmem_ld16(tbase + ((uint32_t)(quarter * 32) << 16) + 128u + (uint32_t)col0, v);
       const int row = quarter * 32 + lane;
 #pragma unroll
       for (int i = 0; i < 16; ++i) E[row * (NN + 1) + col0 + i] = v[i];
@@ -230,7 +285,7 @@ __global__ void __launch_bounds__(kThreads) k_coarse_op_tc(const SP* __restrict_
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tbase, 128);
+  if (warp == 0) tc::tmem_dealloc(tbase, 256);
 }
 
 // ---------------------------------------------------------------------------
@@ -250,18 +305,13 @@ __global__ void __launch_bounds__(kThreads) k_coarse_op_tc(const SP* __restrict_
 // waited for; two CTAs share an SM.
 constexpr int kDcThreads = 256;
 
-__device__ __forceinline__ void tf32_split(float v, uint32_t& hi, uint32_t& lo) {
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(v));
-  const float r = v - __uint_as_float(hi);
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(r));
-}
-
 template <bool SPLIT>
-__global__ void __launch_bounds__(kDcThreads) k_apply_dc_tc(const float* __restrict__ Dc, const float* __restrict__ x,
-                                                            float* __restrict__ y, const int* __restrict__ aggnbr,
-                                                            int nc, int nrhs, uint32_t tm_cols, int* __restrict__ err) {
+__global__ void __launch_bounds__(kDcThreads, 1) k_apply_dc_tc(const float* __restrict__ Dc,
+                                                               const float* __restrict__ x, float* __restrict__ y,
+                                                               const int* __restrict__ aggnbr, int nc, int nrhs,
+                                                               uint32_t tm_cols, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ uint64_t mbar;
+  __shared__ uint64_t full[2], mma_done;
   __shared__ uint32_t s_tmem;
   __shared__ int s_bad;
   const int A = blockIdx.x;
@@ -269,19 +319,23 @@ __global__ void __launch_bounds__(kDcThreads) k_apply_dc_tc(const float* __restr
   const int KG = nc / 4;                     // 16-byte K groups (tf32)
   const int a_bytes = kRows / 8 * KG * 128;  // A tile
   const int b_bytes = NM / 8 * KG * 128;     // B tile
-  unsigned char* Ahi = smem;
+  const uint32_t d_bytes = (uint32_t)nc * nc * 8, x_bytes = (uint32_t)nc * 2 * nrhs * 4;
+  const uint32_t raw_bytes = (d_bytes + x_bytes + 1023) & ~1023u;
+  unsigned char* raw0 = smem;                      // stage s: D block, then the x block
+  unsigned char* Ahi = smem + 2 * raw_bytes;
   unsigned char* Bhi = Ahi + a_bytes;
   unsigned char* Alo = Bhi + b_bytes;
   unsigned char* Blo = Alo + a_bytes;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  // rows of A beyond 2nc stay zero
-  if (2 * nc < kRows) {
+  if (2 * nc < kRows) {  // rows of A beyond 2nc stay zero
     const int nz = (SPLIT ? 2 : 1) * (a_bytes + b_bytes) / 16;
-    for (int i = threadIdx.x; i < nz; i += kDcThreads) reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < nz; i += kDcThreads) reinterpret_cast<uint4*>(Ahi)[i] = make_uint4(0, 0, 0, 0);
   }
-  if (threadIdx.x == 0) {
-    tc::mbar_init(&mbar, 1);
+  if (tid == 0) {
+    tc::mbar_init(&full[0], 1);
+    tc::mbar_init(&full[1], 1);
+    tc::mbar_init(&mma_done, 1);
     tc::fence_mbar_init();
     s_bad = 0;
   }
@@ -292,136 +346,144 @@ __global__ void __launch_bounds__(kDcThreads) k_apply_dc_tc(const float* __restr
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
+  // R (columns 0..NM-1): the MMAs of one block k; S (NM..2NM-1): the sum over
+  // the blocks, kept by the CUDA cores (warp w: lanes 32 (w % 4).., columns
+  // (NM/2) (w / 4)..)
   const uint32_t tbase = s_tmem;
+  const uint32_t t_own = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((NM / 2) * (warp >> 2));
+  {
+    float z[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) z[i] = 0.f;
+    for (int c0 = 0; c0 < NM / 2; c0 += 16) tc::tmem_st16(t_own + NM + c0, z);
+    tc::tmem_wait_st();
+  }
   const uint32_t idesc = tc::instr_desc(tc::kFmtTF32, tc::kFmtTF32, kRows, NM);
 
-  // per thread and block: A units (two K-adjacent core matrices of Dr and Di
-  // per warp pass) and B units (4 kk x 4 rhs of one part p)
-  const int a_units = (nc / 8) * (nc / 8);          // warp passes
-  const int b_units = (nc / 4) * 2 * (nrhs / 4);    // thread units
-  constexpr int kMaxA = 8, kMaxB = 2;               // nc <= 64, nrhs <= 64
-  float4 ra[kMaxA];
-  float4 rb[kMaxB][4];
-  auto load = [&](int k) {
-    const float4* D4 = reinterpret_cast<const float4*>(Dc + ((size_t)A * 9 + k) * nc * nc * 2);
-#pragma unroll
-    for (int j = 0; j < kMaxA; ++j) {
-      const int u = warp + 8 * j;
-      if (u < a_units) {
-        const int g8 = u / (nc / 8), kgp = u % (nc / 8);
-        const int row = 8 * g8 + ((lane >> 1) & 7);
-        const int col = (2 * kgp + (lane >> 4)) * 4 + 2 * (lane & 1);
-        ra[j] = __ldg(D4 + (row * nc + col) / 2);
-      }
-    }
+  // block k of the stencil: D_c[A][k] and x_c of its aggregate, one bulk copy each
+  auto fetch = [&](int k) {
+    unsigned char* raw = raw0 + (k & 1) * raw_bytes;
     const int B = k == 0 ? A : aggnbr[A * 8 + k - 1];
-#pragma unroll
-    for (int j = 0; j < kMaxB; ++j) {
-      const int u = threadIdx.x + kDcThreads * j;
-      if (u < b_units) {
-        const int rq = u % (nrhs / 4), p = (u / (nrhs / 4)) % 2, kq = u / (nrhs / 4) / 2;
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          rb[j][q] = __ldg(reinterpret_cast<const float4*>(x + (((size_t)B * nc + 4 * kq + q) * 2 + p) * nrhs + 4 * rq));
-      }
-    }
+    tc::mbar_expect_tx(&full[k & 1], d_bytes + x_bytes);
+    tc::bulk_g2s(raw, Dc + ((size_t)A * 9 + k) * nc * nc * 2, d_bytes, &full[k & 1]);
+    tc::bulk_g2s(raw + d_bytes, x + (size_t)B * nc * 2 * nrhs, x_bytes, &full[k & 1]);
   };
-  auto store = [&]() {
-#pragma unroll
-    for (int j = 0; j < kMaxA; ++j) {
-      const int u = warp + 8 * j;
-      if (u < a_units) {
-        const int g8 = u / (nc / 8), kgp = u % (nc / 8);
-        const int row = 8 * g8 + ((lane >> 1) & 7);
-        const int col = (2 * kgp + (lane >> 4)) * 4 + 2 * (lane & 1);
-        const uint32_t offr = tc::kmajor_offset(row, col, 4, KG), offi = tc::kmajor_offset(nc + row, col, 4, KG);
-        uint32_t h0, l0, h1, l1, h2, l2, h3, l3;
-        tf32_split(ra[j].x, h0, l0);  // Re D[row][col]
-        tf32_split(ra[j].y, h1, l1);  // Im D[row][col]
-        tf32_split(ra[j].z, h2, l2);  // Re D[row][col+1]
-        tf32_split(ra[j].w, h3, l3);  // Im D[row][col+1]
-        *reinterpret_cast<uint2*>(Ahi + offr) = make_uint2(h0, h2);
-        *reinterpret_cast<uint2*>(Ahi + offi) = make_uint2(h1, h3);
-        if (SPLIT) {
-          *reinterpret_cast<uint2*>(Alo + offr) = make_uint2(l0, l2);
-          *reinterpret_cast<uint2*>(Alo + offi) = make_uint2(l1, l3);
-        }
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < kMaxB; ++j) {
-      const int u = threadIdx.x + kDcThreads * j;
-      if (u < b_units) {
-        const int rq = u % (nrhs / 4), p = (u / (nrhs / 4)) % 2, kq = u / (nrhs / 4) / 2;
-        // transpose 4 (kk) x 4 (rhs): row n = p*nrhs + 4rq + c holds kk = 4kq .. 4kq+3
-        const float v[4][4] = {{rb[j][0].x, rb[j][0].y, rb[j][0].z, rb[j][0].w},
-                               {rb[j][1].x, rb[j][1].y, rb[j][1].z, rb[j][1].w},
-                               {rb[j][2].x, rb[j][2].y, rb[j][2].z, rb[j][2].w},
-                               {rb[j][3].x, rb[j][3].y, rb[j][3].z, rb[j][3].w}};
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const uint32_t off = tc::kmajor_offset(p * nrhs + 4 * rq + c, 4 * kq, 4, KG);
-          uint32_t h[4], l[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) tf32_split(v[q][c], h[q], l[q]);
-          *reinterpret_cast<uint4*>(Bhi + off) = make_uint4(h[0], h[1], h[2], h[3]);
-          if (SPLIT) *reinterpret_cast<uint4*>(Blo + off) = make_uint4(l[0], l[1], l[2], l[3]);
-        }
-      }
-    }
-  };
-
-  load(0);
+  if (tid == 0) {
+    fetch(0);
+    fetch(1);
+  }
   int issued = 0;
   for (int k = 0; k < 9; ++k) {
-    if (k >= 1 && !tc::mbar_wait(&mbar, (k - 1) & 1, kWaitLimit)) s_bad = 1;
+    const unsigned char* raw = raw0 + (k & 1) * raw_bytes;
+    bool ok = tc::mbar_wait(&full[k & 1], (k >> 1) & 1, kWaitLimit);
+    if (k >= 1) {
+      // block k-1 done: fold its partial sum R into S before R is reused
+      ok = ok && tc::mbar_wait(&mma_done, (k - 1) & 1, kWaitLimit);
+      tc::fence_after_sync();
+      tc::tmem_promote(t_own + NM, t_own, NM / 2);  // warp-wide; a failed wait discards the result
+      tc::tmem_wait_st();
+    }
+    if (!ok) s_bad = 1;
+    tc::fence_before_sync();
     __syncthreads();
     if (s_bad) break;
-    store();
-    if (k + 1 < 9) load(k + 1);
+    // A: 16-byte chunks q (two complex columns) of 8 rows per warp pass; lane
+    // (r, qq) takes chunk 8 qq + ((r + t) & 7) of row r, so that the eight
+    // lanes of a row group hit eight different bank groups
+    {
+      const float4* D4 = reinterpret_cast<const float4*>(raw);
+      const int r = lane & 7, qq = lane >> 3;
+      for (int pass = warp; pass < (nc / 8) * 8; pass += kDcThreads / 32) {
+        const int g8 = pass >> 3, t = pass & 7;
+        const int q = qq * 8 + ((r + t) & 7);
+        if (q < nc / 2) {
+          const int row = 8 * g8 + r, col = 2 * q;
+          const float4 v = D4[(row * nc + col) / 2];
+          const uint32_t offr = tc::kmajor_offset(row, col, 4, KG), offi = tc::kmajor_offset(nc + row, col, 4, KG);
+          uint32_t h0, l0, h1, l1, h2, l2, h3, l3;
+          tf32_split(v.x, h0, l0);  // Re D[row][col]
+          tf32_split(v.y, h1, l1);  // Im D[row][col]
+          tf32_split(v.z, h2, l2);  // Re D[row][col+1]
+          tf32_split(v.w, h3, l3);  // Im D[row][col+1]
+          *reinterpret_cast<uint2*>(Ahi + offr) = make_uint2(h0, h2);
+          *reinterpret_cast<uint2*>(Ahi + offi) = make_uint2(h1, h3);
+          if (SPLIT) {
+            *reinterpret_cast<uint2*>(Alo + offr) = make_uint2(l0, l2);
+            *reinterpret_cast<uint2*>(Alo + offi) = make_uint2(l1, l3);
+          }
+        }
+      }
+    }
+    // B: one 16-byte core row (row n = (p, r), K group kq) per unit, from four
+    // rows (kk, p) of the x block
+    {
+      const float* X = reinterpret_cast<const float*>(raw + d_bytes);
+      for (int u = tid; u < NM * KG; u += kDcThreads) {
+        const int n = u % NM, kq = u / NM;
+        const int p = n / nrhs, r = n % nrhs;
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) tf32_split(X[((4 * kq + j) * 2 + p) * nrhs + r], h[j], l[j]);
+        const uint32_t off = tc::kmajor_offset(n, 4 * kq, 4, KG);
+        *reinterpret_cast<uint4*>(Bhi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+        if (SPLIT) *reinterpret_cast<uint4*>(Blo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+      }
+    }
     tc::fence_async_smem();
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
+      if (k + 2 < 9) fetch(k + 2);  // the raw stage is free: every thread has converted it
       tc::fence_after_sync();
       const uint32_t ah = tc::smem_u32(Ahi), bh = tc::smem_u32(Bhi), al = tc::smem_u32(Alo), bl = tc::smem_u32(Blo);
       const uint32_t sbo = KG * 128;
       for (int ks = 0; ks < KG / 2; ++ks) {
         const uint32_t o = ks * 256;
         tc::mma_tf32(tbase, tc::smem_desc(ah + o, 128, sbo), tc::smem_desc(bh + o, 128, sbo), idesc,
-                     (k > 0 || ks > 0) ? 1u : 0u);
+                     ks > 0 ? 1u : 0u);
         if (SPLIT) {
           tc::mma_tf32(tbase, tc::smem_desc(ah + o, 128, sbo), tc::smem_desc(bl + o, 128, sbo), idesc, 1u);
           tc::mma_tf32(tbase, tc::smem_desc(al + o, 128, sbo), tc::smem_desc(bh + o, 128, sbo), idesc, 1u);
         }
       }
-      tc::mma_commit(&mbar);
+      tc::mma_commit(&mma_done);
     }
     issued = k + 1;
   }
-  if (issued > 0 && !tc::mbar_wait(&mbar, (issued - 1) & 1, kWaitLimit)) s_bad = 1;
-  tc::fence_after_sync();
+  if (issued > 0) {
+    if (!tc::mbar_wait(&mma_done, (issued - 1) & 1, kWaitLimit)) s_bad = 1;
+    tc::fence_after_sync();
+    tc::tmem_promote(t_own + NM, t_own, NM / 2);
+    tc::tmem_wait_st();
+  }
+  tc::fence_before_sync();
   __syncthreads();
+  tc::fence_after_sync();
   if (!s_bad && issued == 9) {
-    float* E = reinterpret_cast<float*>(smem);  // [128][NM + 1]
+    float* E = reinterpret_cast<float*>(smem);  // [128][NM + 1], over the (now idle) raw stages
     const int quarter = warp & 3, half = warp >> 2;
     const int ch = NM / 2;
     for (int col0 = half * ch; col0 < half * ch + ch; col0 += 16) {
       float v[16];
-      tc::tmem_ld16(tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)col0, v);
+      tc::tmem_ld16(tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(NM + col0), v);
       const int row = quarter * 32 + lane;
 #pragma unroll
       for (int i = 0; i < 16; ++i) E[row * (NM + 1) + col0 + i] = v[i];
     }
     __syncthreads();
     float* yA = y + (size_t)A * nc * 2 * nrhs;
-    for (int e = threadIdx.x; e < nc * 2 * nrhs; e += kDcThreads) {
+    for (int e = tid; e < nc * 2 * nrhs; e += kDcThreads) {
       const int r = e % nrhs, p = (e / nrhs) % 2, i = e / (2 * nrhs);
       const float v = p == 0 ? E[i * (NM + 1) + r] - E[(nc + i) * (NM + 1) + nrhs + r]
                              : E[i * (NM + 1) + nrhs + r] + E[(nc + i) * (NM + 1) + r];
       yA[e] = v;
     }
-  } else if (threadIdx.x == 0) {
-    atomicExch(err, 1);
+  } else {
+    // a wait ran out: let the copies still in flight land before the CTA's
+    // shared memory is released
+    if (tid == 0) {
+      atomicExch(err, 1);
+      for (int k = issued; k < 9 && k < issued + 2; ++k) tc::mbar_wait(&full[k & 1], (k >> 1) & 1, kWaitLimit);
+    }
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -430,38 +492,31 @@ __global__ void __launch_bounds__(kDcThreads) k_apply_dc_tc(const float* __restr
 
 }  // namespace
 
-// tensor-core contraction for the self and forward blocks of the mixed
-// setups; false when the shape is outside what the kernel handles
-bool build_Dc_tc(mrhs_ctx c, int fmt) {
+// tensor-core contraction for the self and forward blocks (split: tf32
+// operands as hi + lo parts, FP32 accuracy); false when the shape is outside
+// what the kernel handles
+bool build_Dc_tc(mrhs_ctx c, int fmt, bool split) {
   const int Nt = c->ntv, nc = 2 * Nt;
   if (c->work_dtype != MRHS_F32 || 2 * nc > kRows) return false;
   for (int m = 0; m < 4; ++m)
     if ((c->g.Va / c->g.a[m]) < 1) return false;
   Agg4 ag;
   for (int m = 0; m < 4; ++m) ag.a[m] = c->g.a[m];
-  const size_t smem = 4 * (size_t)kTileBytes;
+  split = split && fmt == tc::kFmtTF32;
+  const size_t smem = (split ? 8 : 4) * (size_t)kTileBytes;
   const cx<float>* U = (const cx<float>*)c->U32;
   const float* Acl = (const float*)c->A32;
   int* err = c->dflag + 2;
   MRHS_CUDA(cudaMemsetAsync(err, 0, sizeof(int), c->stream));
   Prof pr(c, "coarse_op_tc");
   MRHS_DISPATCH(c->tv_dtype, SP, {
-    if (fmt == tc::kFmtBF16) {
-      auto kern = k_coarse_op_tc<tc::kFmtBF16, SP>;
-      MRHS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      kern<<<c->g.nagg * 5, kThreads, smem, c->stream>>>((const SP*)c->P, U, Acl, c->nbr, Nt, ag, c->g.Va,
-                                                          (cx<float>*)c->Dc, err);
-    } else if (fmt == tc::kFmtF16) {
-      auto kern = k_coarse_op_tc<tc::kFmtF16, SP>;
-      MRHS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      kern<<<c->g.nagg * 5, kThreads, smem, c->stream>>>((const SP*)c->P, U, Acl, c->nbr, Nt, ag, c->g.Va,
-                                                          (cx<float>*)c->Dc, err);
-    } else {
-      auto kern = k_coarse_op_tc<tc::kFmtTF32, SP>;
-      MRHS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      kern<<<c->g.nagg * 5, kThreads, smem, c->stream>>>((const SP*)c->P, U, Acl, c->nbr, Nt, ag, c->g.Va,
-                                                          (cx<float>*)c->Dc, err);
-    }
+    auto kern = fmt == tc::kFmtBF16 ? k_coarse_op_tc<tc::kFmtBF16, SP, false>
+                : fmt == tc::kFmtF16 ? k_coarse_op_tc<tc::kFmtF16, SP, false>
+                : split              ? k_coarse_op_tc<tc::kFmtTF32, SP, true>
+                                     : k_coarse_op_tc<tc::kFmtTF32, SP, false>;
+    MRHS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<c->g.nagg * 5, kThreads, smem, c->stream>>>((const SP*)c->P, U, Acl, c->nbr, Nt, ag, c->g.Va,
+                                                        (cx<float>*)c->Dc, err);
   });
   MRHS_LAUNCH_CHECK("coarse_op_tc");
   int* h = c->hflag + 2;
@@ -478,9 +533,10 @@ bool apply_Dc_tc(mrhs_ctx c, const void* xc, void* yc, int nrhs, bool split) {
   if (c->work_dtype != MRHS_F32 || nc % 8 != 0 || nc > 64 || nrhs % 16 != 0 || nrhs > 64) return false;
   const int KG = nc / 4;
   const size_t tiles = (size_t)(kRows / 8 * KG * 128 + 2 * nrhs / 8 * KG * 128);
-  const size_t smem = std::max((split ? 2 : 1) * tiles, sizeof(float) * kRows * (2 * nrhs + 1));
+  const size_t raw = ((size_t)nc * nc * 8 + (size_t)nc * 2 * nrhs * 4 + 1023) & ~(size_t)1023;
+  const size_t smem = std::max(2 * raw, sizeof(float) * kRows * (2 * nrhs + 1)) + (split ? 2 : 1) * tiles;
   uint32_t cols = 32;
-  while (cols < (uint32_t)(2 * nrhs)) cols <<= 1;
+  while (cols < (uint32_t)(4 * nrhs)) cols <<= 1;  // R and S regions of 2 nrhs columns each
   int* err = c->dflag + 3;
   Prof pr(c, "apply_dc_tc");
   auto kern = split ? k_apply_dc_tc<true> : k_apply_dc_tc<false>;

@@ -264,7 +264,7 @@ void build_P(mrhs_ctx c);
 void build_Dc(mrhs_ctx c);
 // operand formats of the tensor-core contraction (tcgen05 instruction-descriptor codes)
 constexpr int tc_fmt_f16 = 0, tc_fmt_bf16 = 1, tc_fmt_tf32 = 2;
-bool build_Dc_tc(mrhs_ctx c, int fmt);
+bool build_Dc_tc(mrhs_ctx c, int fmt, bool split);
 // coarse stencil on the tensor cores; sets dflag[3] if a pipeline wait ran out
 bool apply_Dc_tc(mrhs_ctx c, const void* xc, void* yc, int nrhs, bool split);
 void check_tc_timeout(mrhs_ctx c);

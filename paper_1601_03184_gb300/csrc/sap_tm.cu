@@ -85,6 +85,7 @@ __device__ __forceinline__ void hop1(float ore[12], float oim[12], const float p
 struct Dom {
   const float2* sR;  // [12][Va][4] (re, im)
   const float4* sU;  // [20][Va+1]
+  const int* sN;     // [8][Va]: neighbour inside the domain (local index) or ~(device site) outside
   int Va, l, g;
   size_t s0;         // first device site of the domain
 };
@@ -124,25 +125,24 @@ __device__ __forceinline__ void load_u_glob(const float* __restrict__ U20, size_
 // hop (MU, DIR) at the item's site: inside the domain from shared memory;
 // outside (RESID only) from x and the links in global memory
 template <int MU, int DIR, bool RESID>
-__device__ __forceinline__ void hop_dom(const Dom& d, float ore[12], float oim[12], const int* __restrict__ nbr,
-                                        const float* __restrict__ x, const float* __restrict__ U20, int N, int r0) {
-  const int e = __ldg(nbr + (d.s0 + d.l) * 8 + (DIR > 0 ? 0 : 4) + MU);
-  const int n = e & 0x3fffffff;
-  const unsigned nl = (unsigned)(n - (int)d.s0);
+__device__ __forceinline__ void hop_dom(const Dom& d, float ore[12], float oim[12], const float* __restrict__ x,
+                                        const float* __restrict__ U20, int N, int r0) {
+  const int e = d.sN[((DIR > 0 ? 0 : 4) + MU) * d.Va + d.l];
   float pr[12], pi[12], u[18];
-  if (nl < (unsigned)d.Va) {
-    load_rho(d, (int)nl, pr, pi);
-    load_u_smem(d, DIR > 0 ? d.l : (int)nl, MU, u);
+  if (e >= 0) {
+    load_rho(d, e, pr, pi);
+    load_u_smem(d, DIR > 0 ? d.l : e, MU, u);
   } else {
     if (!RESID) return;
-    const float* xn = x + (size_t)n * 24 * N + r0 + d.g;
+    const size_t n = (size_t)(~e);
+    const float* xn = x + n * 24 * N + r0 + d.g;
 #pragma unroll
     for (int c = 0; c < 12; ++c) {
       pr[c] = xn[(2 * c) * N];
       pi[c] = xn[(2 * c + 1) * N];
     }
     if (DIR > 0) load_u_smem(d, d.l, MU, u);
-    else load_u_glob(U20, (size_t)n, MU, u);
+    else load_u_glob(U20, n, MU, u);
   }
   hop1<MU, DIR>(ore, oim, pr, pi, u);
 }
@@ -150,8 +150,7 @@ __device__ __forceinline__ void hop_dom(const Dom& d, float ore[12], float oim[1
 // out = D x (RESID) or D_B rho at the item's site
 template <bool RESID>
 __device__ __forceinline__ void apply_dom(const Dom& d, float ore[12], float oim[12], const float* __restrict__ Acl,
-                                          const int* __restrict__ nbr, const float* __restrict__ x,
-                                          const float* __restrict__ U20, int N, int r0) {
+                                          const float* __restrict__ x, const float* __restrict__ U20, int N, int r0) {
   {
     float pr[12], pi[12];
     load_rho(d, d.l, pr, pi);
@@ -182,14 +181,14 @@ __device__ __forceinline__ void apply_dom(const Dom& d, float ore[12], float oim
       }
     }
   }
-  hop_dom<0, +1, RESID>(d, ore, oim, nbr, x, U20, N, r0);
-  hop_dom<1, +1, RESID>(d, ore, oim, nbr, x, U20, N, r0);
-  hop_dom<2, +1, RESID>(d, ore, oim, nbr, x, U20, N, r0);
-  hop_dom<3, +1, RESID>(d, ore, oim, nbr, x, U20, N, r0);
-  hop_dom<0, -1, RESID>(d, ore, oim, nbr, x, U20, N, r0);
-  hop_dom<1, -1, RESID>(d, ore, oim, nbr, x, U20, N, r0);
-  hop_dom<2, -1, RESID>(d, ore, oim, nbr, x, U20, N, r0);
-  hop_dom<3, -1, RESID>(d, ore, oim, nbr, x, U20, N, r0);
+  hop_dom<0, +1, RESID>(d, ore, oim, x, U20, N, r0);
+  hop_dom<1, +1, RESID>(d, ore, oim, x, U20, N, r0);
+  hop_dom<2, +1, RESID>(d, ore, oim, x, U20, N, r0);
+  hop_dom<3, +1, RESID>(d, ore, oim, x, U20, N, r0);
+  hop_dom<0, -1, RESID>(d, ore, oim, x, U20, N, r0);
+  hop_dom<1, -1, RESID>(d, ore, oim, x, U20, N, r0);
+  hop_dom<2, -1, RESID>(d, ore, oim, x, U20, N, r0);
+  hop_dom<3, -1, RESID>(d, ore, oim, x, U20, N, r0);
 }
 
 // four consecutive right-hand sides of one row of b (16-byte / 8-byte load)
@@ -229,10 +228,11 @@ __global__ void __launch_bounds__(kMaxT, 1) k_sap_tm(const SB* __restrict__ b, f
                                                      int cpb) {
   extern __shared__ float4 smem4[];
   const int T = blockDim.x;
-  float4* sU = smem4;                                     // [20][Va+1]
-  float* sR = reinterpret_cast<float*>(sU + 20 * (Va + 1));  // [12][Va][4] x (re, im)
+  float4* sU = smem4;                                          // [20][Va+1]
+  float* sR = reinterpret_cast<float*>(sU + 20 * (Va + 1));   // [12][Va][4] x (re, im)
   float2* sR2 = reinterpret_cast<float2*>(sR);
-  float* sred = sR + 24 * Va * kG;                        // [T/32][4] float4 (pr, pi, pq, -)
+  float4* sred4 = reinterpret_cast<float4*>(sR + 24 * Va * kG);  // [T/32][4] (pr, pi, pq, -)
+  int* sN = reinterpret_cast<int*>(sred4 + (T / 32) * kG);     // [8][Va]
   __shared__ uint32_t s_tmem;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -243,6 +243,7 @@ __global__ void __launch_bounds__(kMaxT, 1) k_sap_tm(const SB* __restrict__ b, f
   d.s0 = (size_t)blist[blockIdx.x / cpb] * Va;
   d.sR = sR2;
   d.sU = sU;
+  d.sN = sN;
 
   if (warp == 0) {
     tc::tmem_alloc(&s_tmem, tm_cols);
@@ -251,14 +252,20 @@ __global__ void __launch_bounds__(kMaxT, 1) k_sap_tm(const SB* __restrict__ b, f
   {
     const float4* U4 = reinterpret_cast<const float4*>(U20) + d.s0 * 20;
     for (int i = tid; i < 20 * Va; i += T) sU[(i % 20) * (Va + 1) + i / 20] = __ldg(U4 + i);
+    for (int i = tid; i < 8 * Va; i += T) {
+      const int l = i >> 3, k = i & 7;
+      const int n = __ldg(nbr + (d.s0 + l) * 8 + k) & 0x3fffffff;
+      const int nl = n - (int)d.s0;
+      sN[k * Va + l] = (nl >= 0 && nl < Va) ? nl : ~n;
+    }
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   // lane quarter of the warp; warps w, w+4, w+8, w+12 share it and take
-  // disjoint column ranges
-  const uint32_t tm = s_tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * 2 * kColsItem);
-  const bool v0 = tid < nit, v1 = tid + T < nit;
+  // disjoint column ranges: x_B of item 0, x_B of item 1, q of item 0
+  const uint32_t tm = s_tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * 3 * kColsItem);
+  const uint32_t tmq = tm + 2 * kColsItem;
 
   for (int r0 = (blockIdx.x % cpb) * kG; r0 < N; r0 += cpb * kG) {
     // stage x0 into shared memory, one (component pair c, site l) per unit:
@@ -279,30 +286,32 @@ __global__ void __launch_bounds__(kMaxT, 1) k_sap_tm(const SB* __restrict__ b, f
     for (int j = 0; j < 2; ++j) {
       const int i = tid + j * T;
       float v[24];
-      if (i < nit) {
 #pragma unroll
-        for (int c = 0; c < 12; ++c) {
-          const float2 t = sR2[(c * Va + (i >> 2)) * kG + d.g];
-          v[2 * c] = t.x;
-          v[2 * c + 1] = t.y;
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < 24; ++k) v[k] = 0.f;
+      for (int c = 0; c < 12; ++c) {
+        const float2 t = i < nit ? sR2[(c * Va + (i >> 2)) * kG + d.g] : make_float2(0.f, 0.f);
+        v[2 * c] = t.x;
+        v[2 * c + 1] = t.y;
       }
       tm_put(tm + j * kColsItem, v);
     }
     tc::tmem_wait_st();
-    // D x0 for both items (registers)
-    float q0r[12], q0i[12], q1r[12], q1i[12];
-    if (v0) {
-      d.l = tid >> 2;
-      apply_dom<true>(d, q0r, q0i, Acl, nbr, x, U20, N, r0);
+    // D x0 item by item; q of item 0 waits in tensor memory, q of item 1 in registers
+    float qr[12], qi[12];
+#pragma unroll 1
+    for (int j = 0; j < 2; ++j) {
+      const int i = tid + j * T;
+      if (i < nit) {
+        d.l = i >> 2;
+        apply_dom<true>(d, qr, qi, Acl, x, U20, N, r0);
+      }
+      if (j == 0) {
+        float v[24];
+#pragma unroll
+        for (int c = 0; c < 12; ++c) v[2 * c] = qr[c], v[2 * c + 1] = qi[c];
+        tm_put(tmq, v);
+      }
     }
-    if (v1) {
-      d.l = (tid + T) >> 2;
-      apply_dom<true>(d, q1r, q1i, Acl, nbr, x, U20, N, r0);
-    }
+    tc::tmem_wait_st();
     __syncthreads();
     // stage b the same way as x0, then rho = b - D x0 item by item
     for (int u = tid; u < 12 * Va; u += T) {
@@ -316,49 +325,46 @@ __global__ void __launch_bounds__(kMaxT, 1) k_sap_tm(const SB* __restrict__ b, f
       dst[1] = make_float4(re[2], im[2], re[3], im[3]);
     }
     __syncthreads();
-    if (v0) {
-      const int l = tid >> 2;
+    {
+      float q0[24];
+      tm_get(tmq, q0);
 #pragma unroll
-      for (int c = 0; c < 12; ++c) {
-        const int ix = (c * Va + l) * kG + d.g;
-        const float2 bv = sR2[ix];
-        sR2[ix] = make_float2(bv.x - q0r[c], bv.y - q0i[c]);
-      }
-    }
-    if (v1) {
-      const int l = (tid + T) >> 2;
+      for (int j = 0; j < 2; ++j) {
+        const int i = tid + j * T;
+        if (i < nit) {
 #pragma unroll
-      for (int c = 0; c < 12; ++c) {
-        const int ix = (c * Va + l) * kG + d.g;
-        const float2 bv = sR2[ix];
-        sR2[ix] = make_float2(bv.x - q1r[c], bv.y - q1i[c]);
+          for (int c = 0; c < 12; ++c) {
+            const int ix = (c * Va + (i >> 2)) * kG + d.g;
+            const float2 bv = sR2[ix];
+            sR2[ix] = j == 0 ? make_float2(bv.x - q0[2 * c], bv.y - q0[2 * c + 1])
+                             : make_float2(bv.x - qr[c], bv.y - qi[c]);
+          }
+        }
       }
     }
     __syncthreads();
     for (int step = 0; step < n_mr; ++step) {
       float pr = 0.f, pi = 0.f, pq = 0.f;
-      if (v0) {
-        d.l = tid >> 2;
-        apply_dom<false>(d, q0r, q0i, Acl, nbr, x, U20, N, r0);
-        float rr[12], ri[12];
-        load_rho(d, d.l, rr, ri);
+#pragma unroll 1
+      for (int j = 0; j < 2; ++j) {
+        const int i = tid + j * T;
+        if (i < nit) {
+          d.l = i >> 2;
+          apply_dom<false>(d, qr, qi, Acl, x, U20, N, r0);
+          float rr[12], ri[12];
+          load_rho(d, d.l, rr, ri);
 #pragma unroll
-        for (int c = 0; c < 12; ++c) {
-          pr = fmaf(q0r[c], rr[c], fmaf(q0i[c], ri[c], pr));
-          pi = fmaf(q0r[c], ri[c], fmaf(-q0i[c], rr[c], pi));
-          pq = fmaf(q0r[c], q0r[c], fmaf(q0i[c], q0i[c], pq));
+          for (int c = 0; c < 12; ++c) {
+            pr = fmaf(qr[c], rr[c], fmaf(qi[c], ri[c], pr));
+            pi = fmaf(qr[c], ri[c], fmaf(-qi[c], rr[c], pi));
+            pq = fmaf(qr[c], qr[c], fmaf(qi[c], qi[c], pq));
+          }
         }
-      }
-      if (v1) {
-        d.l = (tid + T) >> 2;
-        apply_dom<false>(d, q1r, q1i, Acl, nbr, x, U20, N, r0);
-        float rr[12], ri[12];
-        load_rho(d, d.l, rr, ri);
+        if (j == 0) {
+          float v[24];
 #pragma unroll
-        for (int c = 0; c < 12; ++c) {
-          pr = fmaf(q1r[c], rr[c], fmaf(q1i[c], ri[c], pr));
-          pi = fmaf(q1r[c], ri[c], fmaf(-q1i[c], rr[c], pi));
-          pq = fmaf(q1r[c], q1r[c], fmaf(q1i[c], q1i[c], pq));
+          for (int c = 0; c < 12; ++c) v[2 * c] = qr[c], v[2 * c + 1] = qi[c];
+          tm_put(tmq, v);
         }
       }
       // sums over the lanes of the same rhs (lane % 4), then over warps:
@@ -370,8 +376,8 @@ __global__ void __launch_bounds__(kMaxT, 1) k_sap_tm(const SB* __restrict__ b, f
         pi += __shfl_xor_sync(0xffffffffu, pi, o);
         pq += __shfl_xor_sync(0xffffffffu, pq, o);
       }
-      float4* sred4 = reinterpret_cast<float4*>(sred);
       if (lane < kG) sred4[warp * kG + lane] = make_float4(pr, pi, pq, 0.f);
+      tc::tmem_wait_st();
       __syncthreads();
       float a = 0.f, bb = 0.f, cc = 0.f;
       for (int w = 0; w < T / 32; ++w) {
@@ -382,23 +388,24 @@ __global__ void __launch_bounds__(kMaxT, 1) k_sap_tm(const SB* __restrict__ b, f
       }
       const cx<float> al = cc > 0.f ? mk(a / cc, bb / cc) : mk(0.f, 0.f);
       // x_B += alpha rho (tensor memory), rho -= alpha q (shared memory)
+      float q0[24];
+      tm_get(tmq, q0);
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         float xv[24];
         tm_get(tm + j * kColsItem, xv);
-        const bool vj = j == 0 ? v0 : v1;
-        if (vj) {
-          const int l = (tid + j * T) >> 2;
+        const int i = tid + j * T;
+        if (i < nit) {
 #pragma unroll
           for (int c = 0; c < 12; ++c) {
-            const int i0 = (c * Va + l) * kG + d.g;
+            const int i0 = (c * Va + (i >> 2)) * kG + d.g;
             const float2 r2 = sR2[i0];
             cx<float> rv = mk(r2.x, r2.y);
             cx<float> xc = mk(xv[2 * c], xv[2 * c + 1]);
             fma_(xc, al, rv);
             xv[2 * c] = xc.re;
             xv[2 * c + 1] = xc.im;
-            const cx<float> qv = j == 0 ? mk(-q0r[c], -q0i[c]) : mk(-q1r[c], -q1i[c]);
+            const cx<float> qv = j == 0 ? mk(-q0[2 * c], -q0[2 * c + 1]) : mk(-qr[c], -qi[c]);
             fma_(rv, al, qv);
             sR2[i0] = make_float2(rv.re, rv.im);
           }
@@ -706,7 +713,8 @@ static int sap_tm_threads(int Va, int G) { return G == 4 ? 128 * ((kG * Va + 255
 
 static size_t sap_tm_smem(int Va, int T, int G) {
   if (G == 4)
-    return sizeof(float4) * 20 * (size_t)(Va + 1) + sizeof(float) * ((size_t)24 * Va * kG + (T / 32) * kG * 4);
+    return sizeof(float4) * 20 * (size_t)(Va + 1) + sizeof(float) * ((size_t)24 * Va * kG + (T / 32) * kG * 4) +
+           sizeof(int) * 8 * (size_t)Va;
   return sizeof(float4) * 38 * (size_t)(Va + 1) + sizeof(int) * 8 * (size_t)Va +
          sizeof(float) * ((size_t)24 * Va * kG2 + (T / 32) * kG2 * 3 + 2 * kG2);
 }
@@ -740,9 +748,10 @@ void sap_tm(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int n_swee
   const int G = sap_tm_width(c, nrhs);
   const int T = sap_tm_threads(Va, G);
   const size_t smem = sap_tm_smem(Va, T, G);
-  // columns: (T/128) warpgroups x items per thread x 24, rounded up to a power of two >= 32
+  // columns: (T/128) warpgroups x 24 per item (G = 4: two items and the
+  // stashed q of the first), rounded up to a power of two >= 32
   uint32_t cols = 32;
-  while (cols < (uint32_t)(T / 128) * (G == 4 ? 2 : 1) * kColsItem) cols <<= 1;
+  while (cols < (uint32_t)(T / 128) * (G == 4 ? 3 : 1) * kColsItem) cols <<= 1;
   // CTAs per domain: by default one chunk of G right-hand sides each, so that
   // the CTAs of a domain run side by side and share every 32-byte sector of
   // x and b in L2 (MRHS_SAP_CPB overrides, 1 = one CTA loops over the chunks)

@@ -167,5 +167,45 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8]) {
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float v[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
+      "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
+      "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+      : "memory");
+}
+
+// S += R for the thread's row and columns col0 .. col0+ncols-1 (multiple of
+// 16) of two accumulator regions: the tensor core's own accumulation is
+// summed here in round-to-nearest FP32 chunk by chunk, so that long K sums do
+// not carry the rounding of the MMA accumulator
+__device__ __forceinline__ void tmem_promote(uint32_t s_addr, uint32_t r_addr, int ncols) {
+  for (int c = 0; c < ncols; c += 16) {
+    float a[16], b[16];
+    tmem_ld16(s_addr + c, a);
+    tmem_ld16(r_addr + c, b);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) a[i] += b[i];
+    tmem_st16(s_addr + c, a);
+  }
+}
+
+// ---- bulk (non-tensor) asynchronous copy, global -> shared ------------------
+// the producer announces the bytes on the mbarrier (this is its arrival) and
+// the copies complete the transaction count; 16-byte aligned, size % 16 == 0
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
 }  // namespace tc
 }  // namespace mrhs

@@ -3,7 +3,8 @@ against the FP64 oracle evaluated on the same P.
 
 The tensor-core path computes C = P^dag Y with Y = D_k P (FP32 on the CUDA
 cores) rounded to the operand type (unit roundoff u: bf16 2^-8, fp16 and tf32
-2^-11), P rounded to it as well (exact when P is stored in bf16 / fp16), and
+2^-11, split tf32 2^-21 for the sum of the three partial products), P rounded
+to it as well (exact when P is stored in bf16 / fp16), and
 FP32 accumulation over the K = 2 * 12 * |block| real products. Each entry
 therefore obeys
   |C_gpu[i][j] - C[i][j]| <= (2u + K 2^-24 + e_Y) sum_n |P_ni| |Y_nj|
@@ -22,6 +23,7 @@ import pytest
 import oracle
 from lattice_helpers import aggregate_of_sites
 from paper_1601_03184_gb300 import (MRHS_DC_ALU, MRHS_DC_AUTO, MRHS_DC_TC_BF16, MRHS_DC_TC_F16, MRHS_DC_TC_TF32,
+                                    MRHS_DC_TC_TF32X3,
                                     MRHS_ERR_SHAPE, MRHS_F32, MRHS_PREC_FP32, MRHS_PREC_FP64, MRHS_PREC_MIX_BF16,
                                     MRHS_PREC_MIX_FP16, Lattice, MrhsError, inputs)
 
@@ -42,6 +44,9 @@ ENGINES = {
     "fp32-bf16": (MRHS_PREC_FP32, MRHS_DC_TC_BF16, 2.0 ** -8),
     "fp32-f16": (MRHS_PREC_FP32, MRHS_DC_TC_F16, 2.0 ** -11),
     "fp32-tf32": (MRHS_PREC_FP32, MRHS_DC_TC_TF32, 2.0 ** -11),
+    # split tf32 (hi + lo parts): each operand to 2^-22, the dropped lo*lo term below 2^-22
+    "fp32-tf32x3": (MRHS_PREC_FP32, MRHS_DC_TC_TF32X3, 2.0 ** -21),
+    "fp32-auto": (MRHS_PREC_FP32, MRHS_DC_AUTO, 2.0 ** -21),
 }
 
 
