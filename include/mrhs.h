@@ -180,12 +180,13 @@ int mrhs_build_P(mrhs_ctx ctx);
 int mrhs_build_Dc(mrhs_ctx ctx);
 
 /* Engine of the contraction P^dag (D P) inside mrhs_build_Dc (the dense
- * 2ntv x 2ntv coarse-link products). AUTO: FP64 CUDA cores for the FP64
- * context; tensor cores (tcgen05, FP32 accumulation) otherwise: split tf32
- * (every operand as hi + lo tf32 parts, products hi*hi + hi*lo + lo*hi, FP32
- * accuracy) for FP32, bf16 operands for MIX_BF16, tf32 for MIX_FP16. ALU:
+ * 2ntv x 2ntv coarse-link products). AUTO: CUDA cores for the FP64 and FP32
+ * contexts; tensor cores (tcgen05, FP32 accumulation) for the mixed ones:
+ * bf16 operands for MIX_BF16, tf32 for MIX_FP16. ALU:
  * always the CUDA cores. TC_BF16 / TC_F16 / TC_TF32: the tensor cores with
- * that operand type (P and D P rounded to it); TC_TF32X3: split tf32. The
+ * that operand type (P and D P rounded to it); TC_TF32X3: split tf32 (every
+ * operand as hi + lo tf32 parts, products hi*hi + hi*lo + lo*hi, FP32
+ * accuracy). The
  * tensor-core forms need FP32 work fields (prec FP32 or mixed) and
  * 2*ntv <= 64; mrhs_build_Dc returns MRHS_ERR_SHAPE otherwise,
  * MRHS_ERR_TIMEOUT if a bounded wait of the tensor-core pipeline ran out.

@@ -73,9 +73,9 @@ __device__ __forceinline__ void tf32_split(float v, uint32_t& hi, uint32_t& lo) 
 
 // store the pair of elements (row, k), (row, k+1), k even, of a K-major tile
 template <int FMT>
-__device__ __forceinline__ void put2(unsigned char* tile, int row, int k, float a, float b) {
+__device__ __forceinline__ void put2(unsigned char* tile, int row, int k, float a, float b, int kg = kKG) {
   using E = Elem<FMT>;
-  const uint32_t off = tc::kmajor_offset(row, k, E::size, kKG);
+  const uint32_t off = tc::kmajor_offset(row, k, E::size, kg);
   if constexpr (E::size == 2) {
     *reinterpret_cast<uint32_t*>(tile + off) = E::pack(a, b);
   } else {
@@ -84,8 +84,9 @@ __device__ __forceinline__ void put2(unsigned char* tile, int row, int k, float 
 }
 
 // the same for split tf32: v = hi + lo, hi into one tile and lo into the other
-__device__ __forceinline__ void put2_split(unsigned char* thi, unsigned char* tlo, int row, int k, float a, float b) {
-  const uint32_t off = tc::kmajor_offset(row, k, 4, kKG);
+__device__ __forceinline__ void put2_split(unsigned char* thi, unsigned char* tlo, int row, int k, float a, float b,
+                                           int kg) {
+  const uint32_t off = tc::kmajor_offset(row, k, 4, kg);
   uint32_t ha, la, hb, lb;
   tf32_split(a, ha, la);
   tf32_split(b, hb, lb);
@@ -99,7 +100,11 @@ __global__ void __launch_bounds__(kThreads) k_coarse_op_tc(const SP* __restrict_
                                                            int Nt, Agg4 ag, int Va, cx<float>* __restrict__ Dc,
                                                            int* __restrict__ err) {
   constexpr int ES = Elem<FMT>::size;
-  constexpr int Q = kKG * 16 / ES / 12;       // sites per chunk: 8 (2-byte) or 4 (tf32)
+  // 16-byte K groups per chunk: 12, or 6 for split tf32 so that two CTAs
+  // (four tiles per stage each) still share an SM
+  constexpr int KGT = SPLIT ? kKG / 2 : kKG;
+  constexpr int TB = kRows / 8 * KGT * 128;    // bytes of one tile
+  constexpr int Q = KGT * 16 / ES / 12;        // sites per chunk: 8 (2-byte), 4 (tf32), 2 (split tf32)
   constexpr int KSTEP_BYTES = 256;            // two core matrices along K per MMA
   extern __shared__ __align__(1024) unsigned char smem[];
   // stage st: A tile at smem + 2*st*kTileBytes, B tile right after it
@@ -117,7 +122,7 @@ __global__ void __launch_bounds__(kThreads) k_coarse_op_tc(const SP* __restrict_
 
   // zero both stages once: padding rows and off-chirality entries of A stay zero
   constexpr int NT = SPLIT ? 4 : 2;  // tiles per stage: A, B (and their low parts)
-  for (int i = threadIdx.x; i < 2 * NT * kTileBytes / 16; i += kThreads)
+  for (int i = threadIdx.x; i < 2 * NT * TB / 16; i += kThreads)
     reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
   if (threadIdx.x == 0) {
     tc::mbar_init(&mbar[0], 1);
@@ -156,10 +161,10 @@ __global__ void __launch_bounds__(kThreads) k_coarse_op_tc(const SP* __restrict_
     if (s_bad) break;
     const int q0 = t * Q;
     const int nq = min(Q, nsite - q0);
-    unsigned char* tA = smem + NT * st * kTileBytes;
-    unsigned char* tB = tA + kTileBytes;
-    unsigned char* tAl = tA + 2 * kTileBytes;  // low parts (SPLIT)
-    unsigned char* tBl = tA + 3 * kTileBytes;
+    unsigned char* tA = smem + NT * st * TB;
+    unsigned char* tB = tA + TB;
+    unsigned char* tAl = tA + 2 * TB;  // low parts (SPLIT)
+    unsigned char* tBl = tA + 3 * TB;
     // B: Y = D_k P for (site q, column col); absent sites of a ragged chunk give zeros
     for (int w = threadIdx.x; w < Q * nc; w += kThreads) {
       const int q = w / nc, col = w % nc;
@@ -191,8 +196,8 @@ __global__ void __launch_bounds__(kThreads) k_coarse_op_tc(const SP* __restrict_
 #pragma unroll
       for (int c = 0; c < 12; c += 2) {
         if constexpr (SPLIT) {
-          put2_split(tB, tBl, col, q * 12 + c, out[c].re, out[c + 1].re);
-          put2_split(tB, tBl, nc + col, q * 12 + c, out[c].im, out[c + 1].im);
+          put2_split(tB, tBl, col, q * 12 + c, out[c].re, out[c + 1].re, KGT);
+          put2_split(tB, tBl, nc + col, q * 12 + c, out[c].im, out[c + 1].im, KGT);
         } else {
           put2<FMT>(tB, col, q * 12 + c, out[c].re, out[c + 1].re);
           put2<FMT>(tB, nc + col, q * 12 + c, out[c].im, out[c + 1].im);
@@ -214,7 +219,7 @@ __global__ void __launch_bounds__(kThreads) k_coarse_op_tc(const SP* __restrict_
       const size_t s = (size_t)A * Va + l;
       const float a = to_r(P[((s * 12 + c) * 2 + p) * Nt + j]);
       const float b = to_r(P[((s * 12 + c + 1) * 2 + p) * Nt + j]);
-      if constexpr (SPLIT) put2_split(tA, tAl, p * nc + h * Nt + j, q * 12 + c, a, b);
+      if constexpr (SPLIT) put2_split(tA, tAl, p * nc + h * Nt + j, q * 12 + c, a, b, KGT);
       else put2<FMT>(tA, p * nc + h * Nt + j, q * 12 + c, a, b);
     }
     tc::fence_async_smem();
@@ -233,14 +238,14 @@ __global__ void __launch_bounds__(kThreads) k_coarse_op_tc(const SP* __restrict_
       const uint32_t a0 = tc::smem_u32(tA), b0 = tc::smem_u32(tB);
       const uint32_t a1 = tc::smem_u32(tAl), b1 = tc::smem_u32(tBl);
 #pragma unroll
-      for (int ks = 0; ks < kKG / 2; ++ks) {
-        const uint64_t ad = tc::smem_desc(a0 + ks * KSTEP_BYTES, 128, kKG * 128);
-        const uint64_t bd = tc::smem_desc(b0 + ks * KSTEP_BYTES, 128, kKG * 128);
+      for (int ks = 0; ks < KGT / 2; ++ks) {
+        const uint64_t ad = tc::smem_desc(a0 + ks * KSTEP_BYTES, 128, KGT * 128);
+        const uint64_t bd = tc::smem_desc(b0 + ks * KSTEP_BYTES, 128, KGT * 128);
         if constexpr (FMT == tc::kFmtTF32) {
           tc::mma_tf32(tbase, ad, bd, idesc, ks > 0 ? 1u : 0u);
           if constexpr (SPLIT) {
-            tc::mma_tf32(tbase, ad, tc::smem_desc(b1 + ks * KSTEP_BYTES, 128, kKG * 128), idesc, 1u);
-            tc::mma_tf32(tbase, tc::smem_desc(a1 + ks * KSTEP_BYTES, 128, kKG * 128), bd, idesc, 1u);
+            tc::mma_tf32(tbase, ad, tc::smem_desc(b1 + ks * KSTEP_BYTES, 128, KGT * 128), idesc, 1u);
+            tc::mma_tf32(tbase, tc::smem_desc(a1 + ks * KSTEP_BYTES, 128, KGT * 128), bd, idesc, 1u);
           }
         } else {
           tc::mma_f16(tbase, ad, bd, idesc, ks > 0 ? 1u : 0u);
@@ -503,7 +508,7 @@ bool build_Dc_tc(mrhs_ctx c, int fmt, bool split) {
   Agg4 ag;
   for (int m = 0; m < 4; ++m) ag.a[m] = c->g.a[m];
   split = split && fmt == tc::kFmtTF32;
-  const size_t smem = (split ? 8 : 4) * (size_t)kTileBytes;
+  const size_t smem = 4 * (size_t)kTileBytes;  // two stages of 2 tiles, or of 4 half-size tiles (split)
   const cx<float>* U = (const cx<float>*)c->U32;
   const float* Acl = (const float*)c->A32;
   int* err = c->dflag + 2;

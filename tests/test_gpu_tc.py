@@ -46,7 +46,6 @@ ENGINES = {
     "fp32-tf32": (MRHS_PREC_FP32, MRHS_DC_TC_TF32, 2.0 ** -11),
     # split tf32 (hi + lo parts): each operand to 2^-22, the dropped lo*lo term below 2^-22
     "fp32-tf32x3": (MRHS_PREC_FP32, MRHS_DC_TC_TF32X3, 2.0 ** -21),
-    "fp32-auto": (MRHS_PREC_FP32, MRHS_DC_AUTO, 2.0 ** -21),
 }
 
 
