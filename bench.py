@@ -45,6 +45,10 @@ CONFIGS = {
     "16x16x16x32_ntv20": dict(dims=(16, 16, 16, 32), agg=(4, 4, 4, 4), ntv=20, eps=0.6, csw=1.5, gseed=1002,
                               tvseed=2002, m0_keys=["c2_16x16x16x32_eps0.6_csw1.5_seed1002",
                                                     "proxy_12x12x12x12_eps0.6_csw1.5_seed1002"]),
+    # the 48^3x96 workload's physics and N_tv on a small volume (profiler captures)
+    "16x16x16x32_ntv32": dict(dims=(16, 16, 16, 32), agg=(4, 4, 4, 4), ntv=32, eps=0.6, csw=1.7, gseed=1005,
+                              tvseed=2005, m0_keys=["c5proxy_16x16x16x32_eps0.6_csw1.7_seed1005",
+                                                    "proxy_12x12x12x12_eps0.6_csw1.7_seed1005"]),
 }
 DEFAULT_CONFIG = "48x48x48x96_ntv32"
 SCHEDULE = dict(init_sweeps=5, init_mr=4, n_refine=3, smooth_sweeps=4, smooth_mr=4, coarse_tol=0.05,

@@ -78,17 +78,27 @@ __global__ void __launch_bounds__(kBlock) k_multi_dot(const S* X, size_t stride,
   }
 }
 
+// out[k][r] = sum over the chunks of part[k][chunk][r]: one warp per (k, r),
+// lane l adds chunks l, l+32, ... and the lanes are joined by a fixed
+// butterfly, so the order of the sum does not depend on timing
 __global__ void k_sum_chunks(const double* part, int K, int nchunk, int N, double* out) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (t >= K * N) return;
-  int k = t / N, r = t % N;
+  const int k = t / N, r = t % N;
   double a = 0, b = 0;
-  for (int ch = 0; ch < nchunk; ++ch) {
+  for (int ch = lane; ch < nchunk; ch += 32) {
     a += part[(((size_t)k * nchunk + ch) * N + r) * 2];
     b += part[(((size_t)k * nchunk + ch) * N + r) * 2 + 1];
   }
-  out[2 * t] = a;
-  out[2 * t + 1] = b;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if (lane == 0) {
+    out[2 * t] = a;
+    out[2 * t + 1] = b;
+  }
 }
 
 // coefficients sign*coef in the compute precision, once per (k, r)
@@ -148,7 +158,7 @@ void multi_dot(mrhs_ctx c, const void* X, size_t stride, int K, const void* Y, s
   Prof pr(c, "multi_dot");
   MRHS_DISPATCH(dtype, S, (k_multi_dot<S><<<grid, kBlock, 0, c->stream>>>((const S*)X, stride, K, (const S*)Y, rows, N, nch, part)));
   MRHS_LAUNCH_CHECK("multi_dot");
-  k_sum_chunks<<<grid_for((size_t)K * N, 128), 128, 0, c->stream>>>(part, K, nch, N, out);
+  k_sum_chunks<<<grid_for((size_t)K * N * 32, 256), 256, 0, c->stream>>>(part, K, nch, N, out);
   MRHS_LAUNCH_CHECK("sum_chunks");
 }
 
@@ -166,7 +176,7 @@ void multi_dot_ws(mrhs_ctx c, const void* X, size_t stride, int K, const void* Y
   Prof pr(c, "multi_dot");
   MRHS_DISPATCH(dtype, S, (k_multi_dot<S><<<grid, kBlock, 0, c->stream>>>((const S*)X, stride, K, (const S*)Y, rows, N, nch, part)));
   MRHS_LAUNCH_CHECK("multi_dot");
-  k_sum_chunks<<<grid_for((size_t)K * N, 128), 128, 0, c->stream>>>(part, K, nch, N, out);
+  k_sum_chunks<<<grid_for((size_t)K * N * 32, 256), 256, 0, c->stream>>>(part, K, nch, N, out);
   MRHS_LAUNCH_CHECK("sum_chunks");
 }
 
