@@ -132,6 +132,22 @@ class ClockSampler:
 
 
 # ------------------------------------------------------- algorithmic work ---
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch from
+# the ncu captures summarised in profiles/ (16x16x16x32, N_tv = 32), scaled by
+# the number of sites; None for a kernel whose code changed since its capture
+NCU_TRAFFIC = {
+    "sap_tm": {"bytes": 903.34e6, "sites": 16 * 16 * 16 * 32, "ntv": 32,
+               "profile": "profiles/k_sap_tm_16x16x16x32_ntv32.md"},
+}
+
+
+def ncu_traffic(name, cfg):
+    t = NCU_TRAFFIC.get(name)
+    if t is None or t["ntv"] != cfg["ntv"]:
+        return None
+    return t["bytes"] * int(np.prod(cfg["dims"])) / t["sites"]
+
+
 def kernel_work(name, cfg, launches_per_step, bytes_f=4):
     """Algorithmic bytes and flops of ONE launch of a kernel class for the
     benchmark workload (each operand touched once)."""
@@ -334,12 +350,13 @@ def run_ours(args, cfg, cfg_name, m0, m0_src, rank, world, local_rank):
             alu_ach = fl / avg_ms / 1e9
             if hbm_ach / hbm_peak >= alu_ach / alu_peak:
                 roof = {"kernel": top, "bound": "hbm", "achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s",
-                        "frac": hbm_ach / hbm_peak, "traffic": None, "peak_source": hbm_src,
+                        "frac": hbm_ach / hbm_peak, "traffic": ncu_traffic(top, cfg), "peak_source": hbm_src,
                         "alu_frac": alu_ach / alu_peak, "avg_launch_ms": avg_ms, "bytes_per_launch": byt,
                         "flops_per_launch": fl}
             else:
                 roof = {"kernel": top, "bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s",
-                        "frac": alu_ach / alu_peak, "traffic": None,
+                        "frac": alu_ach / alu_peak, "traffic": ncu_traffic(top, cfg),
+                        "traffic_source": NCU_TRAFFIC.get(top, {}).get("profile"),
                         "peak_source": "FP32: SMs x 128 lanes x 2 flop x median SM clock under load",
                         "hbm_frac": hbm_ach / hbm_peak, "avg_launch_ms": avg_ms, "bytes_per_launch": byt,
                         "flops_per_launch": fl, "arith_intensity": ai}
