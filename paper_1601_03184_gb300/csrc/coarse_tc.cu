@@ -65,11 +65,7 @@ struct Elem<tc::kFmtTF32> {
   }
 };
 
-__device__ __forceinline__ void tf32_split(float v, uint32_t& hi, uint32_t& lo) {
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(v));
-  const float r = v - __uint_as_float(hi);
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(r));
-}
+using tc::tf32_split;
 
 // store the pair of elements (row, k), (row, k+1), k even, of a K-major tile
 template <int FMT>
@@ -308,7 +304,7 @@ __global__ void __launch_bounds__(kThreads) k_coarse_op_tc(const SP* __restrict_
 // accuracy; without SPLIT the operands are rounded to tf32 once.
 // The global loads of block k+1 are issued before the MMAs of block k are
 // waited for; two CTAs share an SM.
-constexpr int kDcThreads = 256;
+constexpr int kDcThreads = 512;  // 16 warps: the operand conversion is the CUDA cores' share
 
 template <bool SPLIT>
 __global__ void __launch_bounds__(kDcThreads, 1) k_apply_dc_tc(const float* __restrict__ Dc,
@@ -355,12 +351,18 @@ __global__ void __launch_bounds__(kDcThreads, 1) k_apply_dc_tc(const float* __re
   // the blocks, kept by the CUDA cores (warp w: lanes 32 (w % 4).., columns
   // (NM/2) (w / 4)..)
   const uint32_t tbase = s_tmem;
-  const uint32_t t_own = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((NM / 2) * (warp >> 2));
+  // column slices of 16 (or more) per warp group: warp w takes lanes
+  // 32 (w % 4).. and slice w / 4 (warp groups beyond the slices idle here)
+  const int nslice = min(kDcThreads / 128, NM / 16);
+  const int sw = NM / nslice;                              // columns per slice
+  const int slice = warp >> 2;
+  const int own = slice < nslice ? sw : 0;
+  const uint32_t t_own = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(sw * min(slice, nslice - 1));
   {
     float z[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) z[i] = 0.f;
-    for (int c0 = 0; c0 < NM / 2; c0 += 16) tc::tmem_st16(t_own + NM + c0, z);
+    for (int c0 = 0; c0 < own; c0 += 16) tc::tmem_st16(t_own + NM + c0, z);
     tc::tmem_wait_st();
   }
   const uint32_t idesc = tc::instr_desc(tc::kFmtTF32, tc::kFmtTF32, kRows, NM);
@@ -385,7 +387,7 @@ __global__ void __launch_bounds__(kDcThreads, 1) k_apply_dc_tc(const float* __re
       // block k-1 done: fold its partial sum R into S before R is reused
       ok = ok && tc::mbar_wait(&mma_done, (k - 1) & 1, kWaitLimit);
       tc::fence_after_sync();
-      tc::tmem_promote(t_own + NM, t_own, NM / 2);  // warp-wide; a failed wait discards the result
+      tc::tmem_promote(t_own + NM, t_own, own);  // warp-wide; a failed wait discards the result
       tc::tmem_wait_st();
     }
     if (!ok) s_bad = 1;
@@ -457,7 +459,7 @@ __global__ void __launch_bounds__(kDcThreads, 1) k_apply_dc_tc(const float* __re
   if (issued > 0) {
     if (!tc::mbar_wait(&mma_done, (issued - 1) & 1, kWaitLimit)) s_bad = 1;
     tc::fence_after_sync();
-    tc::tmem_promote(t_own + NM, t_own, NM / 2);
+    tc::tmem_promote(t_own + NM, t_own, own);
     tc::tmem_wait_st();
   }
   tc::fence_before_sync();
@@ -465,9 +467,8 @@ __global__ void __launch_bounds__(kDcThreads, 1) k_apply_dc_tc(const float* __re
   tc::fence_after_sync();
   if (!s_bad && issued == 9) {
     float* E = reinterpret_cast<float*>(smem);  // [128][NM + 1], over the (now idle) raw stages
-    const int quarter = warp & 3, half = warp >> 2;
-    const int ch = NM / 2;
-    for (int col0 = half * ch; col0 < half * ch + ch; col0 += 16) {
+    const int quarter = warp & 3;
+    for (int col0 = slice * sw; col0 < slice * sw + own; col0 += 16) {
       float v[16];
       tc::tmem_ld16(tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(NM + col0), v);
       const int row = quarter * 32 + lane;
