@@ -150,7 +150,7 @@ def ncu_traffic(name, cfg):
 
 def kernel_work(name, cfg, launches_per_step, bytes_f=4):
     """Algorithmic bytes and flops of ONE launch of a kernel class for the
-    benchmark workload (each operand touched once; see DESIGN.md)."""
+    benchmark workload (each operand touched once)."""
     V = int(np.prod(cfg["dims"]))
     N = cfg["ntv"]
     spin = 24 * bytes_f           # one spinor, one rhs
@@ -368,11 +368,11 @@ def run_ours(args, cfg, cfg_name, m0, m0_src, rank, world, local_rank):
     if not args.no_e2e:
         e2e = run_e2e(args, lat, U, tv0, cfg, m0, stream)
 
-    # ---- the judge of the plain setup: two-level FGMRES to 1e-10
+    # ---- the quality check of the plain setup: two-level FGMRES to 1e-10
     fg_plain = None
     if not args.no_fgmres:
         pkg.mrhs_trim(lat.ctx)
-        fg_plain = fgmres_judge(lat, cfg)
+        fg_plain = fgmres_check(lat, cfg)
     gpu_launches = int(sum(v[0] for v in prof.values()) / args.steps)
     line = {
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -407,7 +407,7 @@ def run_ours(args, cfg, cfg_name, m0, m0_src, rank, world, local_rank):
         dist.destroy_process_group()
 
 
-def fgmres_judge(lat, cfg, seed=3005):
+def fgmres_check(lat, cfg, seed=3005):
     """Two-level FGMRES (FP64 outer, restart 10) on a Gaussian right-hand side to
     relative residual 1e-10 with the context's current setup."""
     b = None
@@ -485,7 +485,7 @@ def run_learned_mixed(args, cfg, U, m0, stream, plain_ms, barrier):
     fg = None
     if not args.no_fgmres:
         pkg.mrhs_trim(lat.ctx)
-        fg = fgmres_judge(lat, cfg)
+        fg = fgmres_check(lat, cfg)
     lat.close()
     return {"value": lm_ms / 1000.0, "unit": "s", "ratio_vs_plain": lm_ms / plain_ms,
             "form": "1 SAP sweep + network (widths %s, bf16 weights) for the initial phase, bf16 test vectors and P, "

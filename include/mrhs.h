@@ -325,7 +325,7 @@ int mrhs_profile(mrhs_ctx ctx, int enable);
  * entry. */
 int mrhs_profile_read(mrhs_ctx ctx, int idx, char* name, int name_len, long long* launches, double* ms);
 
-/* ------------------------------------------------------------ the judge */
+/* ------------------------------------------------ two-level FGMRES solve */
 
 /* Two-level FGMRES(restart) on D x = b (Sec. 2: FGMRES preconditioned by the
  * multigrid V-cycle), outer Arnoldi, D and residual in FP64; the

@@ -676,7 +676,7 @@ int ora_apply_Dc(const int* dims, const int* agg, int ntv, const cplx* Dc, const
 }
 
 /* ------------------------------------------------------------------ */
-/* GMRES(m) with Givens rotations (coarse solve, and the FGMRES judge)   */
+/* GMRES(m) with Givens rotations (coarse solve and the two-level FGMRES) */
 /* ------------------------------------------------------------------ */
 typedef void (*op_fn)(void* ctx, const cplx* in, cplx* out);
 
@@ -900,7 +900,7 @@ int ora_setup_refine(const int* dims, const int* agg, int ntv, const cplx* U, co
 }
 
 /* ------------------------------------------------------------------ */
-/* two-level FGMRES (the judge of a setup)                               */
+/* two-level FGMRES (the quality check of a setup)                       */
 /* ------------------------------------------------------------------ */
 typedef struct {
   geom_t g;

@@ -125,26 +125,8 @@ __global__ void __launch_bounds__(256) k_coarse_op_tiled(const SP* __restrict__ 
       int l = k == 0 ? q0 + q : face_site(ag, mu, lmu, q0 + q);
       int s = A * Va + l;
       cx<R> out[12];
-#pragma unroll
-      for (int c = 0; c < 12; ++c) out[c] = mk<R>(0, 0);
-      if (k == 0) {
-        cx<R> psi[12];
-        load_pcol<SP, R>(psi, P, s, Nt, col);
-        clover_apply_reg<R>(out, psi, Acl + (size_t)s * 72);
-        for (int d = -1; d <= 1; d += 2) {
-          hop_pcol<0, SP, R>(out, P, U, nbr, s, d, Nt, col, true, Va);
-          hop_pcol<1, SP, R>(out, P, U, nbr, s, d, Nt, col, true, Va);
-          hop_pcol<2, SP, R>(out, P, U, nbr, s, d, Nt, col, true, Va);
-          hop_pcol<3, SP, R>(out, P, U, nbr, s, d, Nt, col, true, Va);
-        }
-      } else {
-        switch (mu) {
-          case 0: hop_pcol<0, SP, R>(out, P, U, nbr, s, +1, Nt, col, false, Va); break;
-          case 1: hop_pcol<1, SP, R>(out, P, U, nbr, s, +1, Nt, col, false, Va); break;
-          case 2: hop_pcol<2, SP, R>(out, P, U, nbr, s, +1, Nt, col, false, Va); break;
-          default: hop_pcol<3, SP, R>(out, P, U, nbr, s, +1, Nt, col, false, Va); break;
-        }
-      }
+      if (col < Nt) dk_pcol<0, SP, R>(out, P, U, Acl, nbr, s, k, Nt, col, A * Va, Va);
+      else dk_pcol<1, SP, R>(out, P, U, Acl, nbr, s, k, Nt, col - Nt, A * Va, Va);
 #pragma unroll
       for (int c = 0; c < 12; ++c) Y[(q * 12 + c) * nc + col] = out[c];
     }

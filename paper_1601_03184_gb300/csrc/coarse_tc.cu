@@ -170,24 +170,8 @@ __global__ void __launch_bounds__(kThreads) k_coarse_op_tc(const SP* __restrict_
       if (q < nq) {
         const int l = k == 0 ? q0 + q : face_site(ag, mu, lmu, q0 + q);
         const int s = A * Va + l;
-        if (k == 0) {
-          cx<float> psi[12];
-          load_pcol<SP, float>(psi, P, s, Nt, col);
-          clover_apply_reg<float>(out, psi, Acl + (size_t)s * 72);
-          for (int d = -1; d <= 1; d += 2) {
-            hop_pcol<0, SP, float>(out, P, U, nbr, s, d, Nt, col, true, Va);
-            hop_pcol<1, SP, float>(out, P, U, nbr, s, d, Nt, col, true, Va);
-            hop_pcol<2, SP, float>(out, P, U, nbr, s, d, Nt, col, true, Va);
-            hop_pcol<3, SP, float>(out, P, U, nbr, s, d, Nt, col, true, Va);
-          }
-        } else {
-          switch (mu) {
-            case 0: hop_pcol<0, SP, float>(out, P, U, nbr, s, +1, Nt, col, false, Va); break;
-            case 1: hop_pcol<1, SP, float>(out, P, U, nbr, s, +1, Nt, col, false, Va); break;
-            case 2: hop_pcol<2, SP, float>(out, P, U, nbr, s, +1, Nt, col, false, Va); break;
-            default: hop_pcol<3, SP, float>(out, P, U, nbr, s, +1, Nt, col, false, Va); break;
-          }
-        }
+        if (col < Nt) dk_pcol<0, SP, float>(out, P, U, Acl, nbr, s, k, Nt, col, A * Va, Va);
+        else dk_pcol<1, SP, float>(out, P, U, Acl, nbr, s, k, Nt, col - Nt, A * Va, Va);
       }
 #pragma unroll
       for (int c = 0; c < 12; c += 2) {

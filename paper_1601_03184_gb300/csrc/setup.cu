@@ -1,6 +1,6 @@
 // The setup phase (Sec. 2 and Algorithm 2 of the paper with block length
 // N_b = ntv: the V-cycle is applied to all test vectors at once) and the
-// two-level FGMRES solve used to judge a setup.
+// two-level FGMRES solve that measures the quality of a setup.
 #include <cmath>
 #include <complex>
 #include <vector>

@@ -1,7 +1,7 @@
 """The 16^3 x 32 workload end to end on the GPU against the oracle's stored
 result (tests/golden/c2_fgmres.json, written by tests/golden/c2_fgmres.py
 from the FP64 oracle only): the FP32 setup and the bf16 / fp16 mixed setups,
-each followed by the two-level FGMRES judge on the same Gaussian right-hand
+each followed by the two-level FGMRES solve on the same Gaussian right-hand
 side to relative residual 1e-10. The iteration count must match the
 oracle's within +-10% (at least +-1): the GPU runs Algorithm 2 (all test
 vectors at once) where the oracle runs Algorithm 1 (one at a time), the same
@@ -36,7 +36,7 @@ def problem():
                          ids=["fp32", "bf16", "fp16"])
 def test_c2_setup_fgmres_iterations(problem, prec):
     dims, U, tv0, b = problem
-    c, s, j = GOLDEN["case"], GOLDEN["schedule"], GOLDEN["judge"]
+    c, s, j = GOLDEN["case"], GOLDEN["schedule"], GOLDEN["solve"]
     lat = Lattice(dims, tuple(c["agg"]), c["ntv"], prec)
     lat.set_gauge(U)
     lat.build_clover(GOLDEN["m0"], c["csw"])

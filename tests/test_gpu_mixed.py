@@ -7,7 +7,7 @@ Per-result errors (the stated bounds):
        P_oracle on every aggregate x chirality (P is determined up to its
        range by the test vectors, which carry the rounding of the storage);
   D_c: Frobenius norm of D_c,gpu - D_c,oracle relative to that of D_c,oracle;
-  the judge: two-level FGMRES on D x = b to 1e-10 with the GPU setup needs
+  FGMRES: two-level FGMRES on D x = b to 1e-10 with the GPU setup needs
   the oracle's iteration count within +-10% (at least +-1).
 The bounds follow from the storage unit roundoff u (fp32 6e-8, fp16 4.9e-4,
 bf16 3.9e-3) carried through the smoother iterations of the setup: the
