@@ -48,7 +48,7 @@ namespace {
 using namespace mrhs;
 
 constexpr int kMaxC = 32;
-constexpr int kCB = 8;          // output channels per thread
+constexpr int kCB = 12;         // output channels per thread (one block for the 11-triplet hidden layers)
 
 size_t layer_w(const NNState& s, int l) { return (size_t)9 * s.C[l + 1] * s.C[l]; }
 size_t layer_off(const NNState& s, int l) {
@@ -561,7 +561,7 @@ void nn_infer_chunked(mrhs_ctx c, const float* in, float* out, int N, int chunk)
 
 namespace mrhs {
 void nn_forward(mrhs_ctx c, const float* in, float* out, int N) { nn_forward_impl(c, in, out, N); }
-void nn_infer(mrhs_ctx c, const float* in, float* out, int N) { nn_infer_chunked(c, in, out, N, 4); }
+void nn_infer(mrhs_ctx c, const float* in, float* out, int N) { nn_infer_chunked(c, in, out, N, 8); }
 }  // namespace mrhs
 
 using namespace mrhs;
