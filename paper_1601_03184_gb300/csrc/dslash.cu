@@ -107,70 +107,43 @@ __global__ void k_block_mr(S* x, S* rho, S* q, const cx<R>* __restrict__ U, cons
 }
 
 // ---------------------------------------------------------------------------
-// FP32 full operator with G right-hand sides per thread (N % G == 0), vector
-// loads of the G interleaved right-hand sides, links padded to 20 floats
-// (one float4-aligned record per link, loaded once per thread and applied to
-// all G right-hand sides) and the clover term read as float4.
-template <int G>
-struct VecT;
-template <>
-struct VecT<2> {
-  using T = float2;
-};
-template <>
-struct VecT<4> {
-  using T = float4;
-};
-
-template <int G>
-__device__ __forceinline__ void ldv(const float* p, float v[G]) {
-  if constexpr (G == 2) {
-    float2 t = *reinterpret_cast<const float2*>(p);
-    v[0] = t.x;
-    v[1] = t.y;
+// FP32 full operator, y = D x, on packed pairs of right-hand sides: P pairs
+// per thread (2P interleaved right-hand sides, 8- or 16-byte loads), links
+// padded to 20 floats (one float4-aligned record per link, loaded once per
+// thread and applied to all its right-hand sides), the clover term read as
+// float4; threads in site order so that the CTAs running at one time cover a
+// compact range of aggregates; output stores are streaming (evict-first) so
+// that L2 keeps the input field.
+template <int P>
+__device__ __forceinline__ void ldp(const float* p, float2 v[P]) {
+  if constexpr (P == 1) {
+    v[0] = *reinterpret_cast<const float2*>(p);
   } else {
-    float4 t = *reinterpret_cast<const float4*>(p);
-    v[0] = t.x;
-    v[1] = t.y;
-    v[2] = t.z;
-    v[3] = t.w;
-  }
-}
-template <int G>
-__device__ __forceinline__ void stv(float* p, const float v[G]) {
-  if constexpr (G == 2) {
-    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
-  } else {
-    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = make_float2(t.x, t.y);
+    v[1] = make_float2(t.z, t.w);
   }
 }
 
-// one hop for G right-hand sides: neighbour rows at xn (row base n*12, column
-// offset r0), link record Ul = (1/2) sgn U (20 floats: 9 complex + padding)
-template <int MU, int DIR, int G, int NC>
-__device__ __forceinline__ void hop_vec(float ore[12][G], float oim[12][G], const float* __restrict__ xn, int Nrt,
-                                        const float* __restrict__ Ul) {
+template <int MU, int DIR, int P, int NC>
+__device__ __forceinline__ void hop_f2(c2 o[12][P], const float* __restrict__ xn, int Nrt,
+                                       const float* __restrict__ Ul) {
   const int N = NC > 0 ? NC : Nrt;
-  float hre[2][3][G], him[2][3][G];
+  c2 h[2][3][P];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    float pr[4][G], pi[4][G];
+    float2 pr[4][P], pi[4][P];
 #pragma unroll
     for (int sp = 0; sp < 4; ++sp) {
-      ldv<G>(xn + ((3 * sp + c) * 2 + 0) * N, pr[sp]);
-      ldv<G>(xn + ((3 * sp + c) * 2 + 1) * N, pi[sp]);
+      ldp<P>(xn + ((3 * sp + c) * 2 + 0) * N, pr[sp]);
+      ldp<P>(xn + ((3 * sp + c) * 2 + 1) * N, pi[sp]);
     }
 #pragma unroll
-    for (int g = 0; g < G; ++g) {
-      cx<float> p2 = mk(pr[2][g], pi[2][g]), p3 = mk(pr[3][g], pi[3][g]);
-      cx<float> b0, b1;
-      b_low<MU>(p2, p3, b0, b1);
-      cx<float> h0 = DIR > 0 ? mk(pr[0][g], pi[0][g]) - b0 : mk(pr[0][g], pi[0][g]) + b0;
-      cx<float> h1 = DIR > 0 ? mk(pr[1][g], pi[1][g]) - b1 : mk(pr[1][g], pi[1][g]) + b1;
-      hre[0][c][g] = h0.re;
-      him[0][c][g] = h0.im;
-      hre[1][c][g] = h1.re;
-      him[1][c][g] = h1.im;
+    for (int g = 0; g < P; ++g) {
+      using T = BTab<MU>;
+      // h_s = psi_s -/+ (B psi_low)_s
+      h[0][c][g] = axpy_ph<T::KB0, -DIR>(mk2(pr[0][g], pi[0][g]), mk2(pr[T::SB0][g], pi[T::SB0][g]));
+      h[1][c][g] = axpy_ph<T::KB1, -DIR>(mk2(pr[1][g], pi[1][g]), mk2(pr[T::SB1][g], pi[T::SB1][g]));
     }
   }
   float u[20];
@@ -185,58 +158,56 @@ __device__ __forceinline__ void hop_vec(float ore[12][G], float oim[12][G], cons
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
+    c2 ch[2][P];
 #pragma unroll
-    for (int g = 0; g < G; ++g) {
-      cx<float> ch[2];
+    for (int b = 0; b < 3; ++b) {
+      // U[a][b] forward, conj(U[b][a]) backward
+      const int e = DIR > 0 ? a * 3 + b : b * 3 + a;
+      const float2 ure = bc2(u[2 * e]);
+      const float2 uim = bc2(DIR > 0 ? u[2 * e + 1] : -u[2 * e + 1]);
+      const float2 nuim = bc2(DIR > 0 ? -u[2 * e + 1] : u[2 * e + 1]);
 #pragma unroll
-      for (int sp = 0; sp < 2; ++sp) {
-        cx<float> acc = mk(0.f, 0.f);
+      for (int sp = 0; sp < 2; ++sp)
 #pragma unroll
-        for (int b = 0; b < 3; ++b) {
-          cx<float> hv = mk(hre[sp][b][g], him[sp][b][g]);
-          if (DIR > 0) fma_(acc, mk(u[2 * (a * 3 + b)], u[2 * (a * 3 + b) + 1]), hv);
-          else fmac_(acc, mk(u[2 * (b * 3 + a)], u[2 * (b * 3 + a) + 1]), hv);
+        for (int g = 0; g < P; ++g) {
+          const c2 hv = h[sp][b][g];
+          if (b == 0) {
+            ch[sp][g].re = mul2(ure, hv.re);
+            ch[sp][g].im = mul2(ure, hv.im);
+          } else {
+            ch[sp][g].re = fma2(ure, hv.re, ch[sp][g].re);
+            ch[sp][g].im = fma2(ure, hv.im, ch[sp][g].im);
+          }
+          ch[sp][g].re = fma2(nuim, hv.im, ch[sp][g].re);
+          ch[sp][g].im = fma2(uim, hv.re, ch[sp][g].im);
         }
-        ch[sp] = acc;
-      }
-      cx<float> l0, l1;
-      bdag<MU>(ch[0], ch[1], l0, l1);
-      ore[a][g] -= ch[0].re;
-      oim[a][g] -= ch[0].im;
-      ore[3 + a][g] -= ch[1].re;
-      oim[3 + a][g] -= ch[1].im;
-      if (DIR > 0) {
-        ore[6 + a][g] += l0.re;
-        oim[6 + a][g] += l0.im;
-        ore[9 + a][g] += l1.re;
-        oim[9 + a][g] += l1.im;
-      } else {
-        ore[6 + a][g] -= l0.re;
-        oim[6 + a][g] -= l0.im;
-        ore[9 + a][g] -= l1.re;
-        oim[9 + a][g] -= l1.im;
-      }
+    }
+#pragma unroll
+    for (int g = 0; g < P; ++g) {
+      using T = BTab<MU>;
+      // upper spins -= chi, lower spins +/-= B^dag chi
+      o[a][g] = o[a][g] - ch[0][g];
+      o[3 + a][g] = o[3 + a][g] - ch[1][g];
+      o[6 + a][g] = axpy_ph<T::KD0, DIR>(o[6 + a][g], ch[T::SD0][g]);
+      o[9 + a][g] = axpy_ph<T::KD1, DIR>(o[9 + a][g], ch[T::SD1][g]);
     }
   }
 }
 
-// y = D x, FP32: one thread per (site, group of G right-hand sides), threads
-// in site order so that the CTAs running at one time cover a compact range of
-// aggregates; output stores are streaming (evict-first) so that L2 keeps the
-// input field.
-template <int G, int NC>
-__global__ void __launch_bounds__(128, G == 2 ? 3 : 2) k_dslash_vec(const float* __restrict__ x, float* __restrict__ y,
-                                                                    const float* __restrict__ U20,
-                                                                    const float* __restrict__ Acl,
-                                                                    const int* __restrict__ nbr, int Nrt, int q0, int nq,
-                                                                    size_t nwork) {
+template <int P, int NC, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_dslash_f2(const float* __restrict__ x, float* __restrict__ y,
+                                                         const float* __restrict__ U20,
+                                                         const float* __restrict__ Acl,
+                                                         const int* __restrict__ nbr, int Nrt, int q0, int nq,
+                                                         size_t nwork) {
+  constexpr int G = 2 * P;
   const int N = NC > 0 ? NC : Nrt;
-  const int ng = nq / G;  // right-hand sides q0 .. q0+nq-1 of this pass
+  const int ng = nq / G;
   const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (t >= nwork) return;
   const int r0 = q0 + (int)(t % ng) * G;
   const size_t s = t / ng;
-  float ore[12][G], oim[12][G];
+  c2 o[12][P];
   {
     const float4* A4 = reinterpret_cast<const float4*>(Acl + s * 72);
 #pragma unroll
@@ -250,27 +221,33 @@ __global__ void __launch_bounds__(128, G == 2 ? 3 : 2) k_dslash_vec(const float*
         q[4 * k + 2] = v.z;
         q[4 * k + 3] = v.w;
       }
-      float pr[6][G], pi[6][G];
+      float2 pr[6][P], pi[6][P];
 #pragma unroll
       for (int a = 0; a < 6; ++a) {
-        ldv<G>(x + ((s * 12 + 6 * h + a) * 2 + 0) * N + r0, pr[a]);
-        ldv<G>(x + ((s * 12 + 6 * h + a) * 2 + 1) * N + r0, pi[a]);
+        ldp<P>(x + ((s * 12 + 6 * h + a) * 2 + 0) * N + r0, pr[a]);
+        ldp<P>(x + ((s * 12 + 6 * h + a) * 2 + 1) * N + r0, pi[a]);
       }
 #pragma unroll
-      for (int a = 0; a < 6; ++a)
+      for (int a = 0; a < 6; ++a) {
+        const float2 qa = bc2(q[a]);
 #pragma unroll
-        for (int g = 0; g < G; ++g) {
-          cx<float> acc = scale(mk(pr[a][g], pi[a][g]), q[a]);
+        for (int g = 0; g < P; ++g) o[6 * h + a][g] = mk2(mul2(pr[a][g], qa), mul2(pi[a][g], qa));
 #pragma unroll
-          for (int b2 = 0; b2 < 6; ++b2) {
-            if (b2 == a) continue;
-            cx<float> m = b2 > a ? mk(q[herm_idx(a, b2)], q[herm_idx(a, b2) + 1])
-                                 : mk(q[herm_idx(b2, a)], -q[herm_idx(b2, a) + 1]);
-            fma_(acc, m, mk(pr[b2][g], pi[b2][g]));
+        for (int b2 = 0; b2 < 6; ++b2) {
+          if (b2 == a) continue;
+          const int e = b2 > a ? herm_idx(a, b2) : herm_idx(b2, a);
+          const float mim = b2 > a ? q[e + 1] : -q[e + 1];
+          const float2 mre2 = bc2(q[e]), mim2 = bc2(mim), nmim2 = bc2(-mim);
+#pragma unroll
+          for (int g = 0; g < P; ++g) {
+            c2& acc = o[6 * h + a][g];
+            acc.re = fma2(mre2, pr[b2][g], acc.re);
+            acc.re = fma2(nmim2, pi[b2][g], acc.re);
+            acc.im = fma2(mre2, pi[b2][g], acc.im);
+            acc.im = fma2(mim2, pr[b2][g], acc.im);
           }
-          ore[6 * h + a][g] = acc.re;
-          oim[6 * h + a][g] = acc.im;
         }
+      }
     }
   }
 #pragma unroll
@@ -281,15 +258,15 @@ __global__ void __launch_bounds__(128, G == 2 ? 3 : 2) k_dslash_vec(const float*
       const float* xn = x + n * 24 * N + r0;
       const float* Ul = U20 + ((d == 0 ? s : n) * 4 + mu) * 20;
       if (d == 0) {
-        if (mu == 0) hop_vec<0, +1, G, NC>(ore, oim, xn, Nrt, Ul);
-        if (mu == 1) hop_vec<1, +1, G, NC>(ore, oim, xn, Nrt, Ul);
-        if (mu == 2) hop_vec<2, +1, G, NC>(ore, oim, xn, Nrt, Ul);
-        if (mu == 3) hop_vec<3, +1, G, NC>(ore, oim, xn, Nrt, Ul);
+        if (mu == 0) hop_f2<0, +1, P, NC>(o, xn, Nrt, Ul);
+        if (mu == 1) hop_f2<1, +1, P, NC>(o, xn, Nrt, Ul);
+        if (mu == 2) hop_f2<2, +1, P, NC>(o, xn, Nrt, Ul);
+        if (mu == 3) hop_f2<3, +1, P, NC>(o, xn, Nrt, Ul);
       } else {
-        if (mu == 0) hop_vec<0, -1, G, NC>(ore, oim, xn, Nrt, Ul);
-        if (mu == 1) hop_vec<1, -1, G, NC>(ore, oim, xn, Nrt, Ul);
-        if (mu == 2) hop_vec<2, -1, G, NC>(ore, oim, xn, Nrt, Ul);
-        if (mu == 3) hop_vec<3, -1, G, NC>(ore, oim, xn, Nrt, Ul);
+        if (mu == 0) hop_f2<0, -1, P, NC>(o, xn, Nrt, Ul);
+        if (mu == 1) hop_f2<1, -1, P, NC>(o, xn, Nrt, Ul);
+        if (mu == 2) hop_f2<2, -1, P, NC>(o, xn, Nrt, Ul);
+        if (mu == 3) hop_f2<3, -1, P, NC>(o, xn, Nrt, Ul);
       }
     }
   }
@@ -297,12 +274,12 @@ __global__ void __launch_bounds__(128, G == 2 ? 3 : 2) k_dslash_vec(const float*
   for (int c = 0; c < 12; ++c) {
     float* yr = y + ((s * 12 + c) * 2 + 0) * N + r0;
     float* yi = y + ((s * 12 + c) * 2 + 1) * N + r0;
-    if constexpr (G == 2) {
-      __stcs(reinterpret_cast<float2*>(yr), make_float2(ore[c][0], ore[c][1]));
-      __stcs(reinterpret_cast<float2*>(yi), make_float2(oim[c][0], oim[c][1]));
+    if constexpr (P == 1) {
+      __stcs(reinterpret_cast<float2*>(yr), o[c][0].re);
+      __stcs(reinterpret_cast<float2*>(yi), o[c][0].im);
     } else {
-      __stcs(reinterpret_cast<float4*>(yr), make_float4(ore[c][0], ore[c][1], ore[c][2], ore[c][3]));
-      __stcs(reinterpret_cast<float4*>(yi), make_float4(oim[c][0], oim[c][1], oim[c][2], oim[c][3]));
+      __stcs(reinterpret_cast<float4*>(yr), make_float4(o[c][0].re.x, o[c][0].re.y, o[c][1].re.x, o[c][1].re.y));
+      __stcs(reinterpret_cast<float4*>(yi), make_float4(o[c][0].im.x, o[c][0].im.y, o[c][1].im.x, o[c][1].im.y));
     }
   }
 }
@@ -320,24 +297,24 @@ static int stencil_passes(int N, int G) {
   return p;
 }
 
-template <int G, int NC>
-void launch_dslash_vec(mrhs_ctx c, const float* x, float* y, int N) {
-  const int passes = stencil_passes(N, G);
+template <int NC>
+void launch_dslash_f2(mrhs_ctx c, const float* x, float* y, int N) {
+  const int passes = stencil_passes(N, 2);
   const int nq = N / passes;
-  const size_t work = (size_t)c->g.V * (nq / G);
+  const size_t work = (size_t)c->g.V * (nq / 2);
   for (int p = 0; p < passes; ++p)
-    k_dslash_vec<G, NC><<<grid_for(work, 128), 128, 0, c->stream>>>(x, y, c->U20, c->A32, c->nbr, N, p * nq, nq, work);
+    k_dslash_f2<1, NC, 4><<<grid_for(work, 128), 128, 0, c->stream>>>(x, y, c->U20, c->A32, c->nbr, N, p * nq, nq,
+                                                                       work);
 }
 
-template <int G>
-void dslash_vec(mrhs_ctx c, const float* x, float* y, int N) {
+void dslash_f2(mrhs_ctx c, const float* x, float* y, int N) {
   switch (N) {
-    case 8: launch_dslash_vec<G, 8>(c, x, y, N); break;
-    case 16: launch_dslash_vec<G, 16>(c, x, y, N); break;
-    case 20: launch_dslash_vec<G, 20>(c, x, y, N); break;
-    case 24: launch_dslash_vec<G, 24>(c, x, y, N); break;
-    case 32: launch_dslash_vec<G, 32>(c, x, y, N); break;
-    default: launch_dslash_vec<G, 0>(c, x, y, N); break;
+    case 8: launch_dslash_f2<8>(c, x, y, N); break;
+    case 16: launch_dslash_f2<16>(c, x, y, N); break;
+    case 20: launch_dslash_f2<20>(c, x, y, N); break;
+    case 24: launch_dslash_f2<24>(c, x, y, N); break;
+    case 32: launch_dslash_f2<32>(c, x, y, N); break;
+    default: launch_dslash_f2<0>(c, x, y, N); break;
   }
 }
 
@@ -394,27 +371,14 @@ void block_mr_t(mrhs_ctx c, S* x, S* rho, S* q, int N, const int* blist, int nbl
 
 }  // namespace
 
-// right-hand sides per thread of the FP32 stencil: MRHS_STENCIL_VEC = 1 (one
-// per thread), 2 or 4; default 2 when nrhs is even (measured fastest)
-static int stencil_vec_width() {
-  static int w = [] {
-    const char* e = getenv("MRHS_STENCIL_VEC");
-    int v = e ? atoi(e) : 0;
-    return (v == 1 || v == 2 || v == 4) ? v : 0;
-  }();
-  return w;
-}
-
 void dslash(mrhs_ctx c, const void* x, void* y, const void* b, int nrhs, int dtype, int mode, int colour) {
   MRHS_REQUIRE(c->have_clover, MRHS_ERR_STATE, "operator used before mrhs_build_clover");
   MRHS_REQUIRE(nrhs >= 1, MRHS_ERR_ARG, "nrhs must be >= 1");
-  const int vw = stencil_vec_width();
-  if (dtype == MRHS_F32 && mode == DS_FULL && colour < 0 && c->U20 && nrhs % 2 == 0 && vw != 1) {
-    int G = (nrhs % 4 == 0 && vw == 4) ? 4 : 2;
+  // FP32, even nrhs: the packed-pair kernel (an odd count takes the generic one)
+  if (dtype == MRHS_F32 && mode == DS_FULL && colour < 0 && c->U20 && nrhs % 2 == 0) {
     Prof pr(c, "dslash_full");
-    if (G == 4) dslash_vec<4>(c, (const float*)x, (float*)y, nrhs);
-    else dslash_vec<2>(c, (const float*)x, (float*)y, nrhs);
-    MRHS_LAUNCH_CHECK("dslash_vec");
+    dslash_f2(c, (const float*)x, (float*)y, nrhs);
+    MRHS_LAUNCH_CHECK("dslash_f2");
     return;
   }
   const int* blist = nullptr;

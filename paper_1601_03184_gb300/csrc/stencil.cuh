@@ -160,5 +160,55 @@ __device__ __forceinline__ void dslash_site(cx<R> out[12], const S* x, int s, in
 #undef MRHS_HOP
 }
 
+// Packed pairs of right-hand sides (FP32): a float2 holds one real component
+// of two neighbouring right-hand sides and every arithmetic step is one
+// fma/add/mul .rn.f32x2 instruction doing the work of two. The rounding is
+// per lane, so a packed kernel that performs the scalar operations in the
+// same order gives the same bits. Link and clover entries are broadcast
+// into both lanes.
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b, exactly rounded like the scalar subtraction (one fused step)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
+struct c2 {
+  float2 re, im;
+};
+__device__ __forceinline__ c2 mk2(float2 re, float2 im) {
+  c2 r;
+  r.re = re;
+  r.im = im;
+  return r;
+}
+__device__ __forceinline__ c2 operator+(c2 a, c2 b) { return mk2(add2(a.re, b.re), add2(a.im, b.im)); }
+__device__ __forceinline__ c2 operator-(c2 a, c2 b) { return mk2(sub2(a.re, b.re), sub2(a.im, b.im)); }
+template <int SG>
+__device__ __forceinline__ float2 pm2(float2 a, float2 b) {
+  return SG > 0 ? add2(a, b) : sub2(a, b);
+}
+// a + SG i^K x (K = 0..3): the phase only selects components and signs
+template <int K, int SG>
+__device__ __forceinline__ c2 axpy_ph(c2 a, c2 x) {
+  constexpr int sre = (K == 0 || K == 3) ? SG : -SG;
+  constexpr int sim = (K == 0 || K == 1) ? SG : -SG;
+  return mk2(pm2<sre>(a.re, (K & 1) ? x.im : x.re), pm2<sim>(a.im, (K & 1) ? x.re : x.im));
+}
+
+// The chiral-basis B_mu (B psi_low) and B_mu^dag as (phase i^K, source spin):
+// (B psi_low)_s = i^KB0 psi_{SB0}, ... with psi_low = (psi_2, psi_3), and
+// (B^dag chi)_s = i^KD0 chi_{SD0}, ... with chi = (chi_0, chi_1).
+template <int MU>
+struct BTab {
+  static constexpr int KB0 = MU == 0 ? 3 : MU == 1 ? 2 : MU == 2 ? 3 : 0;
+  static constexpr int SB0 = MU == 0 ? 3 : MU == 1 ? 3 : 2;
+  static constexpr int KB1 = MU == 0 ? 3 : MU == 1 ? 0 : MU == 2 ? 1 : 0;
+  static constexpr int SB1 = MU == 0 ? 2 : MU == 1 ? 2 : 3;
+  static constexpr int KD0 = MU == 0 ? 1 : MU == 1 ? 0 : MU == 2 ? 1 : 0;
+  static constexpr int SD0 = MU == 0 ? 1 : MU == 1 ? 1 : 0;
+  static constexpr int KD1 = MU == 0 ? 1 : MU == 1 ? 2 : MU == 2 ? 3 : 0;
+  static constexpr int SD1 = MU == 0 ? 0 : MU == 1 ? 0 : 1;
+};
 
 }  // namespace mrhs
