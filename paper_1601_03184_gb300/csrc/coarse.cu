@@ -563,6 +563,8 @@ void build_Dc(mrhs_ctx c) {
     k_coarse_backward<float><<<grid_for(tot, 256), 256, 0, c->stream>>>((cx<float>*)c->Dc, c->aggnbr, c->g.nagg, Nt);
     MRHS_LAUNCH_CHECK("coarse_backward");
     c->have_Dc = true;
+    ++c->dc_version;
+    dc_images_build(c);
     return;
   }
   MRHS_REQUIRE(c->dc_engine == MRHS_DC_AUTO || c->dc_engine == MRHS_DC_ALU, MRHS_ERR_SHAPE,
@@ -593,6 +595,8 @@ void build_Dc(mrhs_ctx c) {
     }
   });
   c->have_Dc = true;
+  ++c->dc_version;
+  dc_images_build(c);
 }
 
 // restriction from a fine field of type dv into a coarse field of type dc

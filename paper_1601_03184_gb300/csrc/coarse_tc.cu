@@ -23,6 +23,8 @@
 #include "tc.cuh"
 
 #include <algorithm>
+#include <cstdlib>
+#include <string>
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -290,7 +292,7 @@ __global__ void __launch_bounds__(kThreads) k_coarse_op_tc(const SP* __restrict_
 // waited for; two CTAs share an SM.
 constexpr int kDcThreads = 512;  // 16 warps: the operand conversion is the CUDA cores' share
 
-template <bool SPLIT>
+template <bool SPLIT, bool PRE>
 __global__ void __launch_bounds__(kDcThreads, 1) k_apply_dc_tc(const float* __restrict__ Dc,
                                                                const float* __restrict__ x, float* __restrict__ y,
                                                                const int* __restrict__ aggnbr, int nc, int nrhs,
@@ -305,15 +307,19 @@ __global__ void __launch_bounds__(kDcThreads, 1) k_apply_dc_tc(const float* __re
   const int a_bytes = kRows / 8 * KG * 128;  // A tile
   const int b_bytes = NM / 8 * KG * 128;     // B tile
   const uint32_t d_bytes = (uint32_t)nc * nc * 8, x_bytes = (uint32_t)nc * 2 * nrhs * 4;
-  const uint32_t raw_bytes = (d_bytes + x_bytes + 1023) & ~1023u;
-  unsigned char* raw0 = smem;                      // stage s: D block, then the x block
-  unsigned char* Ahi = smem + 2 * raw_bytes;
-  unsigned char* Bhi = Ahi + a_bytes;
-  unsigned char* Alo = Bhi + b_bytes;
-  unsigned char* Blo = Alo + a_bytes;
+  // PRE: the stage holds the block's ready operand images (hi, then lo) in
+  // place of the FP32 block, and the MMAs read A from the stage itself
+  const uint32_t img_bytes = (SPLIT ? 2 : 1) * (uint32_t)a_bytes;
+  const uint32_t x_off = PRE ? img_bytes : d_bytes;  // the x block inside a stage
+  const uint32_t raw_bytes = (x_off + x_bytes + 1023) & ~1023u;
+  unsigned char* raw0 = smem;                      // stage s: D block (or its images), then the x block
+  unsigned char* Ahi = smem + 2 * raw_bytes;       // (not PRE)
+  unsigned char* Bhi = PRE ? Ahi : Ahi + a_bytes;
+  unsigned char* Alo = Bhi + b_bytes;              // (not PRE)
+  unsigned char* Blo = PRE ? Bhi + b_bytes : Alo + a_bytes;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  if (2 * nc < kRows) {  // rows of A beyond 2nc stay zero
+  if (!PRE && 2 * nc < kRows) {  // rows of A beyond 2nc stay zero
     const int nz = (SPLIT ? 2 : 1) * (a_bytes + b_bytes) / 16;
     for (int i = tid; i < nz; i += kDcThreads) reinterpret_cast<uint4*>(Ahi)[i] = make_uint4(0, 0, 0, 0);
   }
@@ -355,9 +361,13 @@ __global__ void __launch_bounds__(kDcThreads, 1) k_apply_dc_tc(const float* __re
   auto fetch = [&](int k) {
     unsigned char* raw = raw0 + (k & 1) * raw_bytes;
     const int B = k == 0 ? A : aggnbr[A * 8 + k - 1];
-    tc::mbar_expect_tx(&full[k & 1], d_bytes + x_bytes);
-    tc::bulk_g2s(raw, Dc + ((size_t)A * 9 + k) * nc * nc * 2, d_bytes, &full[k & 1]);
-    tc::bulk_g2s(raw + d_bytes, x + (size_t)B * nc * 2 * nrhs, x_bytes, &full[k & 1]);
+    tc::mbar_expect_tx(&full[k & 1], x_off + x_bytes);
+    if (PRE)
+      tc::bulk_g2s(raw, reinterpret_cast<const unsigned char*>(Dc) + ((size_t)A * 9 + k) * img_bytes, img_bytes,
+                   &full[k & 1]);
+    else
+      tc::bulk_g2s(raw, Dc + ((size_t)A * 9 + k) * nc * nc * 2, d_bytes, &full[k & 1]);
+    tc::bulk_g2s(raw + x_off, x + (size_t)B * nc * 2 * nrhs, x_bytes, &full[k & 1]);
   };
   if (tid == 0) {
     fetch(0);
@@ -373,6 +383,8 @@ __global__ void __launch_bounds__(kDcThreads, 1) k_apply_dc_tc(const float* __re
       tc::fence_after_sync();
       tc::tmem_promote(t_own + NM, t_own, own);  // warp-wide; a failed wait discards the result
       tc::tmem_wait_st();
+      // PRE: the MMAs of block k-1 are done with its stage, which takes block k+1
+      if (PRE && tid == 0 && ok && k + 1 < 9) fetch(k + 1);
     }
     if (!ok) s_bad = 1;
     tc::fence_before_sync();
@@ -381,7 +393,7 @@ __global__ void __launch_bounds__(kDcThreads, 1) k_apply_dc_tc(const float* __re
     // A: 16-byte chunks q (two complex columns) of 8 rows per warp pass; lane
     // (r, qq) takes chunk 8 qq + ((r + t) & 7) of row r, so that the eight
     // lanes of a row group hit eight different bank groups
-    {
+    if (!PRE) {
       const float4* D4 = reinterpret_cast<const float4*>(raw);
       const int r = lane & 7, qq = lane >> 3;
       for (int pass = warp; pass < (nc / 8) * 8; pass += kDcThreads / 32) {
@@ -408,7 +420,7 @@ __global__ void __launch_bounds__(kDcThreads, 1) k_apply_dc_tc(const float* __re
     // B: one 16-byte core row (row n = (p, r), K group kq) per unit, from four
     // rows (kk, p) of the x block
     {
-      const float* X = reinterpret_cast<const float*>(raw + d_bytes);
+      const float* X = reinterpret_cast<const float*>(raw + x_off);
       for (int u = tid; u < NM * KG; u += kDcThreads) {
         const int n = u % NM, kq = u / NM;
         const int p = n / nrhs, r = n % nrhs;
@@ -423,9 +435,10 @@ __global__ void __launch_bounds__(kDcThreads, 1) k_apply_dc_tc(const float* __re
     tc::fence_async_smem();
     __syncthreads();
     if (tid == 0) {
-      if (k + 2 < 9) fetch(k + 2);  // the raw stage is free: every thread has converted it
+      if (!PRE && k + 2 < 9) fetch(k + 2);  // the raw stage is free: every thread has converted it
       tc::fence_after_sync();
-      const uint32_t ah = tc::smem_u32(Ahi), bh = tc::smem_u32(Bhi), al = tc::smem_u32(Alo), bl = tc::smem_u32(Blo);
+      const uint32_t ah = PRE ? tc::smem_u32(raw) : tc::smem_u32(Ahi), bh = tc::smem_u32(Bhi),
+                     al = PRE ? ah + a_bytes : tc::smem_u32(Alo), bl = tc::smem_u32(Blo);
       const uint32_t sbo = KG * 128;
       for (int ks = 0; ks < KG / 2; ++ks) {
         const uint32_t o = ks * 256;
@@ -480,6 +493,36 @@ __global__ void __launch_bounds__(kDcThreads, 1) k_apply_dc_tc(const float* __re
   if (warp == 0) tc::tmem_dealloc(tbase, tm_cols);
 }
 
+// D_c blocks as the byte images of k_apply_dc_tc's A operand tiles (tf32 hi,
+// then lo with SPLIT), written once per build of D_c so that the coarse
+// stencil copies them into shared memory as they are. One thread per 16-byte
+// core row (row r, K group kq); the eight rows of a core matrix are adjacent
+// threads, so each warp writes whole 128-byte core matrices. Rows beyond 2 nc
+// are zero.
+template <bool SPLIT>
+__global__ void k_format_dc(const float* __restrict__ Dc, unsigned char* __restrict__ img, int nc, size_t nblk) {
+  const int KG = nc / 4;
+  const uint32_t a_bytes = kRows / 8 * KG * 128;
+  const size_t per_blk = (size_t)kRows * KG;  // core rows of one image
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= nblk * per_blk) return;
+  const size_t blk = t / per_blk;
+  const int u = (int)(t % per_blk);
+  const int r8 = u & 7, kq = (u >> 3) % KG, g8 = (u >> 3) / KG;
+  const int m = 8 * g8 + r8;  // A row: Re rows 0..nc-1, Im rows nc..2nc-1
+  unsigned char* hi = img + blk * (SPLIT ? 2 : 1) * a_bytes;
+  uint32_t h[4] = {0, 0, 0, 0}, l[4] = {0, 0, 0, 0};
+  if (m < 2 * nc) {
+    const int row = m < nc ? m : m - nc, p = m < nc ? 0 : 1;
+    const float* D = Dc + (blk * nc + row) * nc * 2;  // complex row of the block
+#pragma unroll
+    for (int j = 0; j < 4; ++j) tf32_split(D[2 * (4 * kq + j) + p], h[j], l[j]);
+  }
+  const uint32_t off = tc::kmajor_offset(m, 4 * kq, 4, KG);
+  *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+  if (SPLIT) *reinterpret_cast<uint4*>(hi + a_bytes + off) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
 }  // namespace
 
 // tensor-core contraction for the self and forward blocks (split: tf32
@@ -516,6 +559,41 @@ bool build_Dc_tc(mrhs_ctx c, int fmt, bool split) {
   return true;
 }
 
+// the operand images of D_c for the tensor-core coarse stencil, made by every
+// build of D_c (so that the coarse solves, including the allocation-free one,
+// only read them): tf32 hi + lo for the FP32 setup, tf32 for the mixed ones.
+// Skipped (the stencil then converts each block itself) when the stencil
+// would not use them, when MRHS_DC_IMAGES=0, or when they do not fit in
+// device memory.
+void dc_images_build(mrhs_ctx c) {
+  static const bool off = [] {
+    const char* e = std::getenv("MRHS_DC_IMAGES");
+    const char* a = std::getenv("MRHS_DC_APPLY");
+    return (e && std::atoi(e) == 0) || (a && std::string(a) == "alu");
+  }();
+  const int nc = 2 * c->ntv, KG = nc / 4;
+  if (off || c->dc_engine == MRHS_DC_ALU || c->work_dtype != MRHS_F32 || nc % 8 != 0 || nc > 64) return;
+  const bool split = c->prec == MRHS_PREC_FP32;
+  const size_t a_bytes = (size_t)kRows / 8 * KG * 128;
+  const size_t nblk = (size_t)c->g.nagg * 9;
+  if (!c->dc_img) {
+    const size_t bytes = nblk * 2 * a_bytes;  // room for either form
+    size_t free_b = 0, total_b = 0;
+    MRHS_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    if (bytes + ((size_t)1 << 30) > free_b) return;
+    c->dc_img = dalloc(c, bytes);
+  }
+  const size_t n = nblk * (size_t)kRows * KG;
+  Prof pr(c, "format_dc");
+  if (split)
+    k_format_dc<true><<<grid_for(n, 256), 256, 0, c->stream>>>((const float*)c->Dc, (unsigned char*)c->dc_img, nc, nblk);
+  else
+    k_format_dc<false><<<grid_for(n, 256), 256, 0, c->stream>>>((const float*)c->Dc, (unsigned char*)c->dc_img, nc, nblk);
+  MRHS_LAUNCH_CHECK("format_dc");
+  c->dc_img_version = c->dc_version;
+  c->dc_img_split = (int)split;
+}
+
 // coarse stencil on the tensor cores (FP32 coarse fields): split-tf32 (FP32
 // accuracy) or single tf32; false when the shape is outside the kernel's
 bool apply_Dc_tc(mrhs_ctx c, const void* xc, void* yc, int nrhs, bool split) {
@@ -524,14 +602,25 @@ bool apply_Dc_tc(mrhs_ctx c, const void* xc, void* yc, int nrhs, bool split) {
   const int KG = nc / 4;
   const size_t tiles = (size_t)(kRows / 8 * KG * 128 + 2 * nrhs / 8 * KG * 128);
   const size_t raw = ((size_t)nc * nc * 8 + (size_t)nc * 2 * nrhs * 4 + 1023) & ~(size_t)1023;
-  const size_t smem = std::max(2 * raw, sizeof(float) * kRows * (2 * nrhs + 1)) + (split ? 2 : 1) * tiles;
+  size_t smem = std::max(2 * raw, sizeof(float) * kRows * (2 * nrhs + 1)) + (split ? 2 : 1) * tiles;
   uint32_t cols = 32;
   while (cols < (uint32_t)(4 * nrhs)) cols <<= 1;  // R and S regions of 2 nrhs columns each
   int* err = c->dflag + 3;
+  const void* src = c->Dc;
+  const bool pre = c->dc_img && c->dc_img_version == c->dc_version && c->dc_img_split == (int)split;
+  if (pre) {
+    src = c->dc_img;
+    // stages hold the operand images instead of the FP32 blocks; no A tiles
+    const size_t img = (size_t)(split ? 2 : 1) * (kRows / 8 * KG * 128);
+    const size_t stage = (img + (size_t)nc * 2 * nrhs * 4 + 1023) & ~(size_t)1023;
+    const size_t btiles = (size_t)(split ? 2 : 1) * (2 * nrhs / 8 * KG * 128);
+    smem = std::max(2 * stage, sizeof(float) * kRows * (2 * nrhs + 1)) + btiles;
+  }
   Prof pr(c, "apply_dc_tc");
-  auto kern = split ? k_apply_dc_tc<true> : k_apply_dc_tc<false>;
+  auto kern = pre ? (split ? k_apply_dc_tc<true, true> : k_apply_dc_tc<false, true>)
+                  : (split ? k_apply_dc_tc<true, false> : k_apply_dc_tc<false, false>);
   MRHS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  kern<<<c->g.nagg, kDcThreads, smem, c->stream>>>((const float*)c->Dc, (const float*)xc, (float*)yc, c->aggnbr, nc,
+  kern<<<c->g.nagg, kDcThreads, smem, c->stream>>>((const float*)src, (const float*)xc, (float*)yc, c->aggnbr, nc,
                                                    nrhs, cols, err);
   MRHS_LAUNCH_CHECK("apply_dc_tc");
   return true;

@@ -195,6 +195,10 @@ struct mrhs_ctx_s {
   void* tv = nullptr;   // [V][12][2][ntv] in tv_dtype
   void* P = nullptr;    // same
   void* Dc = nullptr;   // [nagg][9][2ntv][2ntv] complex in work dtype
+  long long dc_version = 0;        // bumped by every build of D_c
+  void* dc_img = nullptr;          // D_c as tensor-core operand images (coarse_tc.cu)
+  long long dc_img_version = -1;   // the D_c version the images hold
+  int dc_img_split = -1;           // 1: tf32 hi + lo images, 0: tf32 only
   bool have_tv = false, have_P = false, have_Dc = false;
   // the setup stores its (unit-norm) test vectors multiplied by tv_scale:
   // sqrt(12 V) for fp16 storage (entries of order 1, inside the fp16 range),
@@ -267,6 +271,7 @@ constexpr int tc_fmt_f16 = 0, tc_fmt_bf16 = 1, tc_fmt_tf32 = 2;
 bool build_Dc_tc(mrhs_ctx c, int fmt, bool split);
 // coarse stencil on the tensor cores; sets dflag[3] if a pipeline wait ran out
 bool apply_Dc_tc(mrhs_ctx c, const void* xc, void* yc, int nrhs, bool split);
+void dc_images_build(mrhs_ctx c);
 void check_tc_timeout(mrhs_ctx c);
 void restrict_(mrhs_ctx c, const void* v, void* vc, int nrhs, int dtype);
 void prolong(mrhs_ctx c, const void* uc, void* u, int nrhs, int dtype);

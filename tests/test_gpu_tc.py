@@ -191,3 +191,36 @@ def test_apply_Dc_tensor_cores(prec, nrhs):
 
 def rel_err(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _apply_Dc_result(prec, nrhs):
+    cfg = CASES["4^4-ntv32"]
+    lat, _, _ = setup_P(cfg, prec, MRHS_DC_AUTO)
+    lat.build_Dc()
+    xc = inputs.gaussian_field((nrhs, lat.nagg, 2 * cfg["ntv"]), 902).astype(np.complex64)
+    yd = lat.field(nrhs, MRHS_F32, coarse=True)
+    lat.apply_Dc(lat.to_device(xc, MRHS_F32, coarse=True), yd, nrhs, MRHS_F32)
+    lat.sync()
+    return lat.to_host(yd, nrhs, MRHS_F32, coarse=True, host_dtype=MRHS_F32)
+
+
+@pytest.mark.parametrize("prec", [MRHS_PREC_FP32, MRHS_PREC_MIX_BF16], ids=["fp32-split", "bf16-tf32"])
+def test_apply_Dc_images_equal_block_conversion(prec, tmp_path):
+    """The coarse stencil reads D_c as the operand images made when D_c is
+    built; with MRHS_DC_IMAGES=0 (a child process, the switch is read once) it
+    converts every block itself. Both hold the same tf32 parts in the same
+    layout and run the same MMAs, so the results are equal bit for bit."""
+    import os
+    import subprocess
+    import sys
+    nrhs = 32
+    y_img = _apply_Dc_result(prec, nrhs)
+    out = tmp_path / "y.npy"
+    here = os.path.dirname(os.path.abspath(__file__))
+    code = ("import sys; sys.path.insert(0, %r); sys.path.insert(0, %r); import numpy as np; "
+            "import test_gpu_tc as t; np.save(%r, t._apply_Dc_result(%d, %d))"
+            % (here, os.path.dirname(here), str(out), prec, nrhs))
+    env = dict(os.environ, MRHS_DC_IMAGES="0")
+    subprocess.run([sys.executable, "-c", code], check=True, env=env, cwd=os.path.dirname(here), timeout=600)
+    y_conv = np.load(out)
+    assert y_img.dtype == y_conv.dtype and np.array_equal(y_img.view(np.uint32), y_conv.view(np.uint32))
