@@ -4,6 +4,8 @@
 // Arrays are `rows` complex rows of [2][N]: element (row, re/im, rhs).
 // Reductions use a fixed two-level tree (per-CTA partials, then a fixed-order
 // sum), so results are bitwise reproducible.
+#include <cstdint>
+
 #include "common.cuh"
 
 namespace mrhs {
@@ -78,6 +80,75 @@ __global__ void __launch_bounds__(kBlock) k_multi_dot(const S* X, size_t stride,
   }
 }
 
+// The same for FP32 arrays with N % 4 == 0: a thread takes four right-hand
+// sides (16-byte loads of the real and the imaginary row) and sums its rows
+// of the chunk in FP32 before the CTA adds the threads' sums in FP64. Used
+// when a thread has at most kMaxRows4 rows of the chunk (the coarse fields).
+constexpr int kMaxRows4 = 128;
+
+constexpr int kKG4 = 4;  // vectors per group (register budget of 16 FP32 sums each)
+
+__global__ void __launch_bounds__(kBlock, 2) k_multi_dot4(const float* __restrict__ X, size_t stride, int K,
+                                                          const float* __restrict__ Y, size_t rows, int N, int nchunk,
+                                                          double* __restrict__ part) {
+  constexpr int kKG = kKG4;
+  __shared__ double sre[4 * kBlock], sim[4 * kBlock];  // [lanes][N]
+  const int k0 = blockIdx.y * kKG, ch = blockIdx.x;
+  const int nk = min(kKG, K - k0);
+  const size_t r0 = rows * ch / nchunk, r1 = rows * (ch + 1) / nchunk;
+  const int Q = N / 4, lanes = kBlock / Q;
+  const int tid = threadIdx.x, q = tid % Q, lane = tid / Q;
+  float pre[kKG][4], pim[kKG][4];
+#pragma unroll
+  for (int j = 0; j < kKG; ++j)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) pre[j][e] = pim[j][e] = 0.f;
+  if (lane < lanes) {
+    for (size_t row = r0 + lane; row < r1; row += lanes) {
+      const float4 yr = *reinterpret_cast<const float4*>(Y + fidx(row, 0, N, 4 * q));
+      const float4 yi = *reinterpret_cast<const float4*>(Y + fidx(row, 1, N, 4 * q));
+#pragma unroll
+      for (int j = 0; j < kKG; ++j) {
+        if (j < nk) {
+          const float* Xk = X + (size_t)(k0 + j) * stride;
+          const float4 xr = *reinterpret_cast<const float4*>(Xk + fidx(row, 0, N, 4 * q));
+          const float4 xi = *reinterpret_cast<const float4*>(Xk + fidx(row, 1, N, 4 * q));
+          const float xre[4] = {xr.x, xr.y, xr.z, xr.w}, xim[4] = {xi.x, xi.y, xi.z, xi.w};
+          const float yre[4] = {yr.x, yr.y, yr.z, yr.w}, yim[4] = {yi.x, yi.y, yi.z, yi.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            pre[j][e] = fmaf(xre[e], yre[e], fmaf(xim[e], yim[e], pre[j][e]));
+            pim[j][e] = fmaf(xre[e], yim[e], fmaf(-xim[e], yre[e], pim[j][e]));
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kKG; ++j) {
+    if (j >= nk) break;
+    if (lane < lanes) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        sre[lane * N + 4 * q + e] = (double)pre[j][e];
+        sim[lane * N + 4 * q + e] = (double)pim[j][e];
+      }
+    }
+    __syncthreads();
+    if (tid < N) {
+      double a = 0, b = 0;
+      for (int l = 0; l < lanes; ++l) {
+        a += sre[l * N + tid];
+        b += sim[l * N + tid];
+      }
+      double* o = part + (((size_t)(k0 + j) * nchunk + ch) * N + tid) * 2;
+      o[0] = a;
+      o[1] = b;
+    }
+    __syncthreads();
+  }
+}
+
 // out[k][r] = sum over the chunks of part[k][chunk][r]: one warp per (k, r),
 // lane l adds chunks l, l+32, ... and the lanes are joined by a fixed
 // butterfly, so the order of the sum does not depend on timing
@@ -126,6 +197,37 @@ __global__ void k_multi_axpy(const S* X, size_t stride, int K, S* Y, size_t rows
   Y[fidx(row, 1, N, r)] = from_r<S>(yi);
 }
 
+// FP32, N % 4 == 0: four right-hand sides per thread, 16-byte loads and
+// stores (the scalar kernel's operations in its order: the same bits)
+__global__ void k_multi_axpy4(const float* __restrict__ X, size_t stride, int K, float* __restrict__ Y, size_t rows,
+                              int N, const float* __restrict__ coef) {
+  const int Q = N / 4;
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= rows * Q) return;
+  const int q = (int)(t % Q);
+  const size_t row = t / Q;
+  float4* py = reinterpret_cast<float4*>(Y + fidx(row, 0, N, 4 * q));
+  float4* pyi = reinterpret_cast<float4*>(Y + fidx(row, 1, N, 4 * q));
+  const float4 y0 = *py, y1 = *pyi;
+  float yr[4] = {y0.x, y0.y, y0.z, y0.w}, yi[4] = {y1.x, y1.y, y1.z, y1.w};
+  for (int k = 0; k < K; ++k) {
+    const float4 c01 = *reinterpret_cast<const float4*>(coef + ((size_t)k * N + 4 * q) * 2);
+    const float4 c23 = *reinterpret_cast<const float4*>(coef + ((size_t)k * N + 4 * q) * 2 + 4);
+    const float cr[4] = {c01.x, c01.z, c23.x, c23.z}, ci[4] = {c01.y, c01.w, c23.y, c23.w};
+    const float* Xk = X + (size_t)k * stride;
+    const float4 x0 = *reinterpret_cast<const float4*>(Xk + fidx(row, 0, N, 4 * q));
+    const float4 x1 = *reinterpret_cast<const float4*>(Xk + fidx(row, 1, N, 4 * q));
+    const float xr[4] = {x0.x, x0.y, x0.z, x0.w}, xi[4] = {x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      yr[e] = fmaf(cr[e], xr[e], fmaf(-ci[e], xi[e], yr[e]));
+      yi[e] = fmaf(cr[e], xi[e], fmaf(ci[e], xr[e], yi[e]));
+    }
+  }
+  *py = make_float4(yr[0], yr[1], yr[2], yr[3]);
+  *pyi = make_float4(yi[0], yi[1], yi[2], yi[3]);
+}
+
 // s[r] = 1/sqrt(nrm2[r]) (0 for a zero vector), once per right-hand side
 __global__ void k_inv_sqrt(const double* nrm2, double* s, int N) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -147,6 +249,15 @@ __global__ void k_scale_by(S* X, size_t rows, int N, const double* s) {
   X[fidx(row, 1, N, r)] = from_r<S>(to_r(X[fidx(row, 1, N, r)]) * f);
 }
 
+// the four-RHS kernels need FP32, N % 4 == 0 and 16-byte aligned rows
+bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+bool use_dot4(const void* X, size_t stride, const void* Y, size_t rows, int N, int dtype, int nch) {
+  if (dtype != MRHS_F32 || N % 4 != 0 || N > 4 * kBlock || !aligned16(X) || !aligned16(Y) || stride % 4 != 0)
+    return false;
+  const size_t lanes = kBlock / (N / 4);
+  return (rows / nch + lanes - 1) / lanes <= (size_t)kMaxRows4;
+}
+
 }  // namespace
 
 void multi_dot(mrhs_ctx c, const void* X, size_t stride, int K, const void* Y, size_t rows, int N, int dtype,
@@ -156,7 +267,11 @@ void multi_dot(mrhs_ctx c, const void* X, size_t stride, int K, const void* Y, s
   double* part = (double*)scratch(c, SC_RED, sizeof(double) * 2 * (size_t)K * nch * N);
   dim3 grid(nch, (K + kKG - 1) / kKG);
   Prof pr(c, "multi_dot");
-  MRHS_DISPATCH(dtype, S, (k_multi_dot<S><<<grid, kBlock, 0, c->stream>>>((const S*)X, stride, K, (const S*)Y, rows, N, nch, part)));
+  if (use_dot4(X, stride, Y, rows, N, dtype, nch))
+    k_multi_dot4<<<dim3(nch, (K + kKG4 - 1) / kKG4), kBlock, 0, c->stream>>>((const float*)X, stride, K,
+                                                                             (const float*)Y, rows, N, nch, part);
+  else
+    MRHS_DISPATCH(dtype, S, (k_multi_dot<S><<<grid, kBlock, 0, c->stream>>>((const S*)X, stride, K, (const S*)Y, rows, N, nch, part)));
   MRHS_LAUNCH_CHECK("multi_dot");
   k_sum_chunks<<<grid_for((size_t)K * N * 32, 256), 256, 0, c->stream>>>(part, K, nch, N, out);
   MRHS_LAUNCH_CHECK("sum_chunks");
@@ -174,7 +289,11 @@ void multi_dot_ws(mrhs_ctx c, const void* X, size_t stride, int K, const void* Y
   int nch = n_chunks(rows, N);
   dim3 grid(nch, (K + kKG - 1) / kKG);
   Prof pr(c, "multi_dot");
-  MRHS_DISPATCH(dtype, S, (k_multi_dot<S><<<grid, kBlock, 0, c->stream>>>((const S*)X, stride, K, (const S*)Y, rows, N, nch, part)));
+  if (use_dot4(X, stride, Y, rows, N, dtype, nch))
+    k_multi_dot4<<<dim3(nch, (K + kKG4 - 1) / kKG4), kBlock, 0, c->stream>>>((const float*)X, stride, K,
+                                                                             (const float*)Y, rows, N, nch, part);
+  else
+    MRHS_DISPATCH(dtype, S, (k_multi_dot<S><<<grid, kBlock, 0, c->stream>>>((const S*)X, stride, K, (const S*)Y, rows, N, nch, part)));
   MRHS_LAUNCH_CHECK("multi_dot");
   k_sum_chunks<<<grid_for((size_t)K * N * 32, 256), 256, 0, c->stream>>>(part, K, nch, N, out);
   MRHS_LAUNCH_CHECK("sum_chunks");
@@ -195,7 +314,11 @@ void multi_axpy(mrhs_ctx c, const void* X, size_t stride, int K, void* Y, size_t
     MRHS_REQUIRE(K <= 65 && N <= 256, MRHS_ERR_ARG, "multi_axpy: K <= 65 and N <= 256");
     const int n = 2 * K * N;
     k_coef_to_float<<<grid_for(n, 256), 256, 0, c->stream>>>(coef, sign, c->coef32, n);
-    MRHS_DISPATCH(dtype, S, (k_multi_axpy<S, float><<<grid_for(work, kBlock), kBlock, 0, c->stream>>>((const S*)X, stride, K, (S*)Y, rows, N, (const float*)c->coef32, 1.0f)));
+    if (dtype == MRHS_F32 && N % 4 == 0 && aligned16(X) && aligned16(Y) && stride % 4 == 0)
+      k_multi_axpy4<<<grid_for(rows * (N / 4), kBlock), kBlock, 0, c->stream>>>((const float*)X, stride, K, (float*)Y,
+                                                                                rows, N, (const float*)c->coef32);
+    else
+      MRHS_DISPATCH(dtype, S, (k_multi_axpy<S, float><<<grid_for(work, kBlock), kBlock, 0, c->stream>>>((const S*)X, stride, K, (S*)Y, rows, N, (const float*)c->coef32, 1.0f)));
   }
   MRHS_LAUNCH_CHECK("multi_axpy");
 }
