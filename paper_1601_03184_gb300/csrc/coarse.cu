@@ -1,6 +1,7 @@
 // Coarse grid: D_c = P^dag D P assembly, restriction R = P^dag (Algorithm 3
 // of the paper, all right-hand sides at once), prolongation, the coarse
 // 9-point stencil and the multi-RHS coarse GMRES.
+#include <cstdint>
 #include <cstdlib>
 
 #include "coarse_common.cuh"
@@ -387,6 +388,50 @@ __global__ void k_prolong6(const SP* __restrict__ P, const SC* __restrict__ uc, 
   for (int cc = 0; cc < 6; ++cc) st<SU, R>(u, s * 12 + 6 * h + cc, N, r, acc[cc]);
 }
 
+// The same for FP32 coarse and fine fields with N % 4 == 0: four right-hand
+// sides per thread (16-byte loads of uc and stores of u), so every P entry
+// loaded serves 4 x 6 complex products; the scalar kernel's operations in
+// its order (the same bits).
+template <class SP>
+__global__ void k_prolong6x4(const SP* __restrict__ P, const float* __restrict__ uc, float* __restrict__ u, int Nt,
+                             int N, int Va, size_t nwork) {
+  const int Q = N / 4;
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= nwork) return;
+  const int r0 = 4 * (int)(t % Q);
+  const size_t q = t / Q;
+  const int h = (int)(q % 2);
+  const size_t s = q / 2;
+  const size_t A = s / Va;
+  float are[6][4], aim[6][4];
+#pragma unroll
+  for (int cc = 0; cc < 6; ++cc)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) are[cc][e] = aim[cc][e] = 0.f;
+  for (int j = 0; j < Nt; ++j) {
+    const size_t crow = A * 2 * Nt + h * Nt + j;
+    const float4 w0 = *reinterpret_cast<const float4*>(uc + fidx(crow, 0, N, r0));
+    const float4 w1 = *reinterpret_cast<const float4*>(uc + fidx(crow, 1, N, r0));
+    const float wr[4] = {w0.x, w0.y, w0.z, w0.w}, wi[4] = {w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+    for (int cc = 0; cc < 6; ++cc) {
+      const cx<float> pv = ld<SP, float>(P, s * 12 + 6 * h + cc, Nt, j);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        // fma_(acc, p, w): acc.re += p.re w.re - p.im w.im, acc.im += p.re w.im + p.im w.re
+        are[cc][e] = fmaf(-pv.im, wi[e], fmaf(pv.re, wr[e], are[cc][e]));
+        aim[cc][e] = fmaf(pv.im, wr[e], fmaf(pv.re, wi[e], aim[cc][e]));
+      }
+    }
+  }
+#pragma unroll
+  for (int cc = 0; cc < 6; ++cc) {
+    const size_t row = s * 12 + 6 * h + cc;
+    *reinterpret_cast<float4*>(u + fidx(row, 0, N, r0)) = make_float4(are[cc][0], are[cc][1], are[cc][2], are[cc][3]);
+    *reinterpret_cast<float4*>(u + fidx(row, 1, N, r0)) = make_float4(aim[cc][0], aim[cc][1], aim[cc][2], aim[cc][3]);
+  }
+}
+
 template <class S>
 __global__ void k_sub_from(const S* b, S* w, size_t n) {  // w = b - w
   size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -642,6 +687,12 @@ void prolong_typed(mrhs_ctx c, const void* uc, int dc, void* u, int du, int N) {
   MRHS_REQUIRE(dc == MRHS_F64 || dc == MRHS_F32, MRHS_ERR_ARG, "coarse fields are F64 or F32");
   size_t work = (size_t)c->g.V * 2 * N;
   Prof pr(c, "prolong");
+  if (dc == MRHS_F32 && du == MRHS_F32 && N % 4 == 0 && ((uintptr_t)uc & 15) == 0 && ((uintptr_t)u & 15) == 0) {
+    const size_t w4 = (size_t)c->g.V * 2 * (N / 4);
+    MRHS_DISPATCH(c->tv_dtype, SP, (k_prolong6x4<SP><<<grid_for(w4, 256), 256, 0, c->stream>>>((const SP*)c->P, (const float*)uc, (float*)u, c->ntv, N, c->g.Va, w4)));
+    MRHS_LAUNCH_CHECK("prolong");
+    return;
+  }
   MRHS_DISPATCH(c->tv_dtype, SP, MRHS_DISPATCH(du, SU, {
     if (dc == MRHS_F64)
       k_prolong6<SP, double, SU><<<grid_for(work, 256), 256, 0, c->stream>>>((const SP*)c->P, (const double*)uc, (SU*)u, c->ntv, N, c->g.Va, work);
