@@ -58,6 +58,25 @@ M0_FALLBACK = -0.45
 CPU_SAMPLE_DIMS = (8, 8, 8, 8)
 
 
+def reduce_max_over_ranks(x, dist=None, device="cuda"):
+    """The largest of the ranks' values of x, returned on every rank (x
+    itself when the run is not distributed). Times are reduced this way so
+    that the job is as slow as its slowest replica."""
+    if dist is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_seconds_per_setup(ms_per_step, world):
+    """Each of the `world` replicas completes one whole setup per step, so
+    the job delivers `world` setups in the slowest rank's step time."""
+    return ms_per_step / 1000.0 / world
+
+
 def load_m0(keys):
     """m0 from tests/golden/m0.json (written by tests/golden/tune_m0.py from the
     oracle), first key present wins."""
@@ -324,11 +343,8 @@ def run_ours(args, cfg, cfg_name, m0, m0_src, rank, world, local_rank):
     prof = pkg.mrhs_profile_read(lat.ctx)
     pkg.mrhs_profile(lat.ctx, 0)
     clk = clocks.stop()
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ms / 1000.0 / world  # seconds per setup for the whole job (N replicas per step)
+    ms = reduce_max_over_ranks(ms, dist)
+    value = whole_job_seconds_per_setup(ms, world)
 
     # ---- per-kernel profile and the roofline of the dominant kernel
     total = sum(v[1] for v in prof.values())
@@ -366,7 +382,8 @@ def run_ours(args, cfg, cfg_name, m0, m0_src, rank, world, local_rank):
     # ---- end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(args, lat, U, tv0, cfg, m0, stream)
+        e2e = run_e2e(args, lat, U, tv0, cfg, m0, stream, barrier)
+        e2e["value"] = whole_job_seconds_per_setup(1000.0 * reduce_max_over_ranks(e2e["value"], dist), world)
 
     # ---- the quality check of the plain setup: two-level FGMRES to 1e-10
     fg_plain = None
@@ -400,7 +417,7 @@ def run_ours(args, cfg, cfg_name, m0, m0_src, rank, world, local_rank):
         lat.close()
         del tv0
         torch.cuda.empty_cache()
-        line["learned_mixed"] = run_learned_mixed(args, cfg, U, m0, stream, ms, barrier)
+        line["learned_mixed"] = run_learned_mixed(args, cfg, U, m0, stream, ms, barrier, dist, world)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -422,7 +439,7 @@ def fgmres_check(lat, cfg, seed=3005):
             "tol": 1e-10, "restart": 10}
 
 
-def run_learned_mixed(args, cfg, U, m0, stream, plain_ms, barrier):
+def run_learned_mixed(args, cfg, U, m0, stream, plain_ms, barrier, dist=None, world=1):
     """Train the network on small seeded lattices of the same roughness and
     csw (16^4, 8 fields x 50 Adam steps on 8 vectors), then time the learned
     initial phase (1 SAP sweep + network) and the refinement with bf16 test
@@ -482,12 +499,14 @@ def run_learned_mixed(args, cfg, U, m0, stream, plain_ms, barrier):
     pkg.mrhs_profile(lat.ctx, 0)
     kernels = {k: {"launches": n // args.steps, "ms_per_step": t / args.steps, "share": t / args.steps / lm_ms}
                for k, (n, t) in prof.items()}
+    barrier()
+    lm_ms = reduce_max_over_ranks(lm_ms, dist)
     fg = None
     if not args.no_fgmres:
         pkg.mrhs_trim(lat.ctx)
         fg = fgmres_check(lat, cfg)
     lat.close()
-    return {"value": lm_ms / 1000.0, "unit": "s", "ratio_vs_plain": lm_ms / plain_ms,
+    return {"value": whole_job_seconds_per_setup(lm_ms, world), "unit": "s", "ratio_vs_plain": lm_ms / plain_ms,
             "form": "1 SAP sweep + network (widths %s, bf16 weights) for the initial phase, bf16 test vectors and P, "
                     "FP32 smoother, D_c contraction on bf16 tensor cores with FP32 accumulation (D_c stored FP32), "
                     "tf32 tensor-core coarse stencil, then the same refinement" % (list(learned.WIDTHS),),
@@ -497,7 +516,7 @@ def run_learned_mixed(args, cfg, U, m0, stream, plain_ms, barrier):
             "fgmres": fg}
 
 
-def run_e2e(args, lat, U, tv0, cfg, m0, stream):
+def run_e2e(args, lat, U, tv0, cfg, m0, stream, barrier=lambda: None):
     """Setup through the public C ABI from host buffers: gauge field in,
     clover, test vectors packed from host, setup, P and D_c copied out."""
     import torch
@@ -533,12 +552,14 @@ def run_e2e(args, lat, U, tv0, cfg, m0, stream):
 
     step()
     torch.cuda.synchronize()
+    barrier()
     steps = max(1, min(args.steps, args.e2e_steps))
     t0 = time.perf_counter()
     for _ in range(steps):
         step()
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / steps
+    barrier()
     h2d = U.nbytes + tv_host.numel() * 8
     d2h = p_host.numel() * 8 + dc_host.numel() * 8
     return {"value": dt, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
