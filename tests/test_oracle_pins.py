@@ -360,3 +360,66 @@ def test_init_modes_agree_for_one_sweep():
 def test_gamma5_fine_helper_consistent():
     g = gamma5_fine(2)
     assert g.shape == (24, 24) and np.allclose(np.diag(g)[:12], [1] * 6 + [-1] * 6)
+
+
+def test_mr_block_solve_minimises_the_block_residual():
+    """Right-hand side on one colour-0 domain B and x0 = 0: after one sweep,
+    x on B is the MR iterate for D_B e = b_B, since the colour-1 phase does not
+    touch B. Each MR step minimises the residual along D_B rho. So the block
+    residual never grows with n_mr. After one step the residual is orthogonal
+    to D_B b_B (a conjugated alpha breaks this) and x_B is parallel to b_B.
+    Many steps reach the dense block solve."""
+    U, A = c1_field()
+    dims, agg = C1["dims"], C1["agg"]
+    V = vol(dims)
+    sites = np.where(aggregate_of_sites(dims, agg) == 0)[0]
+    idx = (sites[:, None] * 12 + np.arange(12)[None, :]).reshape(-1)
+    DB = dense_D(dims, U, A)[np.ix_(idx, idx)]
+    b = np.zeros((1, V, 12), complex)
+    b[0, sites] = inputs.gaussian_field((len(sites), 12), 45)
+    bB = b.reshape(-1)[idx]
+    res = []
+    for n_mr in (1, 2, 3, 4, 8, 16):
+        xB = oracle.sap(dims, agg, U, A, b, np.zeros_like(b), 1, n_mr)[0].reshape(-1)[idx]
+        rB = bB - DB @ xB
+        res.append(np.linalg.norm(rB))
+        if n_mr == 1:
+            q = DB @ bB
+            assert abs(np.vdot(q, rB)) < 1e-13 * np.linalg.norm(q) * np.linalg.norm(bB)
+            alpha = np.vdot(bB, xB) / np.vdot(bB, bB)
+            assert np.abs(xB - alpha * bB).max() < 1e-14 * np.abs(xB).max()
+    assert res[0] < np.linalg.norm(bB)
+    assert all(res[i + 1] <= res[i] * (1 + 1e-13) for i in range(len(res) - 1))
+    xB = oracle.sap(dims, agg, U, A, b, np.zeros_like(b), 1, 400)[0].reshape(-1)[idx]
+    ref = np.linalg.solve(DB, bB)
+    assert np.abs(xB - ref).max() / np.abs(ref).max() < 1e-11
+
+
+def test_m0_tuning_on_the_free_field():
+    """The m0 tuning (tests/golden/tune_m0.py: ARPACK on the oracle's D) on the
+    unit gauge field against the closed-form free spectrum
+    lambda(p) = sum_mu (1 - cos p_mu) +/- i sqrt(sum_mu sin^2 p_mu) at m0 = 0,
+    with the antiperiodic p_t. The tuned m0 puts the leftmost real part at
+    1e-3 of the largest |lambda + m0|."""
+    import importlib.util
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "tune_m0.py")
+    spec = importlib.util.spec_from_file_location("tune_m0", path)
+    tune_m0 = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(tune_m0)
+    dims = (4, 4, 4, 4)
+    r = tune_m0.tune(dims, 0.0, 1.0, 7)
+    moms = [2 * np.pi * np.arange(dims[k]) / dims[k] for k in range(3)]
+    moms.append((2 * np.arange(dims[3]) + 1) * np.pi / dims[3])
+    lam = []
+    for p in itertools.product(*moms):
+        p = np.array(p)
+        a, b = np.sum(1 - np.cos(p)), np.sqrt(np.sum(np.sin(p) ** 2))
+        lam += [a + 1j * b, a - 1j * b]
+    lam = np.array(lam)
+    m0 = -lam.real.min()
+    for _ in range(50):
+        m0 = -lam.real.min() + tune_m0.RATIO * np.abs(lam + m0).max()
+    assert abs(r["m0"] - m0) < 1e-10
+    assert abs(r["lambda_max_at_m0"] - np.abs(lam + m0).max()) < 1e-8
