@@ -313,6 +313,31 @@ int mrhs_get_P(mrhs_ctx ctx, void* host, int host_dtype);
 /* copy D_c out: host [nagg][9][2ntv][2ntv] complex */
 int mrhs_get_Dc(mrhs_ctx ctx, void* host, int host_dtype);
 
+/* ------------------------------------------------- checkpoint / restore */
+
+/* Write the finished setup to the file `path`: the test vectors, P and D_c,
+ * the products of the setup phase (Sec. 2; Alg. 1/2) that later solves reuse.
+ * The file holds a header (format version, lattice and aggregate extents,
+ * ntv, precision, a hash of the device site order, the test-vector scale),
+ * the three device images in the context's storage types, and a checksum.
+ * The gauge field and the clover term are not in it. The file is first
+ * written as `path`.part and renamed to `path` only once it is complete; on
+ * failure the .part file is removed. MRHS_ERR_STATE before the setup has run
+ * (no P or no D_c). MRHS_ERR_ARG when the file cannot be written. Waits for
+ * the context's stream. */
+int mrhs_save_setup(mrhs_ctx ctx, const char* path);
+/* Replace the context's setup by the one in the file `path` (written by
+ * mrhs_save_setup), bit for bit, so that mrhs_apply_Dc, the coarse solves,
+ * mrhs_setup_refine and mrhs_solve_fgmres continue from it without a new
+ * setup. The context must have the file's lattice and aggregate extents, ntv
+ * and precision (MRHS_ERR_SHAPE otherwise). The gauge field and clover term
+ * are the caller's to set, as for any setup, before anything that applies D.
+ * MRHS_ERR_ARG for a file that cannot be opened, is not a checkpoint, is
+ * truncated or fails its checksum; after a failure past the header checks
+ * the context holds no setup (MRHS_ERR_STATE from calls that need one).
+ * Waits for the context's stream. */
+int mrhs_load_setup(mrhs_ctx ctx, const char* path);
+
 /* ---------------------------------------------------------- measurement */
 
 /* Per-kernel timing with CUDA events recorded on the context's stream around

@@ -65,6 +65,8 @@ _SIGS = {
     "mrhs_get_tv": (_I, [_VP, _VP, _I]),
     "mrhs_get_P": (_I, [_VP, _VP, _I]),
     "mrhs_get_Dc": (_I, [_VP, _VP, _I]),
+    "mrhs_save_setup": (_I, [_VP, ctypes.c_char_p]),
+    "mrhs_load_setup": (_I, [_VP, ctypes.c_char_p]),
     "mrhs_profile": (_I, [_VP, _I]),
     "mrhs_profile_read": (_I, [_VP, _I, ctypes.c_char_p, _I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D)]),
     "mrhs_nn_create": (_I, [_VP, ctypes.POINTER(_I), _I]),
@@ -279,6 +281,14 @@ def mrhs_get_P(ctx, host, host_dtype):
 
 def mrhs_get_Dc(ctx, host, host_dtype):
     return _check(ctx, lib().mrhs_get_Dc(ctx, _ptr(host), int(host_dtype)))
+
+
+def mrhs_save_setup(ctx, path):
+    return _check(ctx, lib().mrhs_save_setup(ctx, os.fsencode(str(path))))
+
+
+def mrhs_load_setup(ctx, path):
+    return _check(ctx, lib().mrhs_load_setup(ctx, os.fsencode(str(path))))
 
 
 def mrhs_profile(ctx, enable):

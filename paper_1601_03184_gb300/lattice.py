@@ -11,7 +11,8 @@ from . import (MRHS_F32, MRHS_F64, MRHS_PREC_FP64, mrhs_apply_D, mrhs_apply_D_bl
                mrhs_build_clover, mrhs_build_Dc, mrhs_build_P, mrhs_coarse_solve, mrhs_create, mrhs_destroy,
                mrhs_set_dc_engine,
                mrhs_field_bytes, mrhs_get_clover, mrhs_get_Dc, mrhs_get_P, mrhs_get_tables, mrhs_get_tv,
-               mrhs_info, mrhs_pack, mrhs_pack_coarse, mrhs_prolong, mrhs_restrict, mrhs_sap, mrhs_set_gauge,
+               mrhs_info, mrhs_load_setup, mrhs_pack, mrhs_pack_coarse, mrhs_prolong, mrhs_restrict, mrhs_sap,
+               mrhs_save_setup, mrhs_set_gauge,
                mrhs_set_tv, mrhs_setup_init, mrhs_setup_refine, mrhs_solve_fgmres, mrhs_sync, mrhs_unpack,
                mrhs_unpack_coarse)
 
@@ -150,6 +151,12 @@ class Lattice:
         it, rr, st = mrhs_solve_fgmres(self.ctx, b, x, tol, restart, maxit, coarse_tol, coarse_restart,
                                        coarse_maxit, n_sweeps, n_mr, allow_noconv=allow_noconv)
         return x, it, rr
+
+    def save_setup(self, path):
+        mrhs_save_setup(self.ctx, path)
+
+    def load_setup(self, path):
+        mrhs_load_setup(self.ctx, path)
 
     def info(self):
         return mrhs_info(self.ctx)

@@ -69,3 +69,10 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(pkg, "_lib", None)
     with pytest.raises(pkg.MrhsError):
         pkg.lib()
+
+
+def test_checkpoint_calls_refuse_null_arguments(lib):
+    # argument checks come before any device work, so they run without a GPU
+    assert pkg.lib().mrhs_save_setup(None, b"setup.bin") == pkg.MRHS_ERR_ARG
+    assert pkg.lib().mrhs_load_setup(None, b"setup.bin") == pkg.MRHS_ERR_ARG
+    assert b"null" in pkg.lib().mrhs_last_error(None)
