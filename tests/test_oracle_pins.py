@@ -15,7 +15,7 @@ import pytest
 import oracle
 from paper_1601_03184_gb300 import inputs
 from lattice_helpers import (aggregate_of_sites, colour_rotate, coords, dense_coarse, dense_D,
-                             dense_P, gamma5_fine, gauge_transform, vol)
+                             dense_P, gamma5_fine, gauge_transform, shift_index, vol)
 
 C1 = dict(dims=(4, 4, 4, 4), agg=(2, 2, 2, 2), ntv=8, eps=0.3, m0=-0.2, csw=1.0, gseed=1001, tvseed=2001)
 
@@ -102,6 +102,42 @@ def test_clover_hermitian_chiral_and_covariant():
     O12 = np.einsum("ij,sab->siajb", np.eye(4), Om).reshape(-1, 12, 12)
     ref = O12 @ A @ np.conj(np.swapaxes(O12, 1, 2))
     assert np.abs(At - ref).max() < 1e-13
+
+
+@pytest.mark.parametrize("plane", [(0, 1), (1, 3), (2, 3)])
+def test_clover_covariant_under_a_lattice_rotation(plane):
+    """Rotate a random gauge field by 90 degrees in the plane (mu, nu):
+    x -> R x with R e_mu = e_nu and R e_nu = -e_mu. The clover term of the
+    rotated field at R x is S A(x) S^dag for one fixed spin rotation
+    S = cos(pi/4) + sin(pi/4) gamma_mu gamma_nu (either sense), the same at
+    every site. This holds only if all six planes and the four leaves of each
+    clover are oriented consistently."""
+    mu, nu = plane
+    dims = (4, 4, 4, 4)
+    U = inputs.gauge_field(dims, 0.6, 13)
+    A = oracle.clover(dims, U, -0.2, 1.5)
+    X = coords(dims)
+    Xr = X.copy()
+    Xr[:, nu] = X[:, mu]
+    Xr[:, mu] = (-X[:, nu]) % dims[mu]
+    lex = lambda c: c[:, 0] + dims[0] * (c[:, 1] + dims[1] * (c[:, 2] + dims[2] * c[:, 3]))
+    r = lex(Xr)
+    Ur = np.empty_like(U)
+    for rho in range(4):
+        if rho not in plane:
+            Ur[r, rho] = U[:, rho]
+    # the link x -> x + e_mu becomes R x -> R x + e_nu
+    Ur[r, nu] = U[:, mu]
+    # the link x -> x - e_nu becomes R x -> R x + e_mu
+    Ur[r, mu] = np.conj(np.swapaxes(U[shift_index(dims, nu, -1), nu], -1, -2))
+    Ar = oracle.clover(dims, Ur, -0.2, 1.5)
+    G = oracle.gammas()
+    errs = []
+    for sense in (1, -1):
+        S = np.kron(np.cos(np.pi / 4) * np.eye(4) + sense * np.sin(np.pi / 4) * G[mu] @ G[nu], np.eye(3))
+        errs.append(np.abs(Ar[r] - S @ A @ S.conj().T).max())
+    assert min(errs) < 1e-13
+    assert max(errs) > 1e-3  # the other sense is wrong: the check has teeth
 
 
 # ---------------------------------------------------------- Dirac operator --
