@@ -60,6 +60,49 @@ def test_gamma_clifford_and_chiral_basis():
             assert np.allclose(sig @ G[4], G[4] @ sig)  # chirality block diagonal
 
 
+# ------------------------------------------------------------ index tables --
+@pytest.mark.parametrize("dims,agg", [((4, 4, 4, 4), (2, 2, 2, 2)), ((4, 6, 4, 8), (2, 3, 2, 2)),
+                                      ((2, 4, 6, 2), (1, 2, 3, 1))],
+                         ids=["4^4", "ragged", "extent-2"])
+def test_index_tables_by_enumeration(dims, agg):
+    """The oracle's neighbour and aggregate tables against a plain enumeration
+    of the lattice: site s = x + Lx (y + Ly (z + Lz t)); entry k < 4 is
+    s + mu_hat and k >= 4 is s - mu_hat, periodic, with bit 30 set when the
+    hop wraps around in t (the fermion boundary sign); aggregates and offsets
+    in the same lexicographic order on block and intra-block coordinates;
+    aggregate neighbours periodic on the block lattice. Extent 2 makes the
+    forward and backward neighbour the same site, with different t flags."""
+    def lex(c, ext):
+        return c[0] + ext[0] * (c[1] + ext[1] * (c[2] + ext[2] * c[3]))
+
+    nb = [d // a for d, a in zip(dims, agg)]
+    V, na = vol(dims), int(np.prod(nb))
+    nbr = np.zeros((V, 8), np.int64)
+    aggof = np.zeros((V, 2), np.int64)
+    for t, z, y, x in itertools.product(*[range(d) for d in dims[::-1]]):
+        c = [x, y, z, t]
+        s = lex(c, dims)
+        for mu in range(4):
+            for k, step in ((mu, 1), (4 + mu, -1)):
+                n = list(c)
+                n[mu] = (c[mu] + step) % dims[mu]
+                wraps = mu == 3 and not 0 <= c[mu] + step < dims[mu]
+                nbr[s, k] = lex(n, dims) | (int(wraps) << 30)
+        aggof[s] = (lex([c[m] // agg[m] for m in range(4)], nb), lex([c[m] % agg[m] for m in range(4)], agg))
+    aggnbr = np.zeros((na, 8), np.int64)
+    for bt, bz, by, bx in itertools.product(*[range(n) for n in nb[::-1]]):
+        b = [bx, by, bz, bt]
+        for mu in range(4):
+            for k, step in ((mu, 1), (4 + mu, -1)):
+                n = list(b)
+                n[mu] = (b[mu] + step) % nb[mu]
+                aggnbr[lex(b, nb), k] = lex(n, nb)
+    onbr, oaggof, oaggnbr = oracle.tables(dims, agg)
+    assert np.array_equal(onbr, nbr)
+    assert np.array_equal(oaggof, aggof)
+    assert np.array_equal(oaggnbr, aggnbr)
+
+
 # ---------------------------------------------------------------- clover ----
 def test_clover_unit_field():
     dims = (4, 4, 4, 4)
