@@ -408,6 +408,60 @@ def test_setup_and_fgmres_c1():
     assert np.abs(x.reshape(-1) - xd).max() < 1e-8 * np.abs(xd).max()
 
 
+def _dense_sap_exact(D, Ag, colour, b, x, n_sweeps):
+    """Red-black multiplicative Schwarz with exact domain solves: the SAP
+    sweep of Sec. 2 in the limit of many MR steps."""
+    x = x.copy()
+    for _ in range(n_sweeps):
+        for col in (0, 1):
+            r = b - D @ x
+            for Bk in np.unique(Ag[colour == col]):
+                idx = np.concatenate([np.arange(s * 12, s * 12 + 12) for s in np.where(Ag == Bk)[0]])
+                x[idx] += np.linalg.solve(D[np.ix_(idx, idx)], r[idx])
+    return x
+
+
+def test_setup_phases_with_exact_domain_and_coarse_solves():
+    """Initial phase: v_j <- SAP^n(b = v_j, x0 = 0), normalised. Refinement
+    (Alg. 1 order, P and D_c fixed while the vectors are visited):
+    v_j <- SAP^nu(b = v_j, x0 = P D_c^-1 R v_j), normalised, then P and D_c
+    rebuilt. With 400 MR steps per domain and a coarse tolerance of 1e-13 the
+    oracle must reproduce these phases written with dense block solves, a
+    dense coarse solve and the dense P^dag D P."""
+    dims, agg, ntv = C1["dims"], C1["agg"], 4
+    U, A = c1_field()
+    D = dense_D(dims, U, A)
+    Ag = aggregate_of_sites(dims, agg)
+    nb = [d // a for d, a in zip(dims, agg)]
+    bc = np.stack(np.unravel_index(Ag, nb[::-1]), axis=1)[:, ::-1]
+    colour = bc.sum(axis=1) % 2
+    tv0 = inputs.test_vectors(ntv, dims, 95)
+    prm = oracle.make_params(n_init_sweeps=2, n_init_mr=400, n_refine=1, n_smooth_sweeps=2, n_smooth_mr=400,
+                             coarse_tol=1e-13, coarse_restart=40, coarse_maxit=4000)
+    tv, P, Dc = oracle.setup_init(dims, agg, U, A, tv0, prm)
+    ref = []
+    for j in range(ntv):
+        v = _dense_sap_exact(D, Ag, colour, tv0[j].reshape(-1), np.zeros(D.shape[0], complex), 2)
+        ref.append(v / np.linalg.norm(v))
+    ref = np.array(ref).reshape(tv.shape)
+    assert np.abs(tv - ref).max() < 1e-10
+
+    tv1, P1, Dc1, _ = oracle.setup_refine(dims, agg, U, A, tv, P, Dc, prm)
+    Pd = dense_P(dims, agg, P)
+    Dcd = Pd.conj().T @ D @ Pd
+    ref = []
+    for j in range(ntv):
+        v = tv[j].reshape(-1)
+        x0 = Pd @ np.linalg.solve(Dcd, Pd.conj().T @ v)
+        x = _dense_sap_exact(D, Ag, colour, v, x0, 2)
+        ref.append(x / np.linalg.norm(x))
+    ref = np.array(ref).reshape(tv.shape)
+    assert np.abs(tv1 - ref).max() < 1e-9
+    Pd1 = dense_P(dims, agg, P1)
+    assert np.abs(Pd1.conj().T @ Pd1 - np.eye(Pd1.shape[1])).max() < 1e-13
+    assert np.abs(dense_coarse(dims, agg, Dc1) - Pd1.conj().T @ D @ Pd1).max() < 1e-11
+
+
 def test_setup_gauge_invariance():
     """U -> U^Om and tv -> Om tv leave D_c unchanged and map P -> Om P."""
     dims, agg, ntv = C1["dims"], C1["agg"], 4
