@@ -462,6 +462,33 @@ def test_setup_phases_with_exact_domain_and_coarse_solves():
     assert np.abs(dense_coarse(dims, agg, Dc1) - Pd1.conj().T @ D @ Pd1).max() < 1e-11
 
 
+def test_fgmres_first_step_is_the_preconditioned_minimal_residual_step():
+    """Right-preconditioned FGMRES from x0 = 0: after one iteration
+    x = alpha z with z = M b the V-cycle of Sec. 2 (coarse correction
+    x0 = P D_c^-1 R b, then nu SAP sweeps on D x = b) and alpha minimising
+    |b - alpha D z|. With exact domain and coarse solves, M is written here
+    with dense linear algebra; a smoother-first or coarse-only V-cycle fails."""
+    dims, agg, ntv = C1["dims"], C1["agg"], 4
+    U, A = c1_field()
+    D = dense_D(dims, U, A)
+    Ag = aggregate_of_sites(dims, agg)
+    nb = [d // a for d, a in zip(dims, agg)]
+    colour = np.stack(np.unravel_index(Ag, nb[::-1]), axis=1)[:, ::-1].sum(axis=1) % 2
+    tv, P, Dc = oracle.setup_init(dims, agg, U, A, inputs.test_vectors(ntv, dims, 96), oracle.make_params())
+    b = inputs.gaussian_field((vol(dims), 12), 97)
+    x, it, rr = oracle.fgmres(dims, agg, U, A, P, Dc, b, tol=1e-30, restart=25, maxit=1, coarse_tol=1e-13,
+                              coarse_restart=40, coarse_maxit=4000, n_sweeps=2, n_mr=400)
+    assert it == 1
+    Pd = dense_P(dims, agg, P)
+    bb = b.reshape(-1)
+    x0 = Pd @ np.linalg.solve(Pd.conj().T @ D @ Pd, Pd.conj().T @ bb)
+    z = _dense_sap_exact(D, Ag, colour, bb, x0, 2)
+    Dz = D @ z
+    ref = (np.vdot(Dz, bb) / np.vdot(Dz, Dz)) * z
+    assert np.abs(x.reshape(-1) - ref).max() < 1e-9 * np.abs(ref).max()
+    assert abs(rr - np.linalg.norm(bb - D @ ref) / np.linalg.norm(bb)) < 1e-9
+
+
 def test_setup_gauge_invariance():
     """U -> U^Om and tv -> Om tv leave D_c unchanged and map P -> Om P."""
     dims, agg, ntv = C1["dims"], C1["agg"], 4
