@@ -76,3 +76,42 @@ def test_checkpoint_calls_refuse_null_arguments(lib):
     assert pkg.lib().mrhs_save_setup(None, b"setup.bin") == pkg.MRHS_ERR_ARG
     assert pkg.lib().mrhs_load_setup(None, b"setup.bin") == pkg.MRHS_ERR_ARG
     assert b"null" in pkg.lib().mrhs_last_error(None)
+
+
+def test_header_is_plain_c_and_links(lib, tmp_path):
+    """A C99 program that includes mrhs.h, takes the address of every declared
+    entry point and links against libmrhs.so: the boundary needs no C++ or
+    torch type. It then runs the argument checks that need no GPU."""
+    import shutil
+    import subprocess
+
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    names = declared_functions()
+    src = tmp_path / "use_abi.c"
+    src.write_text(
+        "#include <stdio.h>\n#include <string.h>\n#include \"mrhs.h\"\n"
+        "typedef void (*any_fn)(void);\n"
+        "static const any_fn table[] = {\n" + ",\n".join("  (any_fn)%s" % n for n in names) + "\n};\n"
+        "int main(void) {\n"
+        "  const int dims[4] = {4, 4, 4, 4}, bad_agg[4] = {3, 2, 2, 2};\n"
+        "  mrhs_ctx ctx = NULL;\n"
+        "  size_t i;\n"
+        "  for (i = 0; i < sizeof table / sizeof table[0]; ++i)\n"
+        "    if (!table[i]) return 10;\n"
+        "  if (mrhs_create(dims, bad_agg, 4, MRHS_PREC_FP64, NULL, &ctx) != MRHS_ERR_SHAPE) return 11;\n"
+        "  if (ctx != NULL || strlen(mrhs_last_error(NULL)) == 0) return 12;\n"
+        "  if (mrhs_save_setup(NULL, \"setup.bin\") != MRHS_ERR_ARG) return 13;\n"
+        "  if (mrhs_load_setup(NULL, \"setup.bin\") != MRHS_ERR_ARG) return 14;\n"
+        "  mrhs_destroy(NULL);\n"
+        "  printf(\"%u entry points\\n\", (unsigned)(sizeof table / sizeof table[0]));\n"
+        "  return 0;\n"
+        "}\n")
+    exe = tmp_path / "use_abi"
+    libdir = os.path.dirname(pkg.LIB_PATH)
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I",
+                           os.path.join(ROOT, "include"), str(src), "-o", str(exe), "-L", libdir, "-lmrhs",
+                           "-Wl,-rpath," + libdir])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, (out.returncode, out.stderr)
+    assert out.stdout.strip() == "%d entry points" % len(names)
