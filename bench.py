@@ -242,6 +242,11 @@ def cpu_sample(cfg, m0):
 def run_reference(args, cfg, cfg_name, m0, m0_src, rank, world):
     if rank != 0:
         return
+    if world > 1:
+        # torchrun limits every rank to one OpenMP thread; the other ranks do
+        # no work in this arm, so the oracle on rank 0 takes every host core
+        # (read by the OpenMP runtime when the oracle library is loaded)
+        os.environ["OMP_NUM_THREADS"] = str(os.cpu_count() or 1)
     times = []
     threads = 1
     desc = ""
@@ -408,7 +413,7 @@ def run_ours(args, cfg, cfg_name, m0, m0_src, rank, world, local_rank):
         "gpu_launches": gpu_launches,
         "e2e": e2e,
     }
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, scaled, threads, desc = cpu_sample(cfg, m0)
         line["cpu_baseline"] = {"value": scaled, "unit": "s", "cores": threads, "kind": "oracle", "sample": desc}
     line["fgmres_plain"] = fg_plain

@@ -89,3 +89,21 @@ def test_reference_arm_line_on_rank_zero(capsys, monkeypatch):
     assert line["e2e"] == {"value": line["value"], "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert line["cpu_baseline"]["cores"] == 16 and line["cpu_baseline"]["kind"] == "oracle"
     assert line["higher_is_better"] is False and line["n_gpus"] == 2
+
+
+def test_reference_arm_on_rank_zero_uses_every_host_core(capsys, monkeypatch):
+    """torchrun sets OMP_NUM_THREADS=1 for each rank; in the reference arm only
+    rank 0 works, so it lifts that limit before the oracle library loads."""
+    seen = []
+
+    def fake_sample(cfg, m0):
+        seen.append(os.environ.get("OMP_NUM_THREADS"))
+        return 1.0, 1.0, int(seen[-1]), "fake sample"
+
+    monkeypatch.setenv("OMP_NUM_THREADS", "1")
+    monkeypatch.setattr(bench, "cpu_sample", fake_sample)
+    args = argparse.Namespace(steps=1, warmup=0)
+    cfg = bench.CONFIGS[bench.DEFAULT_CONFIG]
+    bench.run_reference(args, cfg, bench.DEFAULT_CONFIG, -0.4, "test", rank=0, world=2)
+    capsys.readouterr()
+    assert seen == [str(os.cpu_count() or 1)]
