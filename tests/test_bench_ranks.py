@@ -77,6 +77,7 @@ def test_reference_arm_line_on_rank_zero(capsys, monkeypatch):
         return 1.0, 40.0 + len(calls), 16, "fake sample"
 
     monkeypatch.setattr(bench, "cpu_sample", fake_sample)
+    monkeypatch.delenv("OMP_NUM_THREADS", raising=False)  # restored after the test
     args = argparse.Namespace(steps=2, warmup=3)
     cfg = bench.CONFIGS[bench.DEFAULT_CONFIG]
     bench.run_reference(args, cfg, bench.DEFAULT_CONFIG, -0.4, "test", rank=0, world=2)
