@@ -32,11 +32,13 @@
  *    library's own pack/unpack calls write or read this order; use
  *    mrhs_field_bytes for sizes.
  *  - Coarse fields: per aggregate 2*ntv complex values (index h*ntv + j,
- *    Sec. 2: "coarse-grid dof 2 Ntv"). Host layout [nrhs][nagg][2ntv]
+ *    2 N_tv coarse degrees of freedom per aggregate, Sec. 4 with Eq. 1, and
+ *    Alg. 3).
+ *    Host layout [nrhs][nagg][2ntv]
  *    complex; device layout ((A*2ntv + i)*2 + re/im)*nrhs + rhs.
  *  - Aggregates are lattice blocks of agg[0]x..xagg[3] sites in
  *    lexicographic block order. They are also the Schwarz domains of the SAP
- *    smoother (Sec. 2, domain size 4^4 in Sec. 6).
+ *    smoother (Sec. 2, domain size 4^4 in Sec. 7).
  */
 #ifndef MRHS_H
 #define MRHS_H
@@ -137,7 +139,7 @@ int mrhs_unpack_coarse(mrhs_ctx ctx, const void* dev, int dev_dtype, void* host,
 /* ------------------------------------------------------------ operators */
 
 /* y = D x for nrhs right-hand sides at once (multi-RHS Wilson-clover
- * stencil; the "Dirac equation" operator of Sec. 1-2):
+ * stencil; the operator whose linear system the solver of Sec. 1-2 targets):
  * y(x) = A(x) x(x) - 1/2 sum_mu [(1-gamma_mu) U_mu(x) x(x+mu)
  *                              + (1+gamma_mu) U_mu(x-mu)^dag x(x-mu)].
  * x, y: device interleaved fields of storage dtype (F64 computes in double,
@@ -166,8 +168,8 @@ int mrhs_sap(mrhs_ctx ctx, const void* b, void* x, int nrhs, int dtype, int n_sw
 int mrhs_set_tv(mrhs_ctx ctx, const void* tv, int dtype);
 
 /* P from the test vectors: per aggregate A and chirality h the vectors
- * v_1..v_ntv restricted to A x h are orthonormalised in order (Sec. 2:
- * "construct restriction R, prolongation P = R^dag"); the result is the Q
+ * v_1..v_ntv restricted to A x h are orthonormalised in order (Sec. 2: the
+ * test vectors define P, and R is its adjoint); the result is the Q
  * factor of the thin QR with positive real diagonal, computed on the GPU
  * by two Cholesky-QR passes with double-precision Gram matrices.
  * MRHS_ERR_NONFINITE if a vector set is (numerically) dependent. */
@@ -216,7 +218,7 @@ int mrhs_prolong(mrhs_ctx ctx, const void* uc, void* u, int nrhs, int dtype);
  * contexts, single tf32 for the mixed ones; otherwise on the CUDA cores. */
 int mrhs_apply_Dc(mrhs_ctx ctx, const void* xc, void* yc, int nrhs, int dtype);
 
-/* Coarse solve "to low accuracy" (Algorithm 1/2, tolerance 0.05 in Sec. 6):
+/* Approximate coarse solve of Algorithm 1/2 (relative tolerance 0.05 in Sec. 7):
  * GMRES(restart) on D_c xc = bc from xc = 0 for every right-hand side at
  * once, each with its own Krylov space; a right-hand side stops when its
  * residual estimate reaches tol*|bc| or after maxit iterations in total.

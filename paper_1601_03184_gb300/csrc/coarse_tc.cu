@@ -1,7 +1,7 @@
 // Coarse-operator contraction D_c[A,k] = P_A^dag (D_k P) on the fifth-
 // generation tensor cores (tcgen05), for the mixed-precision setup: the
-// link products are dense 2N_tv x 2N_tv blocks (Sec. 3.2 / Eq. 6 of the
-// paper: D_c = P^dag D P with the aggregate-local structure of P).
+// link products are dense 2N_tv x 2N_tv blocks (Sec. 2 of the paper builds
+// D_c from P = R^dag; D_c = P^dag D P with the aggregate-local structure of P).
 //
 // One CTA per (aggregate A, k in 0..4): k = 0 the self block, k = 1+mu the
 // forward block towards A+mu. Sites of the block (all of A for k = 0, the +mu

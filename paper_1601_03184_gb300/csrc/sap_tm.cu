@@ -1,4 +1,4 @@
-// SAP sweep (Sec. 3.1 of the paper; red-black multiplicative Schwarz with
+// SAP sweep (Sec. 2 of the paper; red-black multiplicative Schwarz with
 // minimal-residual block solves) with the whole state of a domain on chip.
 //
 // Per colour, one CTA per (domain, chunk of G right-hand sides): the CTAs of a

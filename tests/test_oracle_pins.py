@@ -4,7 +4,7 @@ to library routines (dense eigenvalues, QR, linear solves, least squares) and
 brute-force dense constructions on tiny lattices.
 
 The paper (arXiv:1601.03184) prints no worked numerical example for any
-operator (its Sec. 6 gives only speed-up ratios), so every pin here is
+operator (its Sec. 7 gives only speed-up ratios), so every pin here is
 mathematical.
 """
 import itertools
