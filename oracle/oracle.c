@@ -112,7 +112,9 @@ static int aggregate_neighbour(const geom_t* g, int A, int mu, int dir) {
   return index_of(g->nb, b);
 }
 
-/* Neighbour/aggregate tables in canonical order.
+/* Neighbour/aggregate tables in canonical order (the lattice blocks of
+ * Sec. 2: aggregates of the coarse grid, which are also the Schwarz domains
+ * of the smoother; domain size 4^4 in Sec. 7).
  *   nbr[s][k]    k = 0..3: s + mu_hat, k = 4..7: s - mu_hat; value = site
  *                index, with bit 30 set when the hop crosses the t boundary
  *   aggof[s][2]  (aggregate index, offset of s inside its aggregate)
@@ -250,7 +252,9 @@ static int step2(const geom_t* g, int s, int mu1, int d1, int mu2, int d2) {
 /* ------------------------------------------------------------------ */
 /* clover term                                                          */
 /* ------------------------------------------------------------------ */
-/* A(x) = (4 + m0) 1 + (csw/2) sum_{mu<nu} i sigma_{mu nu} (x) Fhat_{mu nu}(x),
+/* Clover term of the Wilson-clover operator (Sec. 1-2; the paper takes the
+ * operator from its references, this is the standard clover form):
+ * A(x) = (4 + m0) 1 + (csw/2) sum_{mu<nu} i sigma_{mu nu} (x) Fhat_{mu nu}(x),
  * Fhat = (Q - Q^dag)/8 with Q the sum of the four plaquettes of the mu-nu
  * plane that touch x (clover leaf). Output: full 12x12 per site. */
 int ora_clover(const int* dims, const cplx* U, double m0, double csw, cplx* A) {
@@ -304,7 +308,9 @@ int ora_clover(const int* dims, const cplx* U, double m0, double csw, cplx* A) {
 /* ------------------------------------------------------------------ */
 /* Wilson-clover operator                                               */
 /* ------------------------------------------------------------------ */
-/* y(x) = A(x) psi(x)
+/* The Wilson-clover operator D of the linear system that the solver of
+ * Sec. 1-2 targets:
+ * y(x) = A(x) psi(x)
  *      - 1/2 sum_mu [ (1 - gamma_mu) U_mu(x) psi(x+mu)
  *                   + (1 + gamma_mu) U_mu(x-mu)^dag psi(x-mu) ]
  * with a factor -1 on hops across the t boundary. If block >= 0 only sites
@@ -397,7 +403,9 @@ static int* aggregate_sites(const geom_t* g) {
 /* ------------------------------------------------------------------ */
 /* SAP smoother: red-black multiplicative Schwarz, MR block solves      */
 /* ------------------------------------------------------------------ */
-/* One sweep = colour 0 then colour 1 (colour = parity of the sum of the
+/* The domain-decomposition smoother of Sec. 2 (Schwarz alternating
+ * procedure), used in the initial phase and in the V-cycle of Algorithm 1.
+ * One sweep = colour 0 then colour 1 (colour = parity of the sum of the
  * aggregate coordinates). Per colour: r = b - D x; then for every aggregate
  * B of that colour, n_mr minimal-residual steps on D_B e = r_B from e = 0:
  *   q = D_B rho, alpha = <q,rho>/<q,q>, e += alpha rho, rho -= alpha q;
@@ -470,7 +478,9 @@ int ora_sap(const int* dims, const int* agg, const cplx* U, const cplx* A, const
 /* ------------------------------------------------------------------ */
 /* aggregate-wise Gram-Schmidt -> P = R^dag                              */
 /* ------------------------------------------------------------------ */
-/* For every aggregate A and chirality h, the test vectors restricted to
+/* P = R^dag from the test vectors (Sec. 2), aggregate by aggregate and
+ * split by chirality as in Algorithm 3 (Sec. 5).
+ * For every aggregate A and chirality h, the test vectors restricted to
  * (sites of A) x (components of chirality h) are orthonormalised in order
  * j = 0..ntv-1 by modified Gram-Schmidt, applied twice. Column j of P is the
  * orthonormalised vector j; within chirality h it is the column (h, j) of
@@ -521,7 +531,8 @@ int ora_gram_schmidt(const int* dims, const int* agg, int ntv, const cplx* tv, c
 /* ------------------------------------------------------------------ */
 /* restriction, prolongation (R = P^dag)                                */
 /* ------------------------------------------------------------------ */
-/* vc[A][h*ntv + j] = sum_{s in A, c in h} conj(P_j(s,c)) v(s,c) */
+/* restriction R = P^dag (Sec. 2; the sum of Algorithm 3, Sec. 5):
+ * vc[A][h*ntv + j] = sum_{s in A, c in h} conj(P_j(s,c)) v(s,c) */
 static void restrict_one(const geom_t* g, int ntv, const cplx* P, const cplx* v, cplx* vc) {
   size_t n = (size_t)g->V * 12;
   for (int i = 0; i < g->nagg * 2 * ntv; ++i) vc[i] = 0;
@@ -535,7 +546,8 @@ static void restrict_one(const geom_t* g, int ntv, const cplx* P, const cplx* v,
   }
 }
 
-/* u(s,c) = sum_j P_j(s,c) uc[A(s)][h(c)*ntv + j] */
+/* prolongation P (Sec. 2, Algorithm 1):
+ * u(s,c) = sum_j P_j(s,c) uc[A(s)][h(c)*ntv + j] */
 static void prolong_one(const geom_t* g, int ntv, const cplx* P, const cplx* uc, cplx* u) {
   size_t n = (size_t)g->V * 12;
   for (int s = 0; s < g->V; ++s) {
@@ -570,7 +582,9 @@ int ora_prolong(const int* dims, const int* agg, int ntv, const cplx* P, const c
 /* ------------------------------------------------------------------ */
 /* coarse operator Dc = P^dag D P as a 9-point stencil                   */
 /* ------------------------------------------------------------------ */
-/* The hopping terms of D are routed by the aggregate they connect:
+/* The coarse-grid operator of Sec. 2, D_c = R D P (Galerkin product with
+ * R = P^dag), as a nearest-neighbour stencil on the aggregates.
+ * The hopping terms of D are routed by the aggregate they connect:
  *   k = 0      A(x) psi(x) and hops with both ends in the same aggregate
  *   k = 1+mu   the +mu hop of x when x+mu lies in another aggregate
  *   k = 5+mu   the -mu hop of x when x-mu lies in another aggregate
@@ -680,7 +694,9 @@ int ora_apply_Dc(const int* dims, const int* agg, int ntv, const cplx* Dc, const
 /* ------------------------------------------------------------------ */
 typedef void (*op_fn)(void* ctx, const cplx* in, cplx* out);
 
-/* Solves op x = b from x = 0. Stops when the residual estimate falls to
+/* The approximate coarse solve of Algorithm 1 (relative tolerance 0.05 in
+ * Sec. 7) and the outer FGMRES of Sec. 2.
+ * Solves op x = b from x = 0. Stops when the residual estimate falls to
  * tol*|b| or after maxit iterations in total (restarting every m). With
  * precond != NULL it is right-preconditioned flexible GMRES: z_k = M v_k is
  * stored and x is built from the z_k. Returns the iteration count. */
@@ -827,8 +843,9 @@ static void normalise(cplx* v, size_t n) {
     for (size_t i = 0; i < n; ++i) v[i] /= nn;
 }
 
-/* Initial phase: the smoother on every test vector from x0 = 0, normalise,
- * then P (Gram-Schmidt) and Dc. tv is updated in place. */
+/* Initial phase of the setup (Sec. 2): the smoother on every test vector
+ * from x0 = 0, normalise, then P (Gram-Schmidt) and Dc. tv is updated in
+ * place. */
 int ora_setup_init(const int* dims, const int* agg, int ntv, const cplx* U, const cplx* A,
                    cplx* tv, const ora_setup_params* p, cplx* P, cplx* Dc) {
   geom_t g;
@@ -918,7 +935,10 @@ static void fine_op(void* c, const cplx* in, cplx* out) {
   for (int s = 0; s < m->g.V; ++s) apply_D_site(&m->g, m->U, m->A, in, out, s, -1);
 }
 
-/* V-cycle: z = SAP^nu(b = r, x0 = P GMRES_c(R r)) (post-smoothing only) */
+/* V-cycle preconditioner of the outer FGMRES (Sec. 2), steps in the order
+ * of the V-cycle of Algorithm 1: coarse-grid correction, then the smoother
+ * from its result: z = SAP^nu(b = r, x0 = P GMRES_c(R r)) (post-smoothing
+ * only) */
 static void vcycle(void* c, const cplx* r, cplx* z) {
   mg_ctx* m = (mg_ctx*)c;
   coarse_ctx cc = {&m->g, m->ntv, m->Dc};
@@ -984,7 +1004,9 @@ double ora_relres(const int* dims, const cplx* U, const cplx* A, const cplx* b, 
 /* ------------------------------------------------------------------ */
 /* learned test-vector generator: gauge-covariant convolution network   */
 /* ------------------------------------------------------------------ */
-/* Channels are colour triplets: a field of C channels is h[s][c][a],
+/* The paper has no learned part: this network is the project's learned
+ * test-vector generator, replacing initial-phase smoother sweeps (Sec. 2).
+ * Channels are colour triplets: a field of C channels is h[s][c][a],
  * a = colour. One layer maps C_in -> C_out channels:
  *   z(x)[c] = sum_{k=0..8} sum_c' W[k][c][c'] T_k(x) h(x + k)[c']
  * with k = 0 the site itself (T_0 = 1), k = 1+mu the +mu neighbour
