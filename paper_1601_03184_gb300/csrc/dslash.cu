@@ -1,5 +1,7 @@
 // Multi-right-hand-side Wilson-clover stencil (full, block-restricted and
-// residual forms) and the SAP smoother built on it.
+// residual forms) and the SAP smoother built on it: the operator of Sec. 1-2
+// of the paper, with the right-hand sides as the innermost index like the
+// SIMD vectors of Sec. 5, and the smoother of Sec. 2.
 #include <cstdlib>
 
 #include "stencil.cuh"

@@ -1,4 +1,5 @@
-// Aggregate-wise orthonormalisation of the test vectors: P = R^dag.
+// Aggregate-wise orthonormalisation of the test vectors: P = R^dag (Sec. 2
+// of the paper; split by chirality as in Algorithm 3, Sec. 5).
 //
 // For every aggregate A and chirality h the ntv test vectors restricted to
 // (sites of A) x (the 6 spin-colour components of chirality h) form an

@@ -1,4 +1,5 @@
-// SAP colour phase with the Schwarz domain held on chip (FP32 work fields).
+// SAP colour phase (the smoother of Sec. 2 of the paper) with the Schwarz
+// domain held on chip (FP32 work fields).
 //
 // One CTA per domain of the colour being updated. The domain's links and
 // clover blocks are staged once in shared memory (structure-of-arrays over the
