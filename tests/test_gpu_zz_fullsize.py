@@ -46,11 +46,12 @@ def rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
-def gather(field, sites, dims=DIMS, agg=AGG, nrhs=N):
+def gather(field, sites, dims=None, agg=None, nrhs=None):
     """[nrhs, len(sites), 12] complex128 values of a device FP32 field at
-    canonical sites"""
+    canonical sites (default: the benchmark lattice)"""
     import torch
 
+    dims, agg, nrhs = dims or DIMS, agg or AGG, nrhs or N
     vol = int(np.prod(dims))
     sd = device_site(dims, agg, np.asarray(sites))
     assert sd.min() >= 0 and sd.max() < vol
@@ -103,8 +104,10 @@ def test_stencil_full_size_sampled_sites(full):
     lat.apply_D(psi, y, N, MRHS_F32)
     torch.cuda.synchronize()
     L = DIMS
-    sites = [0, V - 1, lex([0, 0, 0, L[3] - 1], L), lex([L[0] - 1, 0, L[2] - 1, 0], L), lex([17, 33, 5, 0], L),
-             lex([3, 47, 0, 95], L), lex([24, 24, 24, 48], L)]
+    # corners, both sides of the t boundary, the middle, random sites
+    sites = [0, V - 1, lex([0, 0, 0, L[3] - 1], L), lex([L[0] - 1, 0, L[2] - 1, 0], L),
+             lex([L[0] // 3, L[1] - 1, L[2] // 9, 0], L), lex([3, L[1] - 1, 0, L[3] - 1], L),
+             lex([L[0] // 2, L[1] // 2, L[2] // 2, L[3] // 2], L)]
     sites += [int(s) for s in np.random.default_rng(73).integers(0, V, 25)]
     got = gather(y, sites)
     for i, s in enumerate(sites):
@@ -120,7 +123,12 @@ def test_sap_sweep_full_size_sampled_domains(full):
     x = torch.zeros_like(psi)
     lat.sap(psi, x, N, MRHS_F32, 1, N_MR)
     torch.cuda.synchronize()
-    for block in [(0, 0, 0, 0), (1, 0, 0, 23), (11, 11, 11, 23), (5, 6, 7, 10), (0, 11, 0, 11)]:
+    nb = [d // a for d, a in zip(DIMS, AGG)]
+    # the first and last domains, domains at the t boundary and inside; the
+    # first coordinate is moved by one where needed to make the domain colour 0
+    for b in [(0, 0, 0, 0), (0, 0, 0, nb[3] - 1), (nb[0] - 1, nb[1] - 1, nb[2] - 1, nb[3] - 1),
+              (nb[0] // 2, nb[1] // 2, nb[2] // 2, nb[3] // 2), (0, nb[1] - 1, 0, nb[3] // 2)]:
+        block = ((b[0] + sum(b) % 2) % nb[0],) + tuple(b[1:])
         assert sum(block) % 2 == 0  # colour 0: updated first
         ref, g = sap_sweep_on_domain(DIMS, AGG, U, M0, CSW, lambda s: gather(psi, s), block, N_MR)
         assert rel(gather(x, g), ref) < 1e-5, block
