@@ -117,14 +117,40 @@ def _ptr(a):
     if a is None:
         return None
     if isinstance(a, np.ndarray):
-        assert a.flags["C_CONTIGUOUS"], "arrays must be C-contiguous"
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
         return a.ctypes.data
     if hasattr(a, "data_ptr"):
-        assert a.is_contiguous(), "tensors must be contiguous"
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
         return a.data_ptr()
     if isinstance(a, int):
         return a
     raise TypeError("cannot pass %r as a pointer" % type(a))
+
+
+def _nbytes(a):
+    """size of a numpy array or torch tensor in bytes (None for a raw pointer)"""
+    if isinstance(a, np.ndarray):
+        return a.nbytes
+    if hasattr(a, "data_ptr"):
+        return a.numel() * a.element_size()
+    return None
+
+
+def _fits(ctx, buf, nrhs, dtype, coarse, what):
+    """Refuse a numpy array or torch tensor smaller than the field of nrhs
+    right-hand sides it is passed as. The library addresses a field by nrhs
+    and dtype alone, so a short buffer would be read or written past its end
+    on the device. The size needed is the library's own (mrhs_field_bytes);
+    raw integer pointers are passed through unchecked."""
+    have = _nbytes(buf)
+    if have is None:
+        return
+    need = mrhs_field_bytes(ctx, nrhs, dtype, coarse)
+    if have < need:
+        raise MrhsError(MRHS_ERR_ARG, "%s: buffer of %d bytes, the %s field of %d right-hand sides needs %d"
+                        % (what, have, "coarse" if coarse else "fine", int(nrhs), need))
 
 
 def _check(ctx, st):
@@ -190,30 +216,40 @@ def mrhs_get_clover(ctx, out):
 
 
 def mrhs_pack(ctx, host, host_dtype, dev, dev_dtype, nrhs):
+    _fits(ctx, dev, nrhs, dev_dtype, 0, "mrhs_pack")
     return _check(ctx, lib().mrhs_pack(ctx, _ptr(host), host_dtype, _ptr(dev), dev_dtype, int(nrhs)))
 
 
 def mrhs_unpack(ctx, dev, dev_dtype, host, host_dtype, nrhs):
+    _fits(ctx, dev, nrhs, dev_dtype, 0, "mrhs_unpack")
     return _check(ctx, lib().mrhs_unpack(ctx, _ptr(dev), dev_dtype, _ptr(host), host_dtype, int(nrhs)))
 
 
 def mrhs_pack_coarse(ctx, host, host_dtype, dev, dev_dtype, nrhs):
+    _fits(ctx, dev, nrhs, dev_dtype, 1, "mrhs_pack_coarse")
     return _check(ctx, lib().mrhs_pack_coarse(ctx, _ptr(host), host_dtype, _ptr(dev), dev_dtype, int(nrhs)))
 
 
 def mrhs_unpack_coarse(ctx, dev, dev_dtype, host, host_dtype, nrhs):
+    _fits(ctx, dev, nrhs, dev_dtype, 1, "mrhs_unpack_coarse")
     return _check(ctx, lib().mrhs_unpack_coarse(ctx, _ptr(dev), dev_dtype, _ptr(host), host_dtype, int(nrhs)))
 
 
 def mrhs_apply_D(ctx, x, y, nrhs, dtype):
+    _fits(ctx, x, nrhs, dtype, 0, "mrhs_apply_D x")
+    _fits(ctx, y, nrhs, dtype, 0, "mrhs_apply_D y")
     return _check(ctx, lib().mrhs_apply_D(ctx, _ptr(x), _ptr(y), int(nrhs), int(dtype)))
 
 
 def mrhs_apply_D_block(ctx, x, y, nrhs, dtype):
+    _fits(ctx, x, nrhs, dtype, 0, "mrhs_apply_D_block x")
+    _fits(ctx, y, nrhs, dtype, 0, "mrhs_apply_D_block y")
     return _check(ctx, lib().mrhs_apply_D_block(ctx, _ptr(x), _ptr(y), int(nrhs), int(dtype)))
 
 
 def mrhs_sap(ctx, b, x, nrhs, dtype, n_sweeps, n_mr):
+    _fits(ctx, b, nrhs, dtype, 0, "mrhs_sap b")
+    _fits(ctx, x, nrhs, dtype, 0, "mrhs_sap x")
     return _check(ctx, lib().mrhs_sap(ctx, _ptr(b), _ptr(x), int(nrhs), int(dtype), int(n_sweeps), int(n_mr)))
 
 
@@ -234,18 +270,26 @@ def mrhs_set_dc_engine(ctx, engine):
 
 
 def mrhs_restrict(ctx, v, vc, nrhs, dtype):
+    _fits(ctx, v, nrhs, dtype, 0, "mrhs_restrict v")
+    _fits(ctx, vc, nrhs, dtype, 1, "mrhs_restrict vc")
     return _check(ctx, lib().mrhs_restrict(ctx, _ptr(v), _ptr(vc), int(nrhs), int(dtype)))
 
 
 def mrhs_prolong(ctx, uc, u, nrhs, dtype):
+    _fits(ctx, uc, nrhs, dtype, 1, "mrhs_prolong uc")
+    _fits(ctx, u, nrhs, dtype, 0, "mrhs_prolong u")
     return _check(ctx, lib().mrhs_prolong(ctx, _ptr(uc), _ptr(u), int(nrhs), int(dtype)))
 
 
 def mrhs_apply_Dc(ctx, xc, yc, nrhs, dtype):
+    _fits(ctx, xc, nrhs, dtype, 1, "mrhs_apply_Dc xc")
+    _fits(ctx, yc, nrhs, dtype, 1, "mrhs_apply_Dc yc")
     return _check(ctx, lib().mrhs_apply_Dc(ctx, _ptr(xc), _ptr(yc), int(nrhs), int(dtype)))
 
 
 def mrhs_coarse_solve(ctx, bc, xc, nrhs, dtype, tol, restart, maxit):
+    _fits(ctx, bc, nrhs, dtype, 1, "mrhs_coarse_solve bc")
+    _fits(ctx, xc, nrhs, dtype, 1, "mrhs_coarse_solve xc")
     its = np.zeros(int(nrhs), np.int32)
     _check(ctx, lib().mrhs_coarse_solve(ctx, _ptr(bc), _ptr(xc), int(nrhs), int(dtype), float(tol), int(restart),
                                         int(maxit), _ptr(its)))
@@ -254,6 +298,8 @@ def mrhs_coarse_solve(ctx, bc, xc, nrhs, dtype, tol, restart, maxit):
 
 def mrhs_coarse_solve_noalloc(ctx, bc, xc, nrhs, dtype, tol, restart, maxit):
     """mrhs_coarse_solve without allocation (fixed 64 MiB device workspace)."""
+    _fits(ctx, bc, nrhs, dtype, 1, "mrhs_coarse_solve_noalloc bc")
+    _fits(ctx, xc, nrhs, dtype, 1, "mrhs_coarse_solve_noalloc xc")
     its = np.zeros(int(nrhs), np.int32)
     _check(ctx, lib().mrhs_coarse_solve_noalloc(ctx, _ptr(bc), _ptr(xc), int(nrhs), int(dtype), float(tol),
                                                 int(restart), int(maxit), _ptr(its)))

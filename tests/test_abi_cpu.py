@@ -115,3 +115,60 @@ def test_header_is_plain_c_and_links(lib, tmp_path):
     out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert out.returncode == 0, (out.returncode, out.stderr)
     assert out.stdout.strip() == "%d entry points" % len(names)
+
+
+def test_short_buffers_are_refused_before_the_library_is_called(monkeypatch):
+    """The binding compares every numpy array or torch tensor passed as a
+    field with the library's size for that field and refuses a short one, so
+    a kernel never reads or writes past the end of a caller's buffer."""
+    import numpy as np
+    import torch
+
+    calls = []
+
+    class FakeLib:
+        def __getattr__(self, name):
+            return lambda *a: calls.append(name) or 0
+
+    monkeypatch.setattr(pkg, "lib", lambda: FakeLib())
+    monkeypatch.setattr(pkg, "mrhs_field_bytes", lambda ctx, nrhs, dtype, coarse=0: (2048 if coarse else 1024) * nrhs)
+    F64 = pkg.MRHS_F64
+    fine = lambda n: np.zeros(128 * n, np.float64)       # exactly 1024 bytes per right-hand side
+    coarse = lambda n: torch.zeros(512 * n, dtype=torch.float32)  # exactly 2048 bytes per right-hand side
+    cases = [
+        ("mrhs_apply_D", lambda f, c: pkg.mrhs_apply_D(1, f(2), f(2), 2, F64), "ff"),
+        ("mrhs_apply_D_block", lambda f, c: pkg.mrhs_apply_D_block(1, f(2), f(2), 2, F64), "ff"),
+        ("mrhs_sap", lambda f, c: pkg.mrhs_sap(1, f(2), f(2), 2, F64, 1, 1), "ff"),
+        ("mrhs_restrict", lambda f, c: pkg.mrhs_restrict(1, f(2), c(2), 2, F64), "fc"),
+        ("mrhs_prolong", lambda f, c: pkg.mrhs_prolong(1, c(2), f(2), 2, F64), "cf"),
+        ("mrhs_apply_Dc", lambda f, c: pkg.mrhs_apply_Dc(1, c(2), c(2), 2, F64), "cc"),
+        ("mrhs_coarse_solve", lambda f, c: pkg.mrhs_coarse_solve(1, c(2), c(2), 2, F64, 0.1, 4, 4), "cc"),
+        ("mrhs_coarse_solve_noalloc", lambda f, c: pkg.mrhs_coarse_solve_noalloc(1, c(2), c(2), 2, F64, 0.1, 4, 4),
+         "cc"),
+        ("mrhs_pack", lambda f, c: pkg.mrhs_pack(1, np.zeros(1), F64, f(2), F64, 2), "f"),
+        ("mrhs_unpack", lambda f, c: pkg.mrhs_unpack(1, f(2), F64, np.zeros(1), F64, 2), "f"),
+        ("mrhs_pack_coarse", lambda f, c: pkg.mrhs_pack_coarse(1, np.zeros(1), F64, c(2), F64, 2), "c"),
+        ("mrhs_unpack_coarse", lambda f, c: pkg.mrhs_unpack_coarse(1, c(2), F64, np.zeros(1), F64, 2), "c"),
+    ]
+    short_f = lambda n: np.zeros(128 * n - 1, np.float64)
+    short_c = lambda n: torch.zeros(512 * n - 1, dtype=torch.float32)
+    for name, call, _ in cases:
+        calls.clear()
+        call(fine, coarse)
+        assert calls[-1] == name
+        for f, c in ((short_f, coarse), (fine, short_c)):
+            calls.clear()
+            try:
+                call(f, c)
+            except pkg.MrhsError as e:
+                assert e.status == pkg.MRHS_ERR_ARG and "needs" in str(e)
+                assert calls == []
+            else:
+                # this call has no argument of the shortened kind
+                assert calls == [name]
+    # raw integer pointers are passed through; strided arrays are refused
+    calls.clear()
+    pkg.mrhs_apply_D(1, 4096, 8192, 2, F64)
+    assert calls == ["mrhs_apply_D"]
+    with pytest.raises(ValueError):
+        pkg.mrhs_apply_D(1, np.zeros(512)[::2], fine(2), 2, F64)
