@@ -56,7 +56,10 @@ class Lattice:
     def to_device(self, host, dtype, coarse=False):
         """host [nrhs, V, 12] (or [nrhs, nagg, 2ntv] for coarse) complex -> device field"""
         hd = MRHS_F64 if host.dtype == np.complex128 else MRHS_F32
-        host = np.ascontiguousarray(host)
+        host = np.ascontiguousarray(host, dtype=np.complex128 if hd == MRHS_F64 else np.complex64)
+        want = (self.nagg, 2 * self.ntv) if coarse else (self.V, 12)
+        if host.ndim != 3 or host.shape[1:] != want:
+            raise ValueError("host field must be [nrhs, %d, %d], got %s" % (want + (host.shape,)))
         nrhs = host.shape[0]
         d = self.field(nrhs, dtype, coarse, zero=False)
         (mrhs_pack_coarse if coarse else mrhs_pack)(self.ctx, host, hd, d, dtype, nrhs)
@@ -70,7 +73,10 @@ class Lattice:
 
     # ------------------------------------------------------------- setup --
     def set_gauge(self, U):
-        mrhs_set_gauge(self.ctx, np.ascontiguousarray(U, dtype=np.complex128))
+        U = np.ascontiguousarray(U, dtype=np.complex128)
+        if U.size != self.V * 36:
+            raise ValueError("gauge field must hold [V, 4, 3, 3] = %d complex numbers, got %d" % (self.V * 36, U.size))
+        mrhs_set_gauge(self.ctx, U)
 
     def build_clover(self, m0, csw):
         mrhs_build_clover(self.ctx, m0, csw)

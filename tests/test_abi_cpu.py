@@ -172,3 +172,22 @@ def test_short_buffers_are_refused_before_the_library_is_called(monkeypatch):
     assert calls == ["mrhs_apply_D"]
     with pytest.raises(ValueError):
         pkg.mrhs_apply_D(1, np.zeros(512)[::2], fine(2), 2, F64)
+
+
+def test_lattice_refuses_misshapen_host_arrays():
+    """Host fields and the gauge field are read by the library with the
+    lattice's own sizes, so the wrapper checks their shapes first."""
+    import numpy as np
+
+    from paper_1601_03184_gb300 import Lattice
+
+    lat = object.__new__(Lattice)  # no device context: the checks come first
+    lat.V, lat.nagg, lat.ntv, lat.ctx = 16, 1, 2, None
+    with pytest.raises(ValueError):
+        lat.to_device(np.zeros((2, 15, 12), np.complex128), pkg.MRHS_F64)
+    with pytest.raises(ValueError):
+        lat.to_device(np.zeros((16, 12), np.complex128), pkg.MRHS_F64)
+    with pytest.raises(ValueError):
+        lat.to_device(np.zeros((2, 1, 3), np.complex64), pkg.MRHS_F32, coarse=True)
+    with pytest.raises(ValueError):
+        lat.set_gauge(np.zeros((16, 4, 3, 2), np.complex128))
