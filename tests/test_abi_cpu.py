@@ -191,3 +191,21 @@ def test_lattice_refuses_misshapen_host_arrays():
         lat.to_device(np.zeros((2, 1, 3), np.complex64), pkg.MRHS_F32, coarse=True)
     with pytest.raises(ValueError):
         lat.set_gauge(np.zeros((16, 4, 3, 2), np.complex128))
+
+
+def test_create_refuses_empty_and_oversized_problems(lib):
+    """Limits checked before any device work: ntv in 1..min(64, 6|aggregate|),
+    volume below 2^30 sites (32-bit site indices with two flag bits), no
+    empty lattice."""
+    pkg.lib()
+    out = ctypes.c_void_p()
+    i4 = lambda v: (ctypes.c_int * 4)(*v)
+    for dims, agg, ntv in [((4, 4, 4, 4), (2, 2, 2, 2), 0),          # no test vectors
+                           ((8, 8, 8, 8), (4, 4, 4, 4), 65),         # above 64 test vectors
+                           ((2, 2, 2, 2), (1, 1, 1, 1), 7),          # above 6 |aggregate|
+                           ((1024, 1024, 1024, 2), (2, 2, 2, 1), 8),  # 2^31 sites
+                           ((0, 4, 4, 4), (2, 2, 2, 2), 4),          # empty lattice
+                           ((4, 4, 4, 4), (0, 2, 2, 2), 4)]:         # empty aggregate
+        st = pkg.lib().mrhs_create(i4(dims), i4(agg), ntv, 0, None, ctypes.byref(out))
+        assert st == pkg.MRHS_ERR_SHAPE, (dims, agg, ntv, st)
+        assert out.value is None
