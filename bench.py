@@ -56,7 +56,7 @@ SCHEDULE = dict(init_sweeps=5, init_mr=4, n_refine=3, smooth_sweeps=4, smooth_mr
 M0_FALLBACK = -0.45
 # bounded CPU sample of the same setup (oracle): 8^3 x 32 lattice (two 4^4
 # domains per spatial direction, eight in time), same aggregates and schedule;
-# about 20 s on 16 host cores of the GPU machine (53 s on 8 x86 cores)
+# about 20 s on 16 Grace cores (53 s on 8 x86 cores)
 CPU_SAMPLE_DIMS = (8, 8, 8, 32)
 
 
