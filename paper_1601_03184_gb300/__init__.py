@@ -153,6 +153,35 @@ def _fits(ctx, buf, nrhs, dtype, coarse, what):
                         % (what, have, "coarse" if coarse else "fine", int(nrhs), need))
 
 
+def _is_torch(a):
+    return hasattr(a, "data_ptr") and hasattr(a, "is_cuda")
+
+
+def _dev(ctx, buf, nrhs, dtype, coarse, what):
+    """A device-field argument: a torch CUDA tensor on the context's GPU (or a
+    raw integer device pointer, which the library checks itself). A numpy
+    array, a CPU tensor or a tensor on another GPU is refused here, before
+    any call, and then held against the field size like _fits."""
+    if buf is None or isinstance(buf, int):
+        return
+    if not _is_torch(buf) or not buf.is_cuda:
+        raise MrhsError(MRHS_ERR_ARG, "%s: a device field must be a CUDA tensor, got %s"
+                        % (what, "a CPU tensor" if _is_torch(buf) else type(buf).__name__))
+    dev = mrhs_info(ctx)[7]
+    if buf.device.index is not None and buf.device.index != dev:
+        raise MrhsError(MRHS_ERR_ARG, "%s: tensor on cuda:%d, the context lives on cuda:%d"
+                        % (what, buf.device.index, dev))
+    _fits(ctx, buf, nrhs, dtype, coarse, what)
+
+
+def _host(buf, what):
+    """A host-array argument: numpy or a CPU torch tensor (pinned or not)."""
+    if buf is None or isinstance(buf, (int, np.ndarray)):
+        return
+    if _is_torch(buf) and buf.is_cuda:
+        raise MrhsError(MRHS_ERR_ARG, "%s: a host array is required, got a CUDA tensor" % what)
+
+
 def _check(ctx, st):
     if st != MRHS_OK:
         msg = lib().mrhs_last_error(ctx)
@@ -216,44 +245,49 @@ def mrhs_get_clover(ctx, out):
 
 
 def mrhs_pack(ctx, host, host_dtype, dev, dev_dtype, nrhs):
-    _fits(ctx, dev, nrhs, dev_dtype, 0, "mrhs_pack")
+    _host(host, "mrhs_pack host")
+    _dev(ctx, dev, nrhs, dev_dtype, 0, "mrhs_pack")
     return _check(ctx, lib().mrhs_pack(ctx, _ptr(host), host_dtype, _ptr(dev), dev_dtype, int(nrhs)))
 
 
 def mrhs_unpack(ctx, dev, dev_dtype, host, host_dtype, nrhs):
-    _fits(ctx, dev, nrhs, dev_dtype, 0, "mrhs_unpack")
+    _host(host, "mrhs_unpack host")
+    _dev(ctx, dev, nrhs, dev_dtype, 0, "mrhs_unpack")
     return _check(ctx, lib().mrhs_unpack(ctx, _ptr(dev), dev_dtype, _ptr(host), host_dtype, int(nrhs)))
 
 
 def mrhs_pack_coarse(ctx, host, host_dtype, dev, dev_dtype, nrhs):
-    _fits(ctx, dev, nrhs, dev_dtype, 1, "mrhs_pack_coarse")
+    _host(host, "mrhs_pack_coarse host")
+    _dev(ctx, dev, nrhs, dev_dtype, 1, "mrhs_pack_coarse")
     return _check(ctx, lib().mrhs_pack_coarse(ctx, _ptr(host), host_dtype, _ptr(dev), dev_dtype, int(nrhs)))
 
 
 def mrhs_unpack_coarse(ctx, dev, dev_dtype, host, host_dtype, nrhs):
-    _fits(ctx, dev, nrhs, dev_dtype, 1, "mrhs_unpack_coarse")
+    _host(host, "mrhs_unpack_coarse host")
+    _dev(ctx, dev, nrhs, dev_dtype, 1, "mrhs_unpack_coarse")
     return _check(ctx, lib().mrhs_unpack_coarse(ctx, _ptr(dev), dev_dtype, _ptr(host), host_dtype, int(nrhs)))
 
 
 def mrhs_apply_D(ctx, x, y, nrhs, dtype):
-    _fits(ctx, x, nrhs, dtype, 0, "mrhs_apply_D x")
-    _fits(ctx, y, nrhs, dtype, 0, "mrhs_apply_D y")
+    _dev(ctx, x, nrhs, dtype, 0, "mrhs_apply_D x")
+    _dev(ctx, y, nrhs, dtype, 0, "mrhs_apply_D y")
     return _check(ctx, lib().mrhs_apply_D(ctx, _ptr(x), _ptr(y), int(nrhs), int(dtype)))
 
 
 def mrhs_apply_D_block(ctx, x, y, nrhs, dtype):
-    _fits(ctx, x, nrhs, dtype, 0, "mrhs_apply_D_block x")
-    _fits(ctx, y, nrhs, dtype, 0, "mrhs_apply_D_block y")
+    _dev(ctx, x, nrhs, dtype, 0, "mrhs_apply_D_block x")
+    _dev(ctx, y, nrhs, dtype, 0, "mrhs_apply_D_block y")
     return _check(ctx, lib().mrhs_apply_D_block(ctx, _ptr(x), _ptr(y), int(nrhs), int(dtype)))
 
 
 def mrhs_sap(ctx, b, x, nrhs, dtype, n_sweeps, n_mr):
-    _fits(ctx, b, nrhs, dtype, 0, "mrhs_sap b")
-    _fits(ctx, x, nrhs, dtype, 0, "mrhs_sap x")
+    _dev(ctx, b, nrhs, dtype, 0, "mrhs_sap b")
+    _dev(ctx, x, nrhs, dtype, 0, "mrhs_sap x")
     return _check(ctx, lib().mrhs_sap(ctx, _ptr(b), _ptr(x), int(nrhs), int(dtype), int(n_sweeps), int(n_mr)))
 
 
 def mrhs_set_tv(ctx, tv, dtype):
+    _dev(ctx, tv, mrhs_info(ctx)[3], dtype, 0, "mrhs_set_tv tv")
     return _check(ctx, lib().mrhs_set_tv(ctx, _ptr(tv), int(dtype)))
 
 
@@ -270,26 +304,26 @@ def mrhs_set_dc_engine(ctx, engine):
 
 
 def mrhs_restrict(ctx, v, vc, nrhs, dtype):
-    _fits(ctx, v, nrhs, dtype, 0, "mrhs_restrict v")
-    _fits(ctx, vc, nrhs, dtype, 1, "mrhs_restrict vc")
+    _dev(ctx, v, nrhs, dtype, 0, "mrhs_restrict v")
+    _dev(ctx, vc, nrhs, dtype, 1, "mrhs_restrict vc")
     return _check(ctx, lib().mrhs_restrict(ctx, _ptr(v), _ptr(vc), int(nrhs), int(dtype)))
 
 
 def mrhs_prolong(ctx, uc, u, nrhs, dtype):
-    _fits(ctx, uc, nrhs, dtype, 1, "mrhs_prolong uc")
-    _fits(ctx, u, nrhs, dtype, 0, "mrhs_prolong u")
+    _dev(ctx, uc, nrhs, dtype, 1, "mrhs_prolong uc")
+    _dev(ctx, u, nrhs, dtype, 0, "mrhs_prolong u")
     return _check(ctx, lib().mrhs_prolong(ctx, _ptr(uc), _ptr(u), int(nrhs), int(dtype)))
 
 
 def mrhs_apply_Dc(ctx, xc, yc, nrhs, dtype):
-    _fits(ctx, xc, nrhs, dtype, 1, "mrhs_apply_Dc xc")
-    _fits(ctx, yc, nrhs, dtype, 1, "mrhs_apply_Dc yc")
+    _dev(ctx, xc, nrhs, dtype, 1, "mrhs_apply_Dc xc")
+    _dev(ctx, yc, nrhs, dtype, 1, "mrhs_apply_Dc yc")
     return _check(ctx, lib().mrhs_apply_Dc(ctx, _ptr(xc), _ptr(yc), int(nrhs), int(dtype)))
 
 
 def mrhs_coarse_solve(ctx, bc, xc, nrhs, dtype, tol, restart, maxit):
-    _fits(ctx, bc, nrhs, dtype, 1, "mrhs_coarse_solve bc")
-    _fits(ctx, xc, nrhs, dtype, 1, "mrhs_coarse_solve xc")
+    _dev(ctx, bc, nrhs, dtype, 1, "mrhs_coarse_solve bc")
+    _dev(ctx, xc, nrhs, dtype, 1, "mrhs_coarse_solve xc")
     its = np.zeros(int(nrhs), np.int32)
     _check(ctx, lib().mrhs_coarse_solve(ctx, _ptr(bc), _ptr(xc), int(nrhs), int(dtype), float(tol), int(restart),
                                         int(maxit), _ptr(its)))
@@ -298,8 +332,8 @@ def mrhs_coarse_solve(ctx, bc, xc, nrhs, dtype, tol, restart, maxit):
 
 def mrhs_coarse_solve_noalloc(ctx, bc, xc, nrhs, dtype, tol, restart, maxit):
     """mrhs_coarse_solve without allocation (fixed 64 MiB device workspace)."""
-    _fits(ctx, bc, nrhs, dtype, 1, "mrhs_coarse_solve_noalloc bc")
-    _fits(ctx, xc, nrhs, dtype, 1, "mrhs_coarse_solve_noalloc xc")
+    _dev(ctx, bc, nrhs, dtype, 1, "mrhs_coarse_solve_noalloc bc")
+    _dev(ctx, xc, nrhs, dtype, 1, "mrhs_coarse_solve_noalloc xc")
     its = np.zeros(int(nrhs), np.int32)
     _check(ctx, lib().mrhs_coarse_solve_noalloc(ctx, _ptr(bc), _ptr(xc), int(nrhs), int(dtype), float(tol),
                                                 int(restart), int(maxit), _ptr(its)))
@@ -307,6 +341,7 @@ def mrhs_coarse_solve_noalloc(ctx, bc, xc, nrhs, dtype, tol, restart, maxit):
 
 
 def mrhs_setup_init(ctx, tv0, dtype, init_mode, n_sweeps, n_mr):
+    _dev(ctx, tv0, mrhs_info(ctx)[3], dtype, 0, "mrhs_setup_init tv0")
     return _check(ctx, lib().mrhs_setup_init(ctx, _ptr(tv0), int(dtype), int(init_mode), int(n_sweeps), int(n_mr)))
 
 
@@ -387,14 +422,20 @@ def mrhs_nn_zero_grads(ctx):
 
 
 def mrhs_nn_forward(ctx, x, y, nrhs):
+    _dev(ctx, x, nrhs, MRHS_F32, 0, "mrhs_nn_forward in")
+    _dev(ctx, y, nrhs, MRHS_F32, 0, "mrhs_nn_forward out")
     return _check(ctx, lib().mrhs_nn_forward(ctx, _ptr(x), _ptr(y), int(nrhs)))
 
 
 def mrhs_nn_backward(ctx, gout, gin, nrhs):
+    _dev(ctx, gout, nrhs, MRHS_F32, 0, "mrhs_nn_backward grad_out")
+    _dev(ctx, gin, nrhs, MRHS_F32, 0, "mrhs_nn_backward grad_in")
     return _check(ctx, lib().mrhs_nn_backward(ctx, _ptr(gout), _ptr(gin), int(nrhs)))
 
 
 def mrhs_nn_loss(ctx, v, gv, nrhs, lam):
+    _dev(ctx, v, nrhs, MRHS_F32, 0, "mrhs_nn_loss v")
+    _dev(ctx, gv, nrhs, MRHS_F32, 0, "mrhs_nn_loss grad_v")
     loss = ctypes.c_double(0)
     per = np.zeros(int(nrhs), np.float64)
     _check(ctx, lib().mrhs_nn_loss(ctx, _ptr(v), _ptr(gv), int(nrhs), float(lam), ctypes.byref(loss), _ptr(per)))
@@ -406,6 +447,7 @@ def mrhs_nn_adam(ctx, lr, beta1, beta2, eps, step):
 
 
 def mrhs_nn_train_step(ctx, v_in, nrhs, lam, lr, step):
+    _dev(ctx, v_in, nrhs, MRHS_F32, 0, "mrhs_nn_train_step v_in")
     loss = ctypes.c_double(0)
     _check(ctx, lib().mrhs_nn_train_step(ctx, _ptr(v_in), int(nrhs), float(lam), float(lr), int(step),
                                          ctypes.byref(loss)))
@@ -413,6 +455,7 @@ def mrhs_nn_train_step(ctx, v_in, nrhs, lam, lr, step):
 
 
 def mrhs_setup_init_learned(ctx, tv0, dtype, n_sweeps, n_mr):
+    _dev(ctx, tv0, mrhs_info(ctx)[3], dtype, 0, "mrhs_setup_init_learned tv0")
     return _check(ctx, lib().mrhs_setup_init_learned(ctx, _ptr(tv0), int(dtype), int(n_sweeps), int(n_mr)))
 
 

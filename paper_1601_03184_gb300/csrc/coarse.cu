@@ -966,6 +966,8 @@ int mrhs_set_dc_engine(mrhs_ctx c, int engine) {
 int mrhs_restrict(mrhs_ctx c, const void* v, void* vc, int nrhs, int dtype) {
   return guarded(c, [&] {
     MRHS_REQUIRE(c && v && vc, MRHS_ERR_ARG, "null argument");
+    require_dev(c, v, "mrhs_restrict v");
+    require_dev(c, vc, "mrhs_restrict vc");
     restrict_(c, v, vc, nrhs, dtype);
   });
 }
@@ -973,6 +975,8 @@ int mrhs_restrict(mrhs_ctx c, const void* v, void* vc, int nrhs, int dtype) {
 int mrhs_prolong(mrhs_ctx c, const void* uc, void* u, int nrhs, int dtype) {
   return guarded(c, [&] {
     MRHS_REQUIRE(c && uc && u, MRHS_ERR_ARG, "null argument");
+    require_dev(c, uc, "mrhs_prolong uc");
+    require_dev(c, u, "mrhs_prolong u");
     prolong(c, uc, u, nrhs, dtype);
   });
 }
@@ -980,6 +984,8 @@ int mrhs_prolong(mrhs_ctx c, const void* uc, void* u, int nrhs, int dtype) {
 int mrhs_apply_Dc(mrhs_ctx c, const void* xc, void* yc, int nrhs, int dtype) {
   return guarded(c, [&] {
     MRHS_REQUIRE(c && xc && yc, MRHS_ERR_ARG, "null argument");
+    require_dev(c, xc, "mrhs_apply_Dc xc");
+    require_dev(c, yc, "mrhs_apply_Dc yc");
     MRHS_REQUIRE(nrhs >= 1, MRHS_ERR_ARG, "nrhs must be >= 1");
     apply_Dc(c, xc, yc, nrhs, dtype);
   });
@@ -989,6 +995,8 @@ int mrhs_coarse_solve(mrhs_ctx c, const void* bc, void* xc, int nrhs, int dtype,
                       int* iters) {
   return guarded(c, [&] {
     MRHS_REQUIRE(c && bc && xc, MRHS_ERR_ARG, "null argument");
+    require_dev(c, bc, "mrhs_coarse_solve bc");
+    require_dev(c, xc, "mrhs_coarse_solve xc");
     coarse_solve(c, bc, xc, nrhs, dtype, tol, restart, maxit, iters);
   });
 }

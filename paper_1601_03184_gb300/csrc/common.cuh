@@ -248,6 +248,12 @@ enum Scratch {
 };
 
 void* scratch(mrhs_ctx c, int which, size_t bytes);
+// refuse (MRHS_ERR_ARG) a caller pointer of the wrong memory type before any
+// launch or copy touches it: require_dev wants device memory of the
+// context's GPU (or managed memory), require_host host memory (pageable,
+// pinned or managed); a null pointer passes (optional arguments)
+void require_dev(mrhs_ctx c, const void* p, const char* what);
+void require_host(mrhs_ctx c, const void* p, const char* what);
 void* dalloc(mrhs_ctx c, size_t bytes);
 double* host_scratch(mrhs_ctx c, size_t bytes);
 

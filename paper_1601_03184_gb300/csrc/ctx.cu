@@ -470,6 +470,36 @@ void convert_scaled(mrhs_ctx c, const void* x, int dx, void* y, int dy, size_t n
 }
 }  // namespace mrhs
 
+namespace mrhs {
+void require_dev(mrhs_ctx c, const void* p, const char* what) {
+  if (!p) return;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // the failed query is recorded as the last error: clear it
+    throw Error(MRHS_ERR_ARG, std::string(what) + ": not a CUDA pointer (" + cudaGetErrorString(e) + ")");
+  }
+  if (a.type == cudaMemoryTypeManaged) return;
+  MRHS_REQUIRE(a.type == cudaMemoryTypeDevice, MRHS_ERR_ARG,
+               std::string(what) + ": host memory passed where a device field is required");
+  MRHS_REQUIRE(a.device == c->device, MRHS_ERR_ARG,
+               std::string(what) + ": device memory of GPU " + std::to_string(a.device) +
+                   ", the context lives on GPU " + std::to_string(c->device));
+}
+void require_host(mrhs_ctx c, const void* p, const char* what) {
+  (void)c;
+  if (!p) return;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return;  // unknown to CUDA: plain pageable host memory
+  }
+  MRHS_REQUIRE(a.type != cudaMemoryTypeDevice, MRHS_ERR_ARG,
+               std::string(what) + ": device memory passed where a host array is required");
+}
+}  // namespace mrhs
+
 // ------------------------------------------------------------------ ABI ----
 extern "C" {
 
@@ -593,7 +623,7 @@ int mrhs_info(mrhs_ctx c, long long out[8]) {
     out[4] = c->prec;
     out[5] = (long long)c->held_bytes;
     out[6] = c->num_sms;
-    out[7] = 0;
+    out[7] = c->device;
   });
 }
 
@@ -606,6 +636,9 @@ size_t mrhs_field_bytes(mrhs_ctx c, int nrhs, int dtype, int coarse) {
 int mrhs_get_tables(mrhs_ctx c, int* nbr, int* aggof, int* aggnbr) {
   return guarded(c, [&] {
     MRHS_REQUIRE(c, MRHS_ERR_ARG, "null context");
+    require_host(c, nbr, "mrhs_get_tables nbr");
+    require_host(c, aggof, "mrhs_get_tables aggof");
+    require_host(c, aggnbr, "mrhs_get_tables aggnbr");
     const Geometry& g = c->g;
     int* d = (int*)scratch(c, SC_STAGE, sizeof(int) * 10 * (size_t)g.V);
     k_tables_canon<<<grid_for(g.V, 256), 256, 0, c->stream>>>(geom_args(g), c->nbr, c->perm, c->iperm, d,
@@ -623,6 +656,7 @@ int mrhs_get_tables(mrhs_ctx c, int* nbr, int* aggof, int* aggnbr) {
 int mrhs_set_gauge(mrhs_ctx c, const double* U) {
   return guarded(c, [&] {
     MRHS_REQUIRE(c && U, MRHS_ERR_ARG, "null argument");
+    require_host(c, U, "mrhs_set_gauge U");
     size_t n = (size_t)c->g.V * 72;
     if (!c->U64) {
       c->U64 = (double*)dalloc(c, n * sizeof(double));
@@ -666,6 +700,7 @@ int mrhs_build_clover(mrhs_ctx c, double m0, double csw) {
 int mrhs_get_clover(mrhs_ctx c, double* out) {
   return guarded(c, [&] {
     MRHS_REQUIRE(c && out, MRHS_ERR_ARG, "null argument");
+    require_host(c, out, "mrhs_get_clover out");
     MRHS_REQUIRE(c->have_clover, MRHS_ERR_STATE, "no clover term yet");
     size_t n = (size_t)c->g.V * 144;
     double* st = (double*)scratch(c, SC_STAGE, n * sizeof(double));
@@ -679,6 +714,8 @@ int mrhs_get_clover(mrhs_ctx c, double* out) {
 int mrhs_pack(mrhs_ctx c, const void* host, int hd, void* dev, int dd, int nrhs) {
   return guarded(c, [&] {
     MRHS_REQUIRE(c && host && dev, MRHS_ERR_ARG, "null argument");
+    require_host(c, host, "mrhs_pack host");
+    require_dev(c, dev, "mrhs_pack dev");
     transfer_fine(c, host, nullptr, hd, nullptr, dev, dd, nrhs);
   });
 }
@@ -686,6 +723,8 @@ int mrhs_pack(mrhs_ctx c, const void* host, int hd, void* dev, int dd, int nrhs)
 int mrhs_unpack(mrhs_ctx c, const void* dev, int dd, void* host, int hd, int nrhs) {
   return guarded(c, [&] {
     MRHS_REQUIRE(c && host && dev, MRHS_ERR_ARG, "null argument");
+    require_host(c, host, "mrhs_unpack host");
+    require_dev(c, dev, "mrhs_unpack dev");
     transfer_fine(c, nullptr, host, hd, dev, nullptr, dd, nrhs);
   });
 }
@@ -693,6 +732,8 @@ int mrhs_unpack(mrhs_ctx c, const void* dev, int dd, void* host, int hd, int nrh
 int mrhs_pack_coarse(mrhs_ctx c, const void* host, int hd, void* dev, int dd, int nrhs) {
   return guarded(c, [&] {
     MRHS_REQUIRE(c && host && dev, MRHS_ERR_ARG, "null argument");
+    require_host(c, host, "mrhs_pack_coarse host");
+    require_dev(c, dev, "mrhs_pack_coarse dev");
     transfer_coarse(c, host, nullptr, hd, nullptr, dev, dd, nrhs);
   });
 }
@@ -700,6 +741,8 @@ int mrhs_pack_coarse(mrhs_ctx c, const void* host, int hd, void* dev, int dd, in
 int mrhs_unpack_coarse(mrhs_ctx c, const void* dev, int dd, void* host, int hd, int nrhs) {
   return guarded(c, [&] {
     MRHS_REQUIRE(c && host && dev, MRHS_ERR_ARG, "null argument");
+    require_host(c, host, "mrhs_unpack_coarse host");
+    require_dev(c, dev, "mrhs_unpack_coarse dev");
     transfer_coarse(c, nullptr, host, hd, dev, nullptr, dd, nrhs);
   });
 }
@@ -707,6 +750,7 @@ int mrhs_unpack_coarse(mrhs_ctx c, const void* dev, int dd, void* host, int hd, 
 int mrhs_set_tv(mrhs_ctx c, const void* tv, int dtype) {
   return guarded(c, [&] {
     MRHS_REQUIRE(c && tv, MRHS_ERR_ARG, "null argument");
+    require_dev(c, tv, "mrhs_set_tv tv");
     size_t n = fine_elems(c, c->ntv);
     if (!c->tv) c->tv = dalloc(c, n * dtype_size(c->tv_dtype));
     convert(c, tv, dtype, c->tv, c->tv_dtype, n);
@@ -719,6 +763,7 @@ int mrhs_set_tv(mrhs_ctx c, const void* tv, int dtype) {
 int mrhs_get_tv(mrhs_ctx c, void* host, int hd) {
   return guarded(c, [&] {
     MRHS_REQUIRE(c && host, MRHS_ERR_ARG, "null argument");
+    require_host(c, host, "mrhs_get_tv host");
     MRHS_REQUIRE(c->have_tv, MRHS_ERR_STATE, "no test vectors yet");
     if (c->tv_scale != 1.0) {
       const size_t n = fine_elems(c, c->ntv);
@@ -734,6 +779,7 @@ int mrhs_get_tv(mrhs_ctx c, void* host, int hd) {
 int mrhs_get_P(mrhs_ctx c, void* host, int hd) {
   return guarded(c, [&] {
     MRHS_REQUIRE(c && host, MRHS_ERR_ARG, "null argument");
+    require_host(c, host, "mrhs_get_P host");
     MRHS_REQUIRE(c->have_P, MRHS_ERR_STATE, "no P yet");
     transfer_fine(c, nullptr, host, hd, c->P, nullptr, c->tv_dtype, c->ntv);
   });
@@ -742,6 +788,7 @@ int mrhs_get_P(mrhs_ctx c, void* host, int hd) {
 int mrhs_get_Dc(mrhs_ctx c, void* host, int hd) {
   return guarded(c, [&] {
     MRHS_REQUIRE(c && host, MRHS_ERR_ARG, "null argument");
+    require_host(c, host, "mrhs_get_Dc host");
     MRHS_REQUIRE(c->have_Dc, MRHS_ERR_STATE, "no D_c yet");
     check_host_dtype(hd);
     size_t n = (size_t)c->g.nagg * 9 * 4 * c->ntv * c->ntv * 2;  // reals

@@ -6,6 +6,16 @@
 
 #include "stencil.cuh"
 
+// tuning switches of the FP32 stencil (compile time): MRHS_DS_PRELOAD = 1
+// loads a site's eight neighbour records before its first hop;
+// MRHS_DS_MINB = CTAs of 128 threads per SM the register budget is sized for
+#ifndef MRHS_DS_PRELOAD
+#define MRHS_DS_PRELOAD 1
+#endif
+#ifndef MRHS_DS_MINB
+#define MRHS_DS_MINB 4
+#endif
+
 namespace mrhs {
 namespace {
 
@@ -209,6 +219,18 @@ __global__ void __launch_bounds__(128, MINB) k_dslash_f2(const float* __restrict
   if (t >= nwork) return;
   const int r0 = q0 + (int)(t % ng) * G;
   const size_t s = t / ng;
+  // the eight neighbour records of the site, loaded first (their latency
+  // overlaps the clover term) so that every hop waits for one round trip
+  // (its spinor), not two (index, then spinor)
+  int nb[8];
+#if MRHS_DS_PRELOAD
+  {
+    const int4 n0 = __ldg(reinterpret_cast<const int4*>(nbr + s * 8));
+    const int4 n1 = __ldg(reinterpret_cast<const int4*>(nbr + s * 8) + 1);
+    nb[0] = n0.x, nb[1] = n0.y, nb[2] = n0.z, nb[3] = n0.w;
+    nb[4] = n1.x, nb[5] = n1.y, nb[6] = n1.z, nb[7] = n1.w;
+  }
+#endif
   c2 o[12][P];
   {
     const float4* A4 = reinterpret_cast<const float4*>(Acl + s * 72);
@@ -256,7 +278,10 @@ __global__ void __launch_bounds__(128, MINB) k_dslash_f2(const float* __restrict
   for (int d = 0; d < 2; ++d) {
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
-      const size_t n = (size_t)(__ldg(nbr + s * 8 + d * 4 + mu) & 0x3fffffff);
+#if !MRHS_DS_PRELOAD
+      nb[d * 4 + mu] = __ldg(nbr + s * 8 + d * 4 + mu);
+#endif
+      const size_t n = (size_t)(nb[d * 4 + mu] & 0x3fffffff);
       const float* xn = x + n * 24 * N + r0;
       const float* Ul = U20 + ((d == 0 ? s : n) * 4 + mu) * 20;
       if (d == 0) {
@@ -305,7 +330,7 @@ void launch_dslash_f2(mrhs_ctx c, const float* x, float* y, int N) {
   const int nq = N / passes;
   const size_t work = (size_t)c->g.V * (nq / 2);
   for (int p = 0; p < passes; ++p)
-    k_dslash_f2<1, NC, 4><<<grid_for(work, 128), 128, 0, c->stream>>>(x, y, c->U20, c->A32, c->nbr, N, p * nq, nq,
+    k_dslash_f2<1, NC, MRHS_DS_MINB><<<grid_for(work, 128), 128, 0, c->stream>>>(x, y, c->U20, c->A32, c->nbr, N, p * nq, nq,
                                                                        work);
 }
 
@@ -438,6 +463,8 @@ extern "C" {
 int mrhs_apply_D(mrhs_ctx c, const void* x, void* y, int nrhs, int dtype) {
   return guarded(c, [&] {
     MRHS_REQUIRE(c && x && y, MRHS_ERR_ARG, "null argument");
+    require_dev(c, x, "mrhs_apply_D x");
+    require_dev(c, y, "mrhs_apply_D y");
     dslash(c, x, y, nullptr, nrhs, dtype, DS_FULL, -1);
   });
 }
@@ -445,6 +472,8 @@ int mrhs_apply_D(mrhs_ctx c, const void* x, void* y, int nrhs, int dtype) {
 int mrhs_apply_D_block(mrhs_ctx c, const void* x, void* y, int nrhs, int dtype) {
   return guarded(c, [&] {
     MRHS_REQUIRE(c && x && y, MRHS_ERR_ARG, "null argument");
+    require_dev(c, x, "mrhs_apply_D_block x");
+    require_dev(c, y, "mrhs_apply_D_block y");
     dslash(c, x, y, nullptr, nrhs, dtype, DS_BLOCK, -1);
   });
 }
@@ -452,6 +481,8 @@ int mrhs_apply_D_block(mrhs_ctx c, const void* x, void* y, int nrhs, int dtype) 
 int mrhs_sap(mrhs_ctx c, const void* b, void* x, int nrhs, int dtype, int n_sweeps, int n_mr) {
   return guarded(c, [&] {
     MRHS_REQUIRE(c && b && x, MRHS_ERR_ARG, "null argument");
+    require_dev(c, b, "mrhs_sap b");
+    require_dev(c, x, "mrhs_sap x");
     MRHS_REQUIRE(dtype == MRHS_F64 || dtype == MRHS_F32, MRHS_ERR_ARG, "smoother fields must be F64 or F32");
     sap(c, b, x, nrhs, dtype, n_sweeps, n_mr);
   });

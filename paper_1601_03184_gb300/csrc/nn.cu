@@ -384,6 +384,7 @@ void nn_destroy(mrhs_ctx c) {
 namespace {
 
 NNState& nn_of(mrhs_ctx c) {
+  MRHS_REQUIRE(c, MRHS_ERR_ARG, "null context");
   MRHS_REQUIRE(c->nn, MRHS_ERR_STATE, "mrhs_nn_create has not been called");
   return *c->nn;
 }
@@ -610,6 +611,7 @@ int mrhs_nn_set_weights(mrhs_ctx c, const float* host) {
   return guarded(c, [&] {
     MRHS_REQUIRE(host, MRHS_ERR_ARG, "null argument");
     NNState& s = nn_of(c);
+    require_host(c, host, "mrhs_nn_set_weights host");
     MRHS_CUDA(cudaMemcpyAsync(s.W, host, sizeof(float) * (2 * s.nw + s.nb), cudaMemcpyHostToDevice, c->stream));
     refresh_compute_weights(c, s);
     MRHS_CUDA(cudaStreamSynchronize(c->stream));
@@ -620,6 +622,7 @@ int mrhs_nn_get_weights(mrhs_ctx c, float* host, int compute_copy) {
   return guarded(c, [&] {
     MRHS_REQUIRE(host, MRHS_ERR_ARG, "null argument");
     NNState& s = nn_of(c);
+    require_host(c, host, "mrhs_nn_get_weights host");
     MRHS_CUDA(cudaMemcpyAsync(host, compute_copy ? s.Wc : s.W, sizeof(float) * (2 * s.nw + s.nb),
                               cudaMemcpyDeviceToHost, c->stream));
     MRHS_CUDA(cudaStreamSynchronize(c->stream));
@@ -630,6 +633,7 @@ int mrhs_nn_get_grads(mrhs_ctx c, float* host) {
   return guarded(c, [&] {
     MRHS_REQUIRE(host, MRHS_ERR_ARG, "null argument");
     NNState& s = nn_of(c);
+    require_host(c, host, "mrhs_nn_get_grads host");
     MRHS_CUDA(cudaMemcpyAsync(host, s.G, sizeof(float) * (2 * s.nw + s.nb), cudaMemcpyDeviceToHost, c->stream));
     MRHS_CUDA(cudaStreamSynchronize(c->stream));
   });
@@ -644,7 +648,9 @@ int mrhs_nn_zero_grads(mrhs_ctx c) {
 
 int mrhs_nn_forward(mrhs_ctx c, const void* in, void* out, int nrhs) {
   return guarded(c, [&] {
-    MRHS_REQUIRE(in && out && nrhs >= 1, MRHS_ERR_ARG, "bad argument");
+    MRHS_REQUIRE(c && in && out && nrhs >= 1, MRHS_ERR_ARG, "bad argument");
+    require_dev(c, in, "mrhs_nn_forward in");
+    require_dev(c, out, "mrhs_nn_forward out");
     MRHS_REQUIRE(c->have_gauge, MRHS_ERR_STATE, "nn forward before mrhs_set_gauge");
     nn_forward_impl(c, (const float*)in, (float*)out, nrhs);
   });
@@ -652,14 +658,19 @@ int mrhs_nn_forward(mrhs_ctx c, const void* in, void* out, int nrhs) {
 
 int mrhs_nn_backward(mrhs_ctx c, const void* grad_out, void* grad_in, int nrhs) {
   return guarded(c, [&] {
-    MRHS_REQUIRE(grad_out && nrhs >= 1, MRHS_ERR_ARG, "bad argument");
+    MRHS_REQUIRE(c && grad_out && nrhs >= 1, MRHS_ERR_ARG, "bad argument");
+    require_dev(c, grad_out, "mrhs_nn_backward grad_out");
+    require_dev(c, grad_in, "mrhs_nn_backward grad_in");
     nn_backward(c, (const float*)grad_out, (float*)grad_in, nrhs);
   });
 }
 
 int mrhs_nn_loss(mrhs_ctx c, const void* v, void* grad_v, int nrhs, double lambda, double* loss, double* per_rhs) {
   return guarded(c, [&] {
-    MRHS_REQUIRE(v && loss && nrhs >= 1, MRHS_ERR_ARG, "bad argument");
+    MRHS_REQUIRE(c && v && loss && nrhs >= 1, MRHS_ERR_ARG, "bad argument");
+    require_dev(c, v, "mrhs_nn_loss v");
+    require_dev(c, grad_v, "mrhs_nn_loss grad_v");
+    require_host(c, per_rhs, "mrhs_nn_loss per_rhs");
     *loss = nn_loss(c, (const float*)v, (float*)grad_v, nrhs, lambda, per_rhs);
   });
 }
@@ -678,7 +689,8 @@ int mrhs_nn_adam(mrhs_ctx c, float lr, float beta1, float beta2, float eps, int 
 
 int mrhs_nn_train_step(mrhs_ctx c, const void* v_in, int nrhs, double lambda, float lr, int step, double* loss) {
   return guarded(c, [&] {
-    MRHS_REQUIRE(v_in && loss && nrhs >= 1, MRHS_ERR_ARG, "bad argument");
+    MRHS_REQUIRE(c && v_in && loss && nrhs >= 1, MRHS_ERR_ARG, "bad argument");
+    require_dev(c, v_in, "mrhs_nn_train_step v_in");
     NNState& s = nn_of(c);
     const size_t n = (size_t)c->g.V * 24 * nrhs;
     float* out = (float*)scratch(c, SC_FINE3, sizeof(float) * n * 2);

@@ -44,6 +44,8 @@ extern "C" int mrhs_coarse_solve_noalloc(mrhs_ctx c, const void* bc, void* xc, i
                                          int restart, int maxit, int* iters) {
   return guarded(c, [&] {
     MRHS_REQUIRE(c && bc && xc, MRHS_ERR_ARG, "null argument");
+    require_dev(c, bc, "mrhs_coarse_solve_noalloc bc");
+    require_dev(c, xc, "mrhs_coarse_solve_noalloc xc");
     MRHS_REQUIRE(nrhs >= 1 && nrhs <= 256 && restart >= 1 && restart <= 64, MRHS_ERR_ARG,
                  "coarse solve: need 1 <= nrhs <= 256, 1 <= restart <= 64");
     MRHS_REQUIRE(dtype == MRHS_F64 || dtype == MRHS_F32, MRHS_ERR_ARG, "coarse fields are F64 or F32");

@@ -252,6 +252,7 @@ extern "C" {
 int mrhs_setup_init(mrhs_ctx c, const void* tv0, int dtype, int init_mode, int n_sweeps, int n_mr) {
   return guarded(c, [&] {
     MRHS_REQUIRE(c && tv0, MRHS_ERR_ARG, "null argument");
+    require_dev(c, tv0, "mrhs_setup_init tv0");
     setup_init(c, tv0, dtype, init_mode, n_sweeps, n_mr);
   });
 }
@@ -259,6 +260,7 @@ int mrhs_setup_init(mrhs_ctx c, const void* tv0, int dtype, int init_mode, int n
 int mrhs_setup_init_learned(mrhs_ctx c, const void* tv0, int dtype, int n_sweeps, int n_mr) {
   return guarded(c, [&] {
     MRHS_REQUIRE(c && tv0, MRHS_ERR_ARG, "null argument");
+    require_dev(c, tv0, "mrhs_setup_init_learned tv0");
     setup_init_learned(c, tv0, dtype, n_sweeps, n_mr);
   });
 }
@@ -276,6 +278,8 @@ int mrhs_solve_fgmres(mrhs_ctx c, const double* b, double* x, double tol, int re
   int rc = MRHS_OK;
   int st = guarded(c, [&] {
     MRHS_REQUIRE(c && b && x, MRHS_ERR_ARG, "null argument");
+    require_host(c, b, "mrhs_solve_fgmres b");
+    require_host(c, x, "mrhs_solve_fgmres x");
     rc = solve_fgmres(c, b, x, tol, restart, maxit, coarse_tol, coarse_restart, coarse_maxit, n_sweeps, n_mr, iters,
                       relres);
   });

@@ -117,42 +117,77 @@ def test_header_is_plain_c_and_links(lib, tmp_path):
     assert out.stdout.strip() == "%d entry points" % len(names)
 
 
-def test_short_buffers_are_refused_before_the_library_is_called(monkeypatch):
-    """The binding compares every numpy array or torch tensor passed as a
-    field with the library's size for that field and refuses a short one, so
-    a kernel never reads or writes past the end of a caller's buffer."""
-    import numpy as np
-    import torch
+class FakeCudaTensor:
+    """Stands in for a torch CUDA tensor on a CPU-only machine: the binding
+    reads only these attributes of a device-field argument."""
 
-    calls = []
+    class _Dev:
+        def __init__(self, index):
+            self.index = index
 
+    def __init__(self, nbytes, device=0, contiguous=True):
+        self.nbytes_ = nbytes
+        self.is_cuda = True
+        self.device = self._Dev(device)
+        self.contiguous = contiguous
+
+    def data_ptr(self):
+        return 1 << 20
+
+    def is_contiguous(self):
+        return self.contiguous
+
+    def numel(self):
+        return self.nbytes_
+
+    def element_size(self):
+        return 1
+
+
+def _fake_library(monkeypatch, calls):
     class FakeLib:
         def __getattr__(self, name):
             return lambda *a: calls.append(name) or 0
 
     monkeypatch.setattr(pkg, "lib", lambda: FakeLib())
     monkeypatch.setattr(pkg, "mrhs_field_bytes", lambda ctx, nrhs, dtype, coarse=0: (2048 if coarse else 1024) * nrhs)
+    monkeypatch.setattr(pkg, "mrhs_info", lambda ctx: [0, 0, 0, 2, 0, 0, 0, 0])  # ntv 2 on cuda:0
+
+
+def _field_cases(np):
     F64 = pkg.MRHS_F64
-    fine = lambda n: np.zeros(128 * n, np.float64)       # exactly 1024 bytes per right-hand side
-    coarse = lambda n: torch.zeros(512 * n, dtype=torch.float32)  # exactly 2048 bytes per right-hand side
-    cases = [
-        ("mrhs_apply_D", lambda f, c: pkg.mrhs_apply_D(1, f(2), f(2), 2, F64), "ff"),
-        ("mrhs_apply_D_block", lambda f, c: pkg.mrhs_apply_D_block(1, f(2), f(2), 2, F64), "ff"),
-        ("mrhs_sap", lambda f, c: pkg.mrhs_sap(1, f(2), f(2), 2, F64, 1, 1), "ff"),
-        ("mrhs_restrict", lambda f, c: pkg.mrhs_restrict(1, f(2), c(2), 2, F64), "fc"),
-        ("mrhs_prolong", lambda f, c: pkg.mrhs_prolong(1, c(2), f(2), 2, F64), "cf"),
-        ("mrhs_apply_Dc", lambda f, c: pkg.mrhs_apply_Dc(1, c(2), c(2), 2, F64), "cc"),
-        ("mrhs_coarse_solve", lambda f, c: pkg.mrhs_coarse_solve(1, c(2), c(2), 2, F64, 0.1, 4, 4), "cc"),
-        ("mrhs_coarse_solve_noalloc", lambda f, c: pkg.mrhs_coarse_solve_noalloc(1, c(2), c(2), 2, F64, 0.1, 4, 4),
-         "cc"),
-        ("mrhs_pack", lambda f, c: pkg.mrhs_pack(1, np.zeros(1), F64, f(2), F64, 2), "f"),
-        ("mrhs_unpack", lambda f, c: pkg.mrhs_unpack(1, f(2), F64, np.zeros(1), F64, 2), "f"),
-        ("mrhs_pack_coarse", lambda f, c: pkg.mrhs_pack_coarse(1, np.zeros(1), F64, c(2), F64, 2), "c"),
-        ("mrhs_unpack_coarse", lambda f, c: pkg.mrhs_unpack_coarse(1, c(2), F64, np.zeros(1), F64, 2), "c"),
+    return [
+        ("mrhs_apply_D", lambda f, c: pkg.mrhs_apply_D(1, f(2), f(2), 2, F64)),
+        ("mrhs_apply_D_block", lambda f, c: pkg.mrhs_apply_D_block(1, f(2), f(2), 2, F64)),
+        ("mrhs_sap", lambda f, c: pkg.mrhs_sap(1, f(2), f(2), 2, F64, 1, 1)),
+        ("mrhs_restrict", lambda f, c: pkg.mrhs_restrict(1, f(2), c(2), 2, F64)),
+        ("mrhs_prolong", lambda f, c: pkg.mrhs_prolong(1, c(2), f(2), 2, F64)),
+        ("mrhs_apply_Dc", lambda f, c: pkg.mrhs_apply_Dc(1, c(2), c(2), 2, F64)),
+        ("mrhs_coarse_solve", lambda f, c: pkg.mrhs_coarse_solve(1, c(2), c(2), 2, F64, 0.1, 4, 4)),
+        ("mrhs_coarse_solve_noalloc", lambda f, c: pkg.mrhs_coarse_solve_noalloc(1, c(2), c(2), 2, F64, 0.1, 4, 4)),
+        ("mrhs_pack", lambda f, c: pkg.mrhs_pack(1, np.zeros(1), F64, f(2), F64, 2)),
+        ("mrhs_unpack", lambda f, c: pkg.mrhs_unpack(1, f(2), F64, np.zeros(1), F64, 2)),
+        ("mrhs_pack_coarse", lambda f, c: pkg.mrhs_pack_coarse(1, np.zeros(1), F64, c(2), F64, 2)),
+        ("mrhs_unpack_coarse", lambda f, c: pkg.mrhs_unpack_coarse(1, c(2), F64, np.zeros(1), F64, 2)),
+        ("mrhs_set_tv", lambda f, c: pkg.mrhs_set_tv(1, f(2), F64)),
+        ("mrhs_setup_init", lambda f, c: pkg.mrhs_setup_init(1, f(2), F64, 0, 1, 1)),
+        ("mrhs_setup_init_learned", lambda f, c: pkg.mrhs_setup_init_learned(1, f(2), F64, 1, 1)),
     ]
-    short_f = lambda n: np.zeros(128 * n - 1, np.float64)
-    short_c = lambda n: torch.zeros(512 * n - 1, dtype=torch.float32)
-    for name, call, _ in cases:
+
+
+def test_short_buffers_are_refused_before_the_library_is_called(monkeypatch):
+    """The binding compares every torch tensor passed as a field with the
+    library's size for that field and refuses a short one, so a kernel never
+    reads or writes past the end of a caller's buffer."""
+    import numpy as np
+
+    calls = []
+    _fake_library(monkeypatch, calls)
+    fine = lambda n: FakeCudaTensor(1024 * n)
+    coarse = lambda n: FakeCudaTensor(2048 * n)
+    short_f = lambda n: FakeCudaTensor(1024 * n - 1)
+    short_c = lambda n: FakeCudaTensor(2048 * n - 1)
+    for name, call in _field_cases(np):
         calls.clear()
         call(fine, coarse)
         assert calls[-1] == name
@@ -166,12 +201,48 @@ def test_short_buffers_are_refused_before_the_library_is_called(monkeypatch):
             else:
                 # this call has no argument of the shortened kind
                 assert calls == [name]
-    # raw integer pointers are passed through; strided arrays are refused
+    # raw integer pointers are passed through (the library checks them);
+    # non-contiguous tensors are refused
     calls.clear()
-    pkg.mrhs_apply_D(1, 4096, 8192, 2, F64)
+    pkg.mrhs_apply_D(1, 4096, 8192, 2, pkg.MRHS_F64)
     assert calls == ["mrhs_apply_D"]
     with pytest.raises(ValueError):
-        pkg.mrhs_apply_D(1, np.zeros(512)[::2], fine(2), 2, F64)
+        pkg.mrhs_apply_D(1, FakeCudaTensor(2048, contiguous=False), fine(2), 2, pkg.MRHS_F64)
+
+
+def test_host_memory_is_refused_as_a_device_field(monkeypatch):
+    """A numpy array, a CPU tensor or a CUDA tensor of another GPU passed
+    where the library expects a device field of the context's GPU is refused
+    by the binding before any call: a host address handed to a kernel would
+    fault the GPU. A CUDA tensor passed where a host array is expected is
+    refused too."""
+    import numpy as np
+    import torch
+
+    calls = []
+    _fake_library(monkeypatch, calls)
+    good_f = lambda n: FakeCudaTensor(1024 * n)
+    good_c = lambda n: FakeCudaTensor(2048 * n)
+    wrong = [lambda n, k=k: k(n) for k in (lambda n: np.zeros(1024 * n, np.uint8),
+                                            lambda n: torch.zeros(1024 * n, dtype=torch.uint8),
+                                            lambda n: FakeCudaTensor(4096 * n, device=1))]
+    for name, call in _field_cases(np):
+        for w in wrong:
+            for f, c in ((w, good_c), (good_f, w)):
+                calls.clear()
+                try:
+                    call(f, c)
+                except pkg.MrhsError as e:
+                    assert e.status == pkg.MRHS_ERR_ARG, (name, str(e))
+                    assert calls == [], name
+                else:
+                    assert calls == [name]  # no argument of this kind
+    for call in (lambda: pkg.mrhs_pack(1, FakeCudaTensor(64), pkg.MRHS_F64, good_f(2), pkg.MRHS_F64, 2),
+                 lambda: pkg.mrhs_unpack(1, good_f(2), pkg.MRHS_F64, FakeCudaTensor(64), pkg.MRHS_F64, 2)):
+        calls.clear()
+        with pytest.raises(pkg.MrhsError):
+            call()
+        assert calls == []
 
 
 def test_lattice_refuses_misshapen_host_arrays():

@@ -89,6 +89,39 @@ def test_identity_network():
     assert np.abs(y - x).max() < 1e-15
 
 
+def test_modrelu_closed_form():
+    """The nonlinearity between layers written out: every colour triplet z
+    of a hidden channel c becomes z max(0, |z| + b_c) / |z| (|z| the norm of
+    the triplet, 0 for z = 0). Network: layer 1 mixes the four input channels
+    at the site only (k = 0), layers 2 and 3 are the identity, the second
+    bias is 0 (so the second modReLU is the identity), the first has both
+    signs, with magnitudes that switch some triplets off and leave others
+    shrunk or grown. A bias entering as |z| - b, a norm over the wrong index
+    or a missing division by |z| fails this."""
+    widths = (4, 4, 4, 4)
+    nw, nb = oracle.nn_sizes(widths)
+    rng = np.random.default_rng(51)
+    W1 = rng.standard_normal((4, 4)) + 1j * rng.standard_normal((4, 4))
+    W = np.zeros(nw, np.complex128)
+    W[:16] = W1.reshape(-1)  # layer 1, k = 0, [c_out][c_in]
+    for layer in (1, 2):
+        off = layer * 9 * 16
+        for c in range(4):
+            W[off + c * 4 + c] = 1.0
+    x = inputs.gaussian_field((2, vol(DIMS), 12), 52)
+    z = np.einsum("oi,rsic->rsoc", W1, x.reshape(2, vol(DIMS), 4, 3))
+    mag = np.linalg.norm(z, axis=-1)
+    b1 = np.array([-0.8, 0.5, -0.3 * np.median(mag), -1.5 * np.median(mag)])
+    bias = np.concatenate([b1, np.zeros(4)])
+    U = inputs.gauge_field(DIMS, 0.5, 53)
+    y = oracle.nn_forward(DIMS, U, widths, W, bias, x)
+    gain = np.maximum(0.0, mag + b1[None, None, :]) / mag
+    ref = (z * gain[..., None]).reshape(x.shape)
+    assert np.abs(y - ref).max() < 1e-13 * np.abs(ref).max()
+    # the chosen biases exercise every regime
+    assert (gain[..., 3] == 0).any() and (gain[..., 3] > 0).any() and (gain[..., 1] > 1).all()
+
+
 def test_loss_gradient_by_central_differences():
     dims, agg, ntv = (4, 4, 4, 4), (2, 2, 2, 2), 4
     U = inputs.gauge_field(dims, 0.3, 41)

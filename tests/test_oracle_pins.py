@@ -517,6 +517,41 @@ def test_init_modes_agree_for_one_sweep():
         assert np.array_equal(u, v)
 
 
+def test_init_mode_1_is_repeated_single_sweep_calls():
+    """The second reading of the initial phase (Sec. 2, 'a few iterations with
+    starting guess 0'): n_sweeps calls of ONE sweep, each v <- SAP(b = v,
+    x0 = 0), the result of a call becoming the right-hand side of the next,
+    normalised once at the end. With 400 MR steps per domain the oracle at
+    three sweeps must equal that composition written with dense block solves;
+    it must also differ from the one-call reading (init_mode 0), which a
+    carried-over starting guess or a reused right-hand side would reproduce."""
+    dims, agg, ntv = C1["dims"], C1["agg"], 3
+    U, A = c1_field()
+    D = dense_D(dims, U, A)
+    Ag = aggregate_of_sites(dims, agg)
+    nb = [d // a for d, a in zip(dims, agg)]
+    colour = np.stack(np.unravel_index(Ag, nb[::-1]), axis=1)[:, ::-1].sum(axis=1) % 2
+    tv0 = inputs.test_vectors(ntv, dims, 93)
+    prm1 = oracle.make_params(init_mode=1, n_init_sweeps=3, n_init_mr=400)
+    prm0 = oracle.make_params(init_mode=0, n_init_sweeps=3, n_init_mr=400)
+    tv1, _, _ = oracle.setup_init(dims, agg, U, A, tv0, prm1)
+    tv0m, _, _ = oracle.setup_init(dims, agg, U, A, tv0, prm0)
+    ref, ref0 = [], []
+    zero = np.zeros(D.shape[0], complex)
+    for j in range(ntv):
+        v = tv0[j].reshape(-1)
+        for _ in range(3):
+            v = _dense_sap_exact(D, Ag, colour, v, zero, 1)
+        ref.append(v / np.linalg.norm(v))
+        w = _dense_sap_exact(D, Ag, colour, tv0[j].reshape(-1), zero, 3)
+        ref0.append(w / np.linalg.norm(w))
+    ref = np.array(ref).reshape(tv1.shape)
+    ref0 = np.array(ref0).reshape(tv1.shape)
+    assert np.abs(tv1 - ref).max() < 1e-10
+    assert np.abs(tv0m - ref0).max() < 1e-10
+    assert np.abs(ref - ref0).max() > 1e-2  # the two readings are different maps
+
+
 def test_gamma5_fine_helper_consistent():
     g = gamma5_fine(2)
     assert g.shape == (24, 24) and np.allclose(np.diag(g)[:12], [1] * 6 + [-1] * 6)
