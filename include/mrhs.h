@@ -15,6 +15,11 @@
  *    the call. Device pointers are owned by the caller, must be 16-byte
  *    aligned, and are read/written in stream order on the context's stream
  *    (the call may return before the GPU has finished; mrhs_sync waits).
+ *    Every call checks the memory type of the caller's pointers before any
+ *    launch or copy (cudaPointerGetAttributes): host memory or another GPU's
+ *    memory where a device field of the context's GPU is expected, or device
+ *    memory where a host array is expected, returns MRHS_ERR_ARG. Managed
+ *    memory is accepted for both.
  *    Everything the library allocates is freed by mrhs_destroy.
  *  - Sites: canonical index s = x + Lx*(y + Ly*(z + Lz*t)); spinor component
  *    c = 3*spin + colour; chirality h = 0 for spins 0,1 (gamma_5 = +1), h = 1
@@ -89,7 +94,7 @@ const char* mrhs_last_error(mrhs_ctx ctx);
  * wait of a tensor-core coarse-stencil launch ran out since the last check */
 int mrhs_sync(mrhs_ctx ctx);
 /* out[0..7] = V, nagg, sites per aggregate, ntv, prec, device bytes held by
- * the library, number of SMs, 0 */
+ * the library, number of SMs, the CUDA device the context lives on */
 int mrhs_info(mrhs_ctx ctx, long long out[8]);
 
 /* release the context's scratch buffers (work fields, Krylov bases, staging);
