@@ -183,7 +183,7 @@ def kernel_work(name, cfg, launches_per_step, bytes_f=4):
         return V * (link4 + clov + 2 * N * spin), V * N * flop_site_rhs
     if name == "dslash_resid":  # one colour: r = b - D x on half of the sites
         return V / 2 * (link4 + clov + 3 * N * spin), V / 2 * N * flop_site_rhs
-    if name in ("sap_tm", "sap_fused8", "sap_fused"):  # one colour: residual + n_mr MR steps, on chip
+    if name in ("sap_tm", "sap_tm2", "sap_fused8", "sap_fused"):  # one colour: residual + n_mr MR steps, on chip
         nmr = SCHEDULE["smooth_mr"]
         flops = V / 2 * N * (flop_site_rhs + nmr * (flop_site_rhs + 336))
         byt = V / 2 * (link4 + clov + 3 * N * spin)  # b in, x in and out, links and clover once
@@ -319,10 +319,27 @@ def run_ours(args, cfg, cfg_name, m0, m0_src, rank, world, local_rank):
     torch.cuda.synchronize()
     st_ms = ev0.elapsed_time(ev1) / reps
     st_bytes, st_flops = kernel_work("dslash_full", cfg, 1)
-    stencil = {"ms": st_ms, "gbs": st_bytes / st_ms / 1e6, "frac": st_bytes / st_ms / 1e6 / hbm_peak,
-               "peak_gbs": hbm_peak, "peak_source": hbm_src, "bytes_per_launch": st_bytes,
-               "tflops": st_flops / st_ms / 1e9, "nrhs": N}
-    del y
+    stencil = {"ms": round(st_ms, 3), "gbs": round(st_bytes / st_ms / 1e6, 1),
+               "frac": round(st_bytes / st_ms / 1e6 / hbm_peak, 4), "peak_gbs": hbm_peak,
+               "peak_source": hbm_src, "bytes_per_launch": st_bytes, "tflops": round(st_flops / st_ms / 1e9, 2),
+               "nrhs": N}
+    # ---- the same stencil with bf16 storage (FP32 arithmetic): FP32-ALU-bound,
+    # reported against the FP32 peak
+    xb = tv0.to(torch.bfloat16)
+    yb = torch.empty_like(xb)
+    for _ in range(3):
+        lat.apply_D(xb, yb, N, pkg.MRHS_BF16)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(reps):
+        lat.apply_D(xb, yb, N, pkg.MRHS_BF16)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    sb_ms = ev0.elapsed_time(ev1) / reps
+    sb_bytes = V * (288 + 288 + 2 * 48 * N)
+    stencil_bf16 = {"ms": round(sb_ms, 3), "gbs": round(sb_bytes / sb_ms / 1e6, 1),
+                    "tflops": round(st_flops / sb_ms / 1e9, 2), "nrhs": N}
+    del y, xb, yb
     torch.cuda.empty_cache()
 
     def step():
@@ -392,29 +409,45 @@ def run_ours(args, cfg, cfg_name, m0, m0_src, rank, world, local_rank):
         e2e = run_e2e(args, lat, U, tv0, cfg, m0, stream, barrier)
         e2e["value"] = whole_job_seconds_per_setup(1000.0 * reduce_max_over_ranks(e2e["value"], dist), world)
 
+    # ---- the order of Algorithm 1 (one vector at a time) against Algorithm 2
+    # with N_b = N_tv on this GPU: one refinement iteration per block length
+    srhs = None
+    if not args.no_srhs:
+        srhs = run_block_lengths(lat, tv0, stream, (N, 8, 1) if N > 8 else (N, 1))
     # ---- the quality check of the plain setup: two-level FGMRES to 1e-10
     fg_plain = None
     if not args.no_fgmres:
         pkg.mrhs_trim(lat.ctx)
         fg_plain = fgmres_check(lat, cfg)
     gpu_launches = int(sum(v[0] for v in prof.values()) / args.steps)
+    sms = lat.info()[6]
+    clock = clk.get("sm_mhz") or peak_json.get("clocks_under_load", {}).get("sm_mhz_median", 1432.0)
+    fp32_peak = sms * 128 * 2 * clock * 1e6 / 1e12
+    stencil_bf16["frac_fp32_peak"] = round(stencil_bf16["tflops"] / fp32_peak, 4)
+    if roof is not None:
+        roof = {k: (round(v, 6) if isinstance(v, float) else v) for k, v in roof.items()}
     line = {
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": cfg_name, "dims": dims, "agg": agg, "ntv": N, "precision": "fp32 (plain setup)",
-                   "m0": m0, "m0_source": m0_src, "csw": cfg["csw"], "roughness": cfg["eps"],
-                   "schedule": SCHEDULE, "parallelism": "replicas" if world > 1 else "single GPU",
-                   "l2": "inputs larger than L2 (test vectors %.1f GB)" % (nb / 1e9),
-                   "last_coarse_iterations": [int(x) for x in np.asarray(its).reshape(-1)[:N]],
-                   "input_generation_s": round(gen_s, 1)},
+        "config": {"workload": cfg_name, "ntv": N, "precision": "fp32 (plain setup)", "m0": round(m0, 6),
+                   "m0_source": m0_src, "csw": cfg["csw"], "roughness": cfg["eps"],
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (test vectors %.1f GB)" % (nb / 1e9)},
         "roofline": roof,
         "stencil": stencil,
-        "kernels": kernels,
+        "stencil_bf16": stencil_bf16,
         "clocks": clk,
         "gpu_launches": gpu_launches,
         "e2e": e2e,
     }
+    if srhs is not None:
+        line["srhs_over_mrhs"] = srhs["srhs_over_mrhs"]
+    # per-kernel tables and the rest of the detail go to stderr, so that the
+    # one JSON line on stdout stays short
+    detail = {"kernels": kernels, "dims": dims, "agg": agg, "schedule": SCHEDULE,
+              "last_coarse_iterations": [int(x) for x in np.asarray(its).reshape(-1)[:N]],
+              "input_generation_s": round(gen_s, 1), "stencil_fp32": stencil, "block_lengths": srhs}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, scaled, threads, desc = cpu_sample(cfg, m0)
         line["cpu_baseline"] = {"value": scaled, "unit": "s", "cores": threads, "kind": "oracle", "sample": desc}
@@ -424,11 +457,71 @@ def run_ours(args, cfg, cfg_name, m0, m0_src, rank, world, local_rank):
         lat.close()
         del tv0
         torch.cuda.empty_cache()
-        line["learned_mixed"] = run_learned_mixed(args, cfg, U, m0, stream, ms, barrier, dist, world)
+        lm = run_learned_mixed(args, cfg, U, m0, stream, ms, barrier, dist, world)
+        detail["learned_mixed"] = lm
+        line["learned_mixed"] = {"value": round(lm["value"], 4), "unit": "s",
+                                 "ratio_vs_plain": round(lm["ratio_vs_plain"], 4),
+                                 "fgmres_iterations": (lm["fgmres"] or {}).get("iterations"),
+                                 "widths": lm["widths"], "storage": "bf16"}
     if rank == 0:
+        print("bench detail: " + json.dumps(detail), file=sys.stderr, flush=True)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+# kernel classes of the library's profile grouped into the phases the paper
+# times separately (Sec. 7): smoother, coarse grid, projections, setup of R
+# and D_c, and the copies that move a block of test vectors in and out
+PHASES = {"smoother": ("sap_tm", "sap_tm2", "sap_fused", "sap_fused8", "sap_block_mr", "dslash_resid"),
+          "coarse_grid": ("apply_dc_tc", "apply_dc", "multi_dot", "multi_axpy"),
+          "projections": ("restrict", "prolong"),
+          "R_and_Dc": ("gs_cholqr2", "coarse_op", "coarse_op_tc", "format_dc"),
+          "block_copies": ("block_gather",)}
+
+
+def phase_times(prof):
+    out = {k: 0.0 for k in PHASES}
+    out["other"] = 0.0
+    for name, (_, ms) in prof.items():
+        ph = next((p for p, names in PHASES.items() if name in names), "other")
+        out[ph] += ms
+    return out
+
+
+def run_block_lengths(lat, tv0, stream, block_lengths=(32, 8, 1)):
+    """One refinement iteration (Algorithm 2) of the plain FP32 setup with
+    block length N_b = each of block_lengths, the setup state reset to the
+    same initial phase before each: total and per-phase device time (CUDA
+    events around every launch), and the N_b = 1 / N_b = N_tv ratios, the
+    single- over multiple-right-hand-side speed-up of Sec. 7 on this GPU."""
+    import torch
+
+    import paper_1601_03184_gb300 as pkg
+    from paper_1601_03184_gb300 import MRHS_F32
+
+    res = {}
+    for nb in block_lengths:
+        lat.set_block_length(0)
+        lat.setup_init(tv0, MRHS_F32, 0, SCHEDULE["init_sweeps"], SCHEDULE["init_mr"])
+        lat.set_block_length(nb)
+        torch.cuda.synchronize()
+        pkg.mrhs_profile(lat.ctx, 1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lat.setup_refine(1, SCHEDULE["smooth_sweeps"], SCHEDULE["smooth_mr"], SCHEDULE["coarse_tol"],
+                         SCHEDULE["coarse_restart"], SCHEDULE["coarse_maxit"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = pkg.mrhs_profile_read(lat.ctx)
+        pkg.mrhs_profile(lat.ctx, 0)
+        ph = phase_times(prof)
+        res[nb] = {"ms": round(e0.elapsed_time(e1), 1), **{k: round(v, 1) for k, v in ph.items()}}
+    lat.set_block_length(0)
+    lo, hi = min(block_lengths), max(block_lengths)
+    ratio = {k: round(res[lo][k] / res[hi][k], 2) for k in res[hi] if res[hi][k] > 0}
+    return {"per_block_length_ms": {str(k): v for k, v in res.items()}, "srhs_over_mrhs": ratio,
+            "what": "one refinement iteration; N_b = %d vs N_b = %d" % (lo, hi)}
 
 
 def fgmres_check(lat, cfg, seed=3005):
@@ -514,6 +607,7 @@ def run_learned_mixed(args, cfg, U, m0, stream, plain_ms, barrier, dist=None, wo
         fg = fgmres_check(lat, cfg)
     lat.close()
     return {"value": whole_job_seconds_per_setup(lm_ms, world), "unit": "s", "ratio_vs_plain": lm_ms / plain_ms,
+            "widths": list(learned.WIDTHS),
             "form": "1 SAP sweep + network (widths %s, bf16 weights) for the initial phase, bf16 test vectors and P, "
                     "FP32 smoother, D_c contraction on bf16 tensor cores with FP32 accumulation (D_c stored FP32), "
                     "tf32 tensor-core coarse stencil, then the same refinement" % (list(learned.WIDTHS),),
@@ -585,6 +679,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fgmres", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-srhs", action="store_true", help="skip the block-length (N_b) comparison")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", args.gpus if args.gpus else 1))

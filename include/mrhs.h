@@ -217,10 +217,12 @@ int mrhs_restrict(mrhs_ctx ctx, const void* v, void* vc, int nrhs, int dtype);
 int mrhs_prolong(mrhs_ctx ctx, const void* uc, void* u, int nrhs, int dtype);
 /* yc = D_c xc on nrhs coarse right-hand sides (Sec. 5: D_c applied with the
  * same broadcast scheme as the restriction). With F32 coarse fields, nrhs a
- * multiple of 16 up to 64, 2*ntv a multiple of 8 up to 64 and an engine other
- * than MRHS_DC_ALU the products run on the tensor cores (tcgen05, FP32
- * accumulation): split tf32 (hi*hi + hi*lo + lo*hi, FP32 accuracy) for FP32
- * contexts, single tf32 for the mixed ones; otherwise on the CUDA cores. */
+ * multiple of 16 up to 64, 2*ntv a multiple of 8 up to 64, an engine other
+ * than MRHS_DC_ALU and pipeline stages that fit in shared memory (the split
+ * form at 2*ntv = 64 takes up to 48 right-hand sides) the products run on the
+ * tensor cores (tcgen05, FP32 accumulation): split tf32 (hi*hi + hi*lo +
+ * lo*hi, FP32 accuracy) for FP32 contexts, single tf32 for the mixed ones;
+ * otherwise on the CUDA cores. */
 int mrhs_apply_Dc(mrhs_ctx ctx, const void* xc, void* yc, int nrhs, int dtype);
 
 /* Approximate coarse solve of Algorithm 1/2 (relative tolerance 0.05 in Sec. 7):
@@ -263,14 +265,37 @@ int mrhs_coarse_solve_noalloc(mrhs_ctx ctx, const void* bc, void* xc, int nrhs, 
  * storage dtype. */
 int mrhs_setup_init(mrhs_ctx ctx, const void* tv0, int dtype, int init_mode, int n_sweeps, int n_mr);
 
-/* Iterative refinement, Algorithm 2 with block length N_b = ntv (all test
- * vectors at once): n_iter times { vc = R v; uc ~ D_c^-1 vc (coarse GMRES,
- * coarse_tol, coarse_restart, coarse_maxit); x = P uc; x <- SAP^n_sweeps
- * (b = v, x0 = x); v <- x normalised; then P and D_c rebuilt }.
+/* Iterative refinement, Algorithm 2 with block length N_b (default N_b =
+ * ntv: all test vectors at once; see mrhs_set_block_length): n_iter times
+ * { for each block of N_b test vectors in order: vc = R v; uc ~ D_c^-1 vc
+ * (coarse GMRES, coarse_tol, coarse_restart, coarse_maxit); x = P uc;
+ * x <- SAP^n_sweeps(b = v, x0 = x); v <- x normalised; after the last block
+ * P and D_c rebuilt }.
  * coarse_iters (host, may be NULL): [n_iter][ntv] coarse iteration counts.
  * MRHS_ERR_STATE before mrhs_setup_init. */
 int mrhs_setup_refine(mrhs_ctx ctx, int n_iter, int n_sweeps, int n_mr, double coarse_tol, int coarse_restart,
                       int coarse_maxit, int* coarse_iters);
+
+/* Setup update after the gauge field has changed (the situation of HMC,
+ * Sec. 1: the setup must be renewed every few solves): the caller has given
+ * the new field (mrhs_set_gauge) and its clover term (mrhs_build_clover);
+ * D_c is rebuilt from the kept P with the new operator, then n_iter
+ * refinement iterations (as mrhs_setup_refine, same arguments) start from
+ * the kept test vectors instead of new random ones. MRHS_ERR_STATE without an
+ * earlier setup or before mrhs_build_clover. */
+int mrhs_setup_update(mrhs_ctx ctx, int n_iter, int n_sweeps, int n_mr, double coarse_tol, int coarse_restart,
+                      int coarse_maxit, int* coarse_iters);
+
+/* Block length N_b of Algorithm 2 for mrhs_setup_init and
+ * mrhs_setup_refine: the test vectors are processed in blocks of N_b in
+ * order, the last block holding the remainder when N_b does not divide ntv
+ * (the footnote to Algorithm 2). nb = 0 or nb >= ntv: all test vectors at
+ * once (the default, N_b = N_tv). nb = 1 is the single-right-hand-side order
+ * of Algorithm 1. Every N_b gives the same setup up to rounding (R, P and
+ * D_c are fixed while the vectors are visited; only the order of the work
+ * changes, Sec. 3); smaller blocks only take longer. MRHS_ERR_ARG if nb < 0.
+ * The learned initial phase always takes all test vectors at once. */
+int mrhs_set_block_length(mrhs_ctx ctx, int nb);
 
 /* ------------------------------------------------- learned generator */
 

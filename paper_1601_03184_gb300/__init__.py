@@ -62,6 +62,8 @@ _SIGS = {
     "mrhs_coarse_solve_noalloc": (_I, [_VP, _VP, _VP, _I, _I, _D, _I, _I, _VP]),
     "mrhs_setup_init": (_I, [_VP, _VP, _I, _I, _I, _I]),
     "mrhs_setup_refine": (_I, [_VP, _I, _I, _I, _D, _I, _I, _VP]),
+    "mrhs_set_block_length": (_I, [_VP, _I]),
+    "mrhs_setup_update": (_I, [_VP, _I, _I, _I, _D, _I, _I, _VP]),
     "mrhs_get_tv": (_I, [_VP, _VP, _I]),
     "mrhs_get_P": (_I, [_VP, _VP, _I]),
     "mrhs_get_Dc": (_I, [_VP, _VP, _I]),
@@ -350,6 +352,17 @@ def mrhs_setup_refine(ctx, n_iter, n_sweeps, n_mr, coarse_tol, coarse_restart, c
     _check(ctx, lib().mrhs_setup_refine(ctx, int(n_iter), int(n_sweeps), int(n_mr), float(coarse_tol),
                                         int(coarse_restart), int(coarse_maxit), _ptr(its)))
     return its
+
+
+def mrhs_setup_update(ctx, n_iter, n_sweeps, n_mr, coarse_tol, coarse_restart, coarse_maxit, ntv=None):
+    its = np.zeros((max(int(n_iter), 1), int(ntv or 64)), np.int32)
+    _check(ctx, lib().mrhs_setup_update(ctx, int(n_iter), int(n_sweeps), int(n_mr), float(coarse_tol),
+                                        int(coarse_restart), int(coarse_maxit), _ptr(its)))
+    return its
+
+
+def mrhs_set_block_length(ctx, nb):
+    return _check(ctx, lib().mrhs_set_block_length(ctx, int(nb)))
 
 
 def mrhs_get_tv(ctx, host, host_dtype):

@@ -3,8 +3,8 @@
 // that every later solve reuses. Restoring one skips the whole setup.
 //
 // File layout (host byte order): a fixed header, then the raw device images
-// of the test vectors, of P and of D_c, then a 64-bit checksum of those three
-// payloads. The images are in the library's device site order, so the header
+// of the test vectors, of P and of D_c, then a 64-bit checksum of the header
+// (padding zeroed) and the three payloads. The images are in the library's device site order, so the header
 // carries a hash of that order (the canonical -> device site permutation) and
 // a file only loads into a context of the same geometry, N_tv and precision.
 // The gauge field and the clover term are not part of it: they are inputs,
@@ -25,7 +25,7 @@ using namespace mrhs;
 namespace {
 
 constexpr char kMagic[8] = {'M', 'R', 'H', 'S', 'S', 'E', 'T', 'P'};
-constexpr int kVersion = 1;
+constexpr int kVersion = 2;  // 2: the checksum covers the header too
 constexpr size_t kChunk = size_t(64) << 20;  // host staging per copy
 
 struct Header {
@@ -142,6 +142,7 @@ int mrhs_save_setup(mrhs_ctx c, const char* path) {
       MRHS_REQUIRE(out.f, MRHS_ERR_ARG, "checkpoint: cannot open " + part + " for writing");
       MRHS_REQUIRE(std::fwrite(&hd, sizeof hd, 1, out.f) == 1, MRHS_ERR_ARG, "checkpoint: write failed");
       Hash64 h;
+      h.words((const unsigned char*)&hd, sizeof hd);  // fields the load does not compare (tv_scale)
       write_buffer(c, out.f, c->tv, hd.tv_bytes, h);
       write_buffer(c, out.f, c->P, hd.P_bytes, h);
       write_buffer(c, out.f, c->Dc, hd.Dc_bytes, h);
@@ -182,6 +183,7 @@ int mrhs_load_setup(mrhs_ctx c, const char* path) {
     // the context holds no setup until the whole file has been read and checked
     c->have_tv = c->have_P = c->have_Dc = false;
     Hash64 h;
+    h.words((const unsigned char*)&hd, sizeof hd);
     read_buffer(c, in.f, c->tv, hd.tv_bytes, h);
     read_buffer(c, in.f, c->P, hd.P_bytes, h);
     read_buffer(c, in.f, c->Dc, hd.Dc_bytes, h);

@@ -616,6 +616,11 @@ bool apply_Dc_tc(mrhs_ctx c, const void* xc, void* yc, int nrhs, bool split) {
     const size_t btiles = (size_t)(split ? 2 : 1) * (2 * nrhs / 8 * KG * 128);
     smem = std::max(2 * stage, sizeof(float) * kRows * (2 * nrhs + 1)) + btiles;
   }
+  // a shape whose pipeline stages do not fit in shared memory (e.g. 64
+  // right-hand sides in split form at 2 ntv = 64) takes the CUDA-core stencil
+  int maxsm = 0;
+  MRHS_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+  if (smem > (size_t)maxsm) return false;
   Prof pr(c, "apply_dc_tc");
   auto kern = pre ? (split ? k_apply_dc_tc<true, true> : k_apply_dc_tc<false, true>)
                   : (split ? k_apply_dc_tc<true, false> : k_apply_dc_tc<false, false>);

@@ -167,6 +167,7 @@ struct mrhs_ctx_s {
   mrhs::Geometry g;
   int ntv = 0, prec = 0;
   int dc_engine = 0;    // mrhs_dc_engine
+  int block_len = 0;    // N_b of Alg. 2 for the setup phases (0: all ntv at once)
   int tv_dtype = 0;     // storage of test vectors and P
   int work_dtype = 0;   // storage/compute of smoother work fields, D_c, coarse fields (F64 or F32)
   cudaStream_t stream = nullptr;
@@ -244,6 +245,7 @@ enum Scratch {
   SC_FINE3,
   SC_KRYLOV_F,    // FGMRES basis
   SC_MISC,
+  SC_BLOCK,       // one block of test vectors (block length N_b < ntv)
   SC_COUNT
 };
 
@@ -291,6 +293,10 @@ void multi_dot(mrhs_ctx c, const void* X, size_t stride, int K, const void* Y, s
 void norms(mrhs_ctx c, const void* X, size_t rows, int N, int dtype, double* out /* device [N] (squared) */);
 void convert(mrhs_ctx c, const void* x, int dx, void* y, int dy, size_t n);
 void convert_scaled(mrhs_ctx c, const void* x, int dx, void* y, int dy, size_t n, float scale);
+// columns k0 .. k0+nb-1 of a fine field of ntv right-hand sides to a field of
+// nb (same storage type), and back with conversion and a scale factor
+void gather_cols(mrhs_ctx c, const void* src, int ntv, void* dst, int nb, int k0, int dtype);
+void scatter_cols(mrhs_ctx c, const void* src, int ds, int nb, void* dst, int dd, int ntv, int k0, float scale);
 void sap_mixed(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int dtype, int n_sweeps, int n_mr);
 // sap.cu: the on-chip SAP (FP32 work fields)
 bool sap_fused_ok(mrhs_ctx c, int dtype);

@@ -457,6 +457,24 @@ void transfer_coarse(mrhs_ctx c, const void* host_in, void* host_out, int hd, co
 
 }  // namespace
 
+// columns k0 .. k0+nb-1 of a field of ntv right-hand sides <-> a field of nb
+// (rows = sites x 12 components x re/im, right-hand sides innermost)
+template <class S>
+__global__ void k_gather_cols(const S* __restrict__ src, int ntv, S* __restrict__ dst, int nb, int k0, size_t n) {
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const size_t row = t / nb;
+  dst[t] = src[row * ntv + k0 + (int)(t % nb)];
+}
+template <class SI, class SO>
+__global__ void k_scatter_cols(const SI* __restrict__ src, int nb, SO* __restrict__ dst, int ntv, int k0, size_t n,
+                               float scale) {
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const size_t row = t / nb;
+  dst[row * ntv + k0 + (int)(t % nb)] = from_r<SO>((float)to_r(src[t]) * scale);
+}
+
 namespace mrhs {
 void convert(mrhs_ctx c, const void* x, int dx, void* y, int dy, size_t n) {
   Prof pr(c, "convert");
@@ -497,6 +515,18 @@ void require_host(mrhs_ctx c, const void* p, const char* what) {
   }
   MRHS_REQUIRE(a.type != cudaMemoryTypeDevice, MRHS_ERR_ARG,
                std::string(what) + ": device memory passed where a host array is required");
+}
+void gather_cols(mrhs_ctx c, const void* src, int ntv, void* dst, int nb, int k0, int dtype) {
+  const size_t n = (size_t)c->g.V * 24 * nb;
+  Prof pr(c, "block_gather");
+  MRHS_DISPATCH(dtype, S, (k_gather_cols<S><<<grid_for(n, 256), 256, 0, c->stream>>>((const S*)src, ntv, (S*)dst, nb, k0, n)));
+  MRHS_LAUNCH_CHECK("gather_cols");
+}
+void scatter_cols(mrhs_ctx c, const void* src, int ds, int nb, void* dst, int dd, int ntv, int k0, float scale) {
+  const size_t n = (size_t)c->g.V * 24 * nb;
+  Prof pr(c, "block_gather");
+  MRHS_DISPATCH(ds, SI, MRHS_DISPATCH(dd, SO, (k_scatter_cols<SI, SO><<<grid_for(n, 256), 256, 0, c->stream>>>((const SI*)src, nb, (SO*)dst, ntv, k0, n, scale))));
+  MRHS_LAUNCH_CHECK("scatter_cols");
 }
 }  // namespace mrhs
 

@@ -136,9 +136,30 @@ __device__ __forceinline__ void ldp(const float* p, float2 v[P]) {
     v[1] = make_float2(t.z, t.w);
   }
 }
+// bf16 / fp16 storage: one pair of right-hand sides (4 bytes) widened to FP32
+template <int P>
+__device__ __forceinline__ void ldp(const __nv_bfloat16* p, float2 v[P]) {
+  static_assert(P == 1, "reduced storage: one pair per thread");
+  v[0] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+}
+template <int P>
+__device__ __forceinline__ void ldp(const __half* p, float2 v[P]) {
+  static_assert(P == 1, "reduced storage: one pair per thread");
+  v[0] = __half22float2(*reinterpret_cast<const __half2*>(p));
+}
+// store one pair (streaming: the output is not read again by this kernel)
+__device__ __forceinline__ void stp(float* p, float2 v) { __stcs(reinterpret_cast<float2*>(p), v); }
+__device__ __forceinline__ void stp(__nv_bfloat16* p, float2 v) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+  __stcs(reinterpret_cast<unsigned int*>(p), *reinterpret_cast<const unsigned int*>(&h));
+}
+__device__ __forceinline__ void stp(__half* p, float2 v) {
+  const __half2 h = __floats2half2_rn(v.x, v.y);
+  __stcs(reinterpret_cast<unsigned int*>(p), *reinterpret_cast<const unsigned int*>(&h));
+}
 
-template <int MU, int DIR, int P, int NC>
-__device__ __forceinline__ void hop_f2(c2 o[12][P], const float* __restrict__ xn, int Nrt,
+template <int MU, int DIR, int P, int NC, class S>
+__device__ __forceinline__ void hop_f2(c2 o[12][P], const S* __restrict__ xn, int Nrt,
                                        const float* __restrict__ Ul) {
   const int N = NC > 0 ? NC : Nrt;
   c2 h[2][3][P];
@@ -206,8 +227,8 @@ __device__ __forceinline__ void hop_f2(c2 o[12][P], const float* __restrict__ xn
   }
 }
 
-template <int P, int NC, int MINB>
-__global__ void __launch_bounds__(128, MINB) k_dslash_f2(const float* __restrict__ x, float* __restrict__ y,
+template <class S, int P, int NC, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_dslash_f2(const S* __restrict__ x, S* __restrict__ y,
                                                          const float* __restrict__ U20,
                                                          const float* __restrict__ Acl,
                                                          const int* __restrict__ nbr, int Nrt, int q0, int nq,
@@ -282,28 +303,28 @@ __global__ void __launch_bounds__(128, MINB) k_dslash_f2(const float* __restrict
       nb[d * 4 + mu] = __ldg(nbr + s * 8 + d * 4 + mu);
 #endif
       const size_t n = (size_t)(nb[d * 4 + mu] & 0x3fffffff);
-      const float* xn = x + n * 24 * N + r0;
+      const S* xn = x + n * 24 * N + r0;
       const float* Ul = U20 + ((d == 0 ? s : n) * 4 + mu) * 20;
       if (d == 0) {
-        if (mu == 0) hop_f2<0, +1, P, NC>(o, xn, Nrt, Ul);
-        if (mu == 1) hop_f2<1, +1, P, NC>(o, xn, Nrt, Ul);
-        if (mu == 2) hop_f2<2, +1, P, NC>(o, xn, Nrt, Ul);
-        if (mu == 3) hop_f2<3, +1, P, NC>(o, xn, Nrt, Ul);
+        if (mu == 0) hop_f2<0, +1, P, NC, S>(o, xn, Nrt, Ul);
+        if (mu == 1) hop_f2<1, +1, P, NC, S>(o, xn, Nrt, Ul);
+        if (mu == 2) hop_f2<2, +1, P, NC, S>(o, xn, Nrt, Ul);
+        if (mu == 3) hop_f2<3, +1, P, NC, S>(o, xn, Nrt, Ul);
       } else {
-        if (mu == 0) hop_f2<0, -1, P, NC>(o, xn, Nrt, Ul);
-        if (mu == 1) hop_f2<1, -1, P, NC>(o, xn, Nrt, Ul);
-        if (mu == 2) hop_f2<2, -1, P, NC>(o, xn, Nrt, Ul);
-        if (mu == 3) hop_f2<3, -1, P, NC>(o, xn, Nrt, Ul);
+        if (mu == 0) hop_f2<0, -1, P, NC, S>(o, xn, Nrt, Ul);
+        if (mu == 1) hop_f2<1, -1, P, NC, S>(o, xn, Nrt, Ul);
+        if (mu == 2) hop_f2<2, -1, P, NC, S>(o, xn, Nrt, Ul);
+        if (mu == 3) hop_f2<3, -1, P, NC, S>(o, xn, Nrt, Ul);
       }
     }
   }
 #pragma unroll
   for (int c = 0; c < 12; ++c) {
-    float* yr = y + ((s * 12 + c) * 2 + 0) * N + r0;
-    float* yi = y + ((s * 12 + c) * 2 + 1) * N + r0;
+    S* yr = y + ((s * 12 + c) * 2 + 0) * N + r0;
+    S* yi = y + ((s * 12 + c) * 2 + 1) * N + r0;
     if constexpr (P == 1) {
-      __stcs(reinterpret_cast<float2*>(yr), o[c][0].re);
-      __stcs(reinterpret_cast<float2*>(yi), o[c][0].im);
+      stp(yr, o[c][0].re);
+      stp(yi, o[c][0].im);
     } else {
       __stcs(reinterpret_cast<float4*>(yr), make_float4(o[c][0].re.x, o[c][0].re.y, o[c][1].re.x, o[c][1].re.y));
       __stcs(reinterpret_cast<float4*>(yi), make_float4(o[c][0].im.x, o[c][0].im.y, o[c][1].im.x, o[c][1].im.y));
@@ -324,24 +345,25 @@ static int stencil_passes(int N, int G) {
   return p;
 }
 
-template <int NC>
-void launch_dslash_f2(mrhs_ctx c, const float* x, float* y, int N) {
+template <class S, int NC>
+void launch_dslash_f2(mrhs_ctx c, const S* x, S* y, int N) {
   const int passes = stencil_passes(N, 2);
   const int nq = N / passes;
   const size_t work = (size_t)c->g.V * (nq / 2);
   for (int p = 0; p < passes; ++p)
-    k_dslash_f2<1, NC, MRHS_DS_MINB><<<grid_for(work, 128), 128, 0, c->stream>>>(x, y, c->U20, c->A32, c->nbr, N, p * nq, nq,
-                                                                       work);
+    k_dslash_f2<S, 1, NC, MRHS_DS_MINB><<<grid_for(work, 128), 128, 0, c->stream>>>(x, y, c->U20, c->A32, c->nbr, N,
+                                                                                  p * nq, nq, work);
 }
 
-void dslash_f2(mrhs_ctx c, const float* x, float* y, int N) {
+template <class S>
+void dslash_f2(mrhs_ctx c, const S* x, S* y, int N) {
   switch (N) {
-    case 8: launch_dslash_f2<8>(c, x, y, N); break;
-    case 16: launch_dslash_f2<16>(c, x, y, N); break;
-    case 20: launch_dslash_f2<20>(c, x, y, N); break;
-    case 24: launch_dslash_f2<24>(c, x, y, N); break;
-    case 32: launch_dslash_f2<32>(c, x, y, N); break;
-    default: launch_dslash_f2<0>(c, x, y, N); break;
+    case 8: launch_dslash_f2<S, 8>(c, x, y, N); break;
+    case 16: launch_dslash_f2<S, 16>(c, x, y, N); break;
+    case 20: launch_dslash_f2<S, 20>(c, x, y, N); break;
+    case 24: launch_dslash_f2<S, 24>(c, x, y, N); break;
+    case 32: launch_dslash_f2<S, 32>(c, x, y, N); break;
+    default: launch_dslash_f2<S, 0>(c, x, y, N); break;
   }
 }
 
@@ -401,10 +423,13 @@ void block_mr_t(mrhs_ctx c, S* x, S* rho, S* q, int N, const int* blist, int nbl
 void dslash(mrhs_ctx c, const void* x, void* y, const void* b, int nrhs, int dtype, int mode, int colour) {
   MRHS_REQUIRE(c->have_clover, MRHS_ERR_STATE, "operator used before mrhs_build_clover");
   MRHS_REQUIRE(nrhs >= 1, MRHS_ERR_ARG, "nrhs must be >= 1");
-  // FP32, even nrhs: the packed-pair kernel (an odd count takes the generic one)
-  if (dtype == MRHS_F32 && mode == DS_FULL && colour < 0 && c->U20 && nrhs % 2 == 0) {
+  // FP32 arithmetic, even nrhs: the packed-pair kernel for FP32, bf16 and
+  // fp16 storage (an odd count and FP64 take the generic one)
+  if (dtype != MRHS_F64 && mode == DS_FULL && colour < 0 && c->U20 && nrhs % 2 == 0) {
     Prof pr(c, "dslash_full");
-    dslash_f2(c, (const float*)x, (float*)y, nrhs);
+    if (dtype == MRHS_F32) dslash_f2(c, (const float*)x, (float*)y, nrhs);
+    else if (dtype == MRHS_BF16) dslash_f2(c, (const __nv_bfloat16*)x, (__nv_bfloat16*)y, nrhs);
+    else dslash_f2(c, (const __half*)x, (__half*)y, nrhs);
     MRHS_LAUNCH_CHECK("dslash_f2");
     return;
   }

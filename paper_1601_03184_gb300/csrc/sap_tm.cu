@@ -764,7 +764,7 @@ void sap_tm(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int n_swee
   for (int sw = 0; sw < n_sweeps; ++sw)
     for (int col = 0; col < 2; ++col) {
       const int* blist = c->blocks_col + (col ? c->ncol[0] : 0);
-      Prof pr(c, "sap_tm");
+      Prof pr(c, G == 4 ? "sap_tm" : "sap_tm2");
       MRHS_DISPATCH(bdtype, SB, {
         auto kern = G == 4 ? k_sap_tm<SB> : k_sap_tm2<SB>;
         MRHS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

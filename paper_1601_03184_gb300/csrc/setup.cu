@@ -1,6 +1,7 @@
 // The setup phase (Sec. 2 and Algorithm 2 of the paper with block length
 // N_b = ntv: the V-cycle is applied to all test vectors at once) and the
 // two-level FGMRES solve that measures the quality of a setup.
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <vector>
@@ -14,6 +15,39 @@ void prolong_typed(mrhs_ctx c, const void* uc, int dc, void* u, int du, int N);
 
 namespace {
 
+// Block length of the setup phases: N_b of Alg. 2 (0 or >= ntv: all test
+// vectors at once, the default).
+int block_length(mrhs_ctx c) { return c->block_len > 0 && c->block_len < c->ntv ? c->block_len : c->ntv; }
+
+// The initial phase on the test vectors k0 .. k0+nb-1 (all of them when
+// nb = ntv): x = SAP^n_sweeps(b = v, x0 = 0) (init_mode 0) or n_sweeps times
+// v <- SAP(b = v, x0 = 0) (init_mode 1); the normalised x replaces v.
+void init_block(mrhs_ctx c, int k0, int nb, int init_mode, int n_sweeps, int n_mr) {
+  const int N = c->ntv;
+  const int wd = c->work_dtype;
+  const size_t n = fine_elems(c, nb);
+  void* x = scratch(c, SC_X, n * dtype_size(wd));
+  void* v = c->tv;  // b: the block's test vectors in their storage type
+  if (nb < N) {
+    v = scratch(c, SC_BLOCK, n * dtype_size(c->tv_dtype));
+    gather_cols(c, c->tv, N, v, nb, k0, c->tv_dtype);
+  }
+  if (init_mode == 0) {
+    MRHS_CUDA(cudaMemsetAsync(x, 0, n * dtype_size(wd), c->stream));
+    sap_mixed(c, v, c->tv_dtype, x, nb, wd, n_sweeps, n_mr);
+  } else {
+    for (int it = 0; it < n_sweeps; ++it) {
+      MRHS_CUDA(cudaMemsetAsync(x, 0, n * dtype_size(wd), c->stream));
+      sap_mixed(c, v, c->tv_dtype, x, nb, wd, 1, n_mr);
+      if (it + 1 < n_sweeps) convert(c, x, wd, v, c->tv_dtype, n);
+    }
+  }
+  normalise_rhs(c, x, (size_t)c->g.V * 12, nb, wd);
+  const float scale = (float)(c->tv_dtype == MRHS_F16 ? std::sqrt(12.0 * c->g.V) : 1.0);
+  if (nb < N) scatter_cols(c, x, wd, nb, c->tv, c->tv_dtype, N, k0, scale);
+  else convert_scaled(c, x, wd, c->tv, c->tv_dtype, n, scale);
+}
+
 void setup_init(mrhs_ctx c, const void* tv0, int dtype, int init_mode, int n_sweeps, int n_mr) {
   MRHS_REQUIRE(c->have_clover, MRHS_ERR_STATE, "mrhs_setup_init before mrhs_build_clover");
   MRHS_REQUIRE(init_mode == 0 || init_mode == 1, MRHS_ERR_ARG, "init_mode must be 0 or 1");
@@ -24,20 +58,11 @@ void setup_init(mrhs_ctx c, const void* tv0, int dtype, int init_mode, int n_swe
   convert(c, tv0, dtype, c->tv, c->tv_dtype, n);
   c->have_tv = true;
   c->have_P = c->have_Dc = false;
-  void* x = scratch(c, SC_X, n * dtype_size(c->work_dtype));
-  if (init_mode == 0) {
-    MRHS_CUDA(cudaMemsetAsync(x, 0, n * dtype_size(c->work_dtype), c->stream));
-    sap_mixed(c, c->tv, c->tv_dtype, x, N, c->work_dtype, n_sweeps, n_mr);
-  } else {
-    for (int it = 0; it < n_sweeps; ++it) {
-      MRHS_CUDA(cudaMemsetAsync(x, 0, n * dtype_size(c->work_dtype), c->stream));
-      sap_mixed(c, c->tv, c->tv_dtype, x, N, c->work_dtype, 1, n_mr);
-      if (it + 1 < n_sweeps) convert(c, x, c->work_dtype, c->tv, c->tv_dtype, n);
-    }
-  }
-  normalise_rhs(c, x, (size_t)c->g.V * 12, N, c->work_dtype);
+  // blocks of N_b test vectors in order; the last one holds the remainder
+  // when N_b does not divide ntv (Alg. 2 and its remainder rule)
+  const int nb = block_length(c);
+  for (int k0 = 0; k0 < N; k0 += nb) init_block(c, k0, std::min(nb, N - k0), init_mode, n_sweeps, n_mr);
   c->tv_scale = c->tv_dtype == MRHS_F16 ? std::sqrt(12.0 * c->g.V) : 1.0;
-  convert_scaled(c, x, c->work_dtype, c->tv, c->tv_dtype, n, (float)c->tv_scale);
   build_P(c);
   build_Dc(c);
 }
@@ -76,23 +101,39 @@ void setup_refine(mrhs_ctx c, int n_iter, int n_sweeps, int n_mr, double ctol, i
   MRHS_REQUIRE(n_iter >= 0 && n_sweeps >= 0 && n_mr >= 0, MRHS_ERR_ARG, "bad refinement parameters");
   const int N = c->ntv;
   const int wd = c->work_dtype;
-  const size_t n = fine_elems(c, N);
-  const size_t nce = coarse_elems(c, N);
+  const int nb = block_length(c);
+  const size_t n = fine_elems(c, nb);
+  const size_t nce = coarse_elems(c, nb);
   void* x = scratch(c, SC_X, n * dtype_size(wd));
   char* cbuf = (char*)scratch(c, SC_COARSE, 2 * nce * dtype_size(wd));
   void* vc = cbuf;
   void* uc = cbuf + nce * dtype_size(wd);
+  void* vb = nb < N ? scratch(c, SC_BLOCK, n * dtype_size(c->tv_dtype)) : c->tv;
+  const float scale = (float)(c->tv_dtype == MRHS_F16 ? std::sqrt(12.0 * c->g.V) : 1.0);
+  std::vector<int> its;
   for (int i = 0; i < n_iter; ++i) {
-    // coarse-grid correction for all test vectors at once
-    restrict_typed(c, c->tv, c->tv_dtype, vc, wd, N);
-    coarse_solve(c, vc, uc, N, wd, ctol, crestart, cmaxit, coarse_iters ? coarse_iters + (size_t)i * N : nullptr);
-    prolong_typed(c, uc, wd, x, wd, N);
-    // smoother with the coarse-grid result as starting guess
-    sap_mixed(c, c->tv, c->tv_dtype, x, N, wd, n_sweeps, n_mr);
-    // replace the test vectors by the result, then rebuild R = P^dag and D_c
-    normalise_rhs(c, x, (size_t)c->g.V * 12, N, wd);
-    c->tv_scale = c->tv_dtype == MRHS_F16 ? std::sqrt(12.0 * c->g.V) : 1.0;
-    convert_scaled(c, x, wd, c->tv, c->tv_dtype, n, (float)c->tv_scale);
+    // the V-cycle on blocks of N_b test vectors in order (Alg. 2; N_b = ntv:
+    // all at once; the last block holds the remainder); R, P and D_c stay
+    // fixed until every vector has been replaced (Alg. 1 and 2 alike)
+    for (int k0 = 0; k0 < N; k0 += nb) {
+      const int m = std::min(nb, N - k0);
+      if (m < N) gather_cols(c, c->tv, N, vb, m, k0, c->tv_dtype);
+      // coarse-grid correction
+      restrict_typed(c, vb, c->tv_dtype, vc, wd, m);
+      its.assign(m, 0);
+      coarse_solve(c, vc, uc, m, wd, ctol, crestart, cmaxit, coarse_iters ? its.data() : nullptr);
+      if (coarse_iters)
+        for (int j = 0; j < m; ++j) coarse_iters[(size_t)i * N + k0 + j] = its[j];
+      prolong_typed(c, uc, wd, x, wd, m);
+      // smoother with the coarse-grid result as starting guess
+      sap_mixed(c, vb, c->tv_dtype, x, m, wd, n_sweeps, n_mr);
+      // replace the block's test vectors by the result
+      normalise_rhs(c, x, (size_t)c->g.V * 12, m, wd);
+      if (m < N) scatter_cols(c, x, wd, m, c->tv, c->tv_dtype, N, k0, scale);
+      else convert_scaled(c, x, wd, c->tv, c->tv_dtype, n, scale);
+    }
+    c->tv_scale = scale;
+    // rebuild R = P^dag and D_c from the new test vectors
     build_P(c);
     build_Dc(c);
   }
@@ -262,6 +303,27 @@ int mrhs_setup_init_learned(mrhs_ctx c, const void* tv0, int dtype, int n_sweeps
     MRHS_REQUIRE(c && tv0, MRHS_ERR_ARG, "null argument");
     require_dev(c, tv0, "mrhs_setup_init_learned tv0");
     setup_init_learned(c, tv0, dtype, n_sweeps, n_mr);
+  });
+}
+
+int mrhs_setup_update(mrhs_ctx c, int n_iter, int n_sweeps, int n_mr, double coarse_tol, int coarse_restart,
+                      int coarse_maxit, int* coarse_iters) {
+  return guarded(c, [&] {
+    MRHS_REQUIRE(c, MRHS_ERR_ARG, "null context");
+    MRHS_REQUIRE(c->have_P && c->have_tv, MRHS_ERR_STATE, "mrhs_setup_update before a setup");
+    MRHS_REQUIRE(c->have_clover, MRHS_ERR_STATE, "mrhs_setup_update before mrhs_build_clover of the new field");
+    // the coarse operator of the kept P with the new links and clover term,
+    // then refinement from the kept test vectors
+    build_Dc(c);
+    setup_refine(c, n_iter, n_sweeps, n_mr, coarse_tol, coarse_restart, coarse_maxit, coarse_iters);
+  });
+}
+
+int mrhs_set_block_length(mrhs_ctx c, int nb) {
+  return guarded(c, [&] {
+    MRHS_REQUIRE(c, MRHS_ERR_ARG, "null context");
+    MRHS_REQUIRE(nb >= 0, MRHS_ERR_ARG, "block length must be >= 0");
+    c->block_len = nb;
   });
 }
 

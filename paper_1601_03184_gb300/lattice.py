@@ -12,7 +12,7 @@ from . import (MRHS_F32, MRHS_F64, MRHS_PREC_FP64, mrhs_apply_D, mrhs_apply_D_bl
                mrhs_set_dc_engine,
                mrhs_field_bytes, mrhs_get_clover, mrhs_get_Dc, mrhs_get_P, mrhs_get_tables, mrhs_get_tv,
                mrhs_info, mrhs_load_setup, mrhs_pack, mrhs_pack_coarse, mrhs_prolong, mrhs_restrict, mrhs_sap,
-               mrhs_save_setup, mrhs_set_gauge,
+               mrhs_save_setup, mrhs_set_block_length, mrhs_set_gauge, mrhs_setup_update,
                mrhs_set_tv, mrhs_setup_init, mrhs_setup_refine, mrhs_solve_fgmres, mrhs_sync, mrhs_unpack,
                mrhs_unpack_coarse)
 
@@ -128,6 +128,17 @@ class Lattice:
 
     def setup_init(self, tv0, dtype, init_mode=0, n_sweeps=3, n_mr=4):
         mrhs_setup_init(self.ctx, tv0, dtype, init_mode, n_sweeps, n_mr)
+
+    def setup_update(self, n_iter, n_sweeps=4, n_mr=4, coarse_tol=0.05, coarse_restart=20, coarse_maxit=200):
+        """after set_gauge + build_clover of a changed field: D_c from the kept P,
+        then n_iter refinement iterations from the kept test vectors"""
+        its = mrhs_setup_update(self.ctx, n_iter, n_sweeps, n_mr, coarse_tol, coarse_restart, coarse_maxit,
+                                ntv=self.ntv)
+        return its[:n_iter]
+
+    def set_block_length(self, nb):
+        """N_b of Algorithm 2 for the setup phases (0: all test vectors at once)"""
+        mrhs_set_block_length(self.ctx, nb)
 
     def setup_refine(self, n_iter, n_sweeps=4, n_mr=4, coarse_tol=0.05, coarse_restart=20, coarse_maxit=200):
         its = mrhs_setup_refine(self.ctx, n_iter, n_sweeps, n_mr, coarse_tol, coarse_restart, coarse_maxit,

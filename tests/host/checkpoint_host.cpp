@@ -6,6 +6,7 @@
 // file logic: header checks, chunked copies, checksum, .part handling and
 // every refusal. Usage: checkpoint_host <scratch directory>; exit status 0
 // when every check passes.
+#include <cstddef>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -127,6 +128,17 @@ void write_all(const std::string& p, const unsigned char* d, size_t n) {
   std::fclose(f);
 }
 
+// the file header as checkpoint.cu writes it (for offsets of its fields)
+struct HeaderView {
+  char magic[8];
+  int version;
+  int L[4], a[4];
+  int ntv, prec, tv_dtype, work_dtype;
+  unsigned long long order_hash;
+  double tv_scale;
+  unsigned long long tv_bytes, P_bytes, Dc_bytes;
+};
+
 bool same_setup(mrhs_ctx a, mrhs_ctx b) {
   return std::memcmp(a->tv, b->tv, tv_size(a)) == 0 && std::memcmp(a->P, b->P, tv_size(a)) == 0 &&
          std::memcmp(a->Dc, b->Dc, dc_size(a)) == 0 && a->tv_scale == b->tv_scale;
@@ -170,6 +182,20 @@ void run_case(const std::string& dir, const int L[4], const int a[4], int ntv, i
   mrhs_ctx d2 = make_ctx(L, a, ntv, prec);
   CHECK(mrhs_load_setup(d2, damaged.c_str()) == MRHS_ERR_ARG);
   CHECK(!d2->have_tv && !d2->have_P && !d2->have_Dc);
+  // a damaged header field that the load does not compare with the context
+  // (the fp16 scale, still finite and positive): checksum mismatch
+  {
+    std::vector<unsigned char> hb(data);
+    const size_t off = offsetof(HeaderView, tv_scale);
+    double sc;
+    std::memcpy(&sc, hb.data() + off, sizeof sc);
+    sc *= 1.5;
+    std::memcpy(hb.data() + off, &sc, sizeof sc);
+    const std::string hdr = dir + "/header.bin";
+    write_all(hdr, hb.data(), hb.size());
+    CHECK(mrhs_load_setup(d2, hdr.c_str()) == MRHS_ERR_ARG);
+    CHECK(!d2->have_tv && !d2->have_P && !d2->have_Dc);
+  }
   // truncated, one byte short
   const std::string shortf = dir + "/short.bin";
   write_all(shortf, data.data(), data.size() - 1);

@@ -25,9 +25,10 @@ import sys
 import numpy as np
 import pytest
 
+import oracle
 import paper_1601_03184_gb300 as pkg
 from paper_1601_03184_gb300 import MRHS_F32, MRHS_PREC_FP32, Lattice, inputs
-from lattice_helpers import device_site, lex, sap_sweep_on_domain, stencil_at_site
+from lattice_helpers import cutout, device_site, lex, sap_sweep_on_domain, stencil_at_site
 
 sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 import bench  # noqa: E402  (the benchmark's workload definition)
@@ -194,4 +195,55 @@ def test_gram_schmidt_and_coarse_operator_full_size(full):
     torch.cuda.synchronize()
     assert float(torch.linalg.vector_norm((yc - vc).double()) / torch.linalg.vector_norm(vc.double())) < 1e-4
     del u, du
+    pkg.mrhs_trim(lat.ctx)
+
+
+def test_coarse_operator_full_size_against_oracle_cutouts(full):
+    """The nine D_c blocks of sampled aggregates at full size against the
+    oracle. A block of aggregate A involves only P on A and on its neighbour,
+    the links between them and the clover term on A, and P on an aggregate is
+    the thin-QR factor of the test vectors there: so the oracle's FP64
+    Gram-Schmidt and coarse operator on the 12^4 cut-out of the fields around
+    A (3^4 aggregates, A in the middle) give A's blocks exactly. The GPU's
+    blocks are read column by column from the coarse stencil: x_c = e_j on
+    the neighbour aggregate B and zero elsewhere gives column j of
+    D_c[A][k] in y_c(A) (2 N_tv = 64 right-hand sides, one per column).
+    Sampled aggregates: the middle of the lattice and one at x = 0 (periodic
+    wrap in x); the t boundary is avoided (the cut-out has its own)."""
+    import torch
+
+    lat, psi, U = full["lat"], full["psi"], full["U"]
+    lat.set_tv(psi, MRHS_F32)
+    lat.build_P()
+    lat.build_Dc()
+    _, _, aggnbr = lat.tables()
+    nb = [d // a for d, a in zip(DIMS, AGG)]
+    nc = 2 * N
+    ncb = pkg.mrhs_field_bytes(lat.ctx, nc, MRHS_F32, 1) // 4
+    xc = torch.zeros(ncb, device="cuda", dtype=torch.float32)
+    yc = torch.empty_like(xc)
+    xv = xc.view(NAGG, nc, 2, nc)
+    yv = yc.view(NAGG, nc, 2, nc)
+    eye = torch.arange(nc, device="cuda")
+    for b in [(nb[0] // 2, nb[1] // 2, nb[2] // 2, nb[3] // 2), (0, nb[1] - 1, 3, 5)]:
+        A_ = int(lex(np.asarray(b), nb))
+        gpu = np.zeros((9, nc, nc), np.complex128)
+        for k in range(9):
+            B = A_ if k == 0 else int(aggnbr[A_, k - 1])
+            xc.zero_()
+            xv[B, eye, 0, eye] = 1.0
+            lat.apply_Dc(xc, yc, nc, MRHS_F32)
+            blk = yv[A_].double().cpu().numpy()  # [i][re/im][column r]
+            gpu[k] = blk[:, 0, :] + 1j * blk[:, 1, :]
+        origin = np.asarray(b) * np.asarray(AGG)
+        glob, wrapped = cutout(DIMS, origin - np.asarray(AGG), 3 * AGG[0])
+        assert not wrapped.any()
+        d12 = (3 * AGG[0],) * 4
+        Uc = U[glob]
+        Ac = oracle.clover(d12, Uc, M0, CSW)
+        Pc = oracle.gram_schmidt(d12, AGG, gather(psi, glob))
+        Dref = oracle.coarse_op(d12, AGG, Uc, Ac, Pc)[int(lex(np.array([1, 1, 1, 1]), (3, 3, 3, 3)))]
+        for k in range(9):
+            assert rel(gpu[k], Dref[k]) < 1e-5, (b, k, rel(gpu[k], Dref[k]))
+    del xc, yc
     pkg.mrhs_trim(lat.ctx)

@@ -10,7 +10,8 @@ import numpy as np
 import pytest
 
 import oracle
-from paper_1601_03184_gb300 import (MRHS_ERR_SHAPE, MRHS_F64, MRHS_PREC_FP64, Lattice, MrhsError,
+from paper_1601_03184_gb300 import (MRHS_ERR_SHAPE, MRHS_F32, MRHS_F64, MRHS_PREC_FP32, MRHS_PREC_FP64, Lattice,
+                                    MrhsError,
                                     mrhs_coarse_solve, mrhs_coarse_solve_noalloc, inputs)
 
 pytestmark = pytest.mark.gpu
@@ -67,3 +68,30 @@ def test_noalloc_rejects_problems_beyond_its_workspace(lat):
         mrhs_coarse_solve_noalloc(lat.ctx, bcd, xcd, nrhs, MRHS_F64, 0.05, 64, 10)
     assert e.value.status == MRHS_ERR_SHAPE
     assert "64" in str(e.value) or "bytes" in str(e.value)
+
+
+def test_noalloc_fp32_tensor_core_path_is_bit_identical():
+    """FP32 context with 16 right-hand sides and 2 N_tv = 16: the coarse
+    stencil inside both solves runs on the tensor cores, and the four-wide
+    reductions and updates read the Krylov basis from the library's fixed
+    array (16-byte aligned rows). The two entry points run the same kernels
+    on the same data, so iteration counts and x agree bit for bit."""
+    dims, agg, ntv, nrhs = (8, 8, 8, 8), (4, 4, 4, 4), 8, 16
+    U = inputs.gauge_field(dims, 0.4, 1301)
+    lat32 = Lattice(dims, agg, ntv, MRHS_PREC_FP32)
+    lat32.set_gauge(U)
+    lat32.build_clover(-0.1, 1.2)
+    lat32.set_tv(lat32.to_device(inputs.test_vectors(ntv, dims, 2301).astype(np.complex64), MRHS_F32), MRHS_F32)
+    lat32.build_P()
+    lat32.build_Dc()
+    for seed in (4101, 4102):
+        bc = inputs.gaussian_field((nrhs, lat32.nagg, 2 * ntv), seed).astype(np.complex64)
+        bcd = lat32.to_device(bc, MRHS_F32, coarse=True)
+        ref = lat32.field(nrhs, MRHS_F32, coarse=True)
+        got = lat32.field(nrhs, MRHS_F32, coarse=True)
+        got.fill_(255)
+        its_ref = mrhs_coarse_solve(lat32.ctx, bcd, ref, nrhs, MRHS_F32, 1e-5, 8, 60)
+        its = mrhs_coarse_solve_noalloc(lat32.ctx, bcd, got, nrhs, MRHS_F32, 1e-5, 8, 60)
+        assert list(its) == list(its_ref)
+        assert bool((ref == got).all())
+    lat32.close()
