@@ -183,7 +183,7 @@ def kernel_work(name, cfg, launches_per_step, bytes_f=4):
         return V * (link4 + clov + 2 * N * spin), V * N * flop_site_rhs
     if name == "dslash_resid":  # one colour: r = b - D x on half of the sites
         return V / 2 * (link4 + clov + 3 * N * spin), V / 2 * N * flop_site_rhs
-    if name in ("sap_tm", "sap_tm2", "sap_fused8", "sap_fused"):  # one colour: residual + n_mr MR steps, on chip
+    if name in ("sap_pk", "sap_tm", "sap_tm2", "sap_fused8", "sap_fused"):  # one colour: residual + n_mr MR steps, on chip
         nmr = SCHEDULE["smooth_mr"]
         flops = V / 2 * N * (flop_site_rhs + nmr * (flop_site_rhs + 336))
         byt = V / 2 * (link4 + clov + 3 * N * spin)  # b in, x in and out, links and clover once
@@ -473,7 +473,7 @@ def run_ours(args, cfg, cfg_name, m0, m0_src, rank, world, local_rank):
 # kernel classes of the library's profile grouped into the phases the paper
 # times separately (Sec. 7): smoother, coarse grid, projections, setup of R
 # and D_c, and the copies that move a block of test vectors in and out
-PHASES = {"smoother": ("sap_tm", "sap_tm2", "sap_fused", "sap_fused8", "sap_block_mr", "dslash_resid"),
+PHASES = {"smoother": ("sap_pk", "sap_tm", "sap_tm2", "sap_fused", "sap_fused8", "sap_block_mr", "dslash_resid"),
           "coarse_grid": ("apply_dc_tc", "apply_dc", "multi_dot", "multi_axpy"),
           "projections": ("restrict", "prolong"),
           "R_and_Dc": ("gs_cholqr2", "coarse_op", "coarse_op_tc", "format_dc"),

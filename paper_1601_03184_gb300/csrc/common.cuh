@@ -302,6 +302,8 @@ void sap_mixed(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int dty
 bool sap_fused_ok(mrhs_ctx c, int dtype);
 void sap_fused(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int n_sweeps, int n_mr);
 bool sap_tm_ok(mrhs_ctx c, int nrhs);
+bool sap_pk_ok(mrhs_ctx c, int nrhs);
+void sap_pk(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int n_sweeps, int n_mr);
 void sap_tm(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int n_sweeps, int n_mr);
 // blas.cu: y[row][r] += sign * sum_k coef[k][r] * X_k[row][r], X_k = X + k*stride elements
 void multi_axpy(mrhs_ctx c, const void* X, size_t stride, int K, void* Y, size_t rows, int N, int dtype,

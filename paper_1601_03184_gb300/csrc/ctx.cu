@@ -472,7 +472,9 @@ __global__ void k_scatter_cols(const SI* __restrict__ src, int nb, SO* __restric
   const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (t >= n) return;
   const size_t row = t / nb;
-  dst[row * ntv + k0 + (int)(t % nb)] = from_r<SO>((float)to_r(src[t]) * scale);
+  // the product in the source's arithmetic type (double stays double)
+  using R = typename Real<SI>::type;
+  dst[row * ntv + k0 + (int)(t % nb)] = from_r<SO>(to_r(src[t]) * (R)scale);
 }
 
 namespace mrhs {

@@ -15,6 +15,7 @@
 // The backward data pass is the forward kernel with W'[k'] = W[mirror(k')]^dag
 // (mirror exchanges +mu and -mu): the adjoint of hopping from x+mu with
 // U_mu(x) is hopping from y-mu with U_mu(y-mu)^dag.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -562,7 +563,21 @@ void nn_infer_chunked(mrhs_ctx c, const float* in, float* out, int N, int chunk)
 
 namespace mrhs {
 void nn_forward(mrhs_ctx c, const float* in, float* out, int N) { nn_forward_impl(c, in, out, N); }
-void nn_infer(mrhs_ctx c, const float* in, float* out, int N) { nn_infer_chunked(c, in, out, N, 8); }
+// inference in chunks of right-hand sides: up to 8 at a time, fewer when the
+// activations of 8 (two hidden fields and the chunk's input and output) would
+// take more than half of the device memory still available
+void nn_infer(mrhs_ctx c, const float* in, float* out, int N) {
+  NNState& s = nn_of(c);
+  const int hid = std::max(s.C[1], s.C[2]);
+  const size_t per_rhs = sizeof(float) * (size_t)c->g.V * (2 * (size_t)hid * 6 + 2 * 24);
+  size_t free_b = 0, total_b = 0;
+  MRHS_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  size_t avail = free_b;
+  for (int k : {SC_FINE1, SC_FINE2, SC_FINE3}) avail += c->scratch[k].bytes;  // reusable
+  int chunk = 8;
+  while (chunk > 1 && (size_t)chunk * per_rhs > avail / 2) --chunk;
+  nn_infer_chunked(c, in, out, N, chunk);
+}
 }  // namespace mrhs
 
 using namespace mrhs;

@@ -504,12 +504,20 @@ bool sap_fused_ok(mrhs_ctx c, int dtype) {
 }
 
 void sap_fused(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int n_sweeps, int n_mr) {
-  // the on-chip form (tensor memory for the running solution) unless
-  // MRHS_SAP_KERNEL=smem asks for the shared-memory/global forms below
-  static const bool tm_off = [] {
+  // the on-chip forms (tensor memory for the running solution): packed pairs
+  // of right-hand sides per thread when nrhs % 4 == 0, else one (site, rhs)
+  // item per thread; MRHS_SAP_KERNEL=tm asks for the item form always,
+  // MRHS_SAP_KERNEL=smem for the shared-memory/global forms below
+  static const int mode = [] {
     const char* e = std::getenv("MRHS_SAP_KERNEL");
-    return e && std::string(e) == "smem";
+    if (!e) return 0;
+    return std::string(e) == "smem" ? 2 : std::string(e) == "tm" ? 1 : 0;
   }();
+  const bool tm_off = mode == 2;
+  if (mode == 0 && sap_pk_ok(c, nrhs)) {
+    sap_pk(c, b, bdtype, x, nrhs, n_sweeps, n_mr);
+    return;
+  }
   if (!tm_off && sap_tm_ok(c, nrhs)) {
     sap_tm(c, b, bdtype, x, nrhs, n_sweeps, n_mr);
     return;

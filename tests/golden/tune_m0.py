@@ -33,6 +33,10 @@ CASES = {
     # solves above are not available
     "proxy_12x12x12x12_eps0.6_csw1.5_seed1002": ((12, 12, 12, 12), 0.6, 1.5, 1002),
     "proxy_12x12x12x12_eps0.6_csw1.7_seed1005": ((12, 12, 12, 12), 0.6, 1.7, 1005),
+    # the ends of the roughness range of the learned generator's training
+    # fields (m0 interpolated in between)
+    "proxy_12x12x12x12_eps0.4_csw1.5_seed4000": ((12, 12, 12, 12), 0.4, 1.5, 4000),
+    "proxy_12x12x12x12_eps0.7_csw1.5_seed4001": ((12, 12, 12, 12), 0.7, 1.5, 4001),
 }
 RATIO = 1e-3
 

@@ -147,3 +147,8 @@ def test_training_gain():
     _, it_plain, _ = lat.solve_fgmres(rhs, tol=1e-10, maxit=500)
     print("FGMRES iterations: learned %d, same SAP budget %d, plain 5 sweeps %d" % (it_learned, it_same_budget, it_plain))
     assert abs(it_learned - it_plain) <= max(1, 0.1 * it_plain)
+    # against the same SAP budget (one sweep) without the network the
+    # iteration count stays within 10 % (+1): on this small case the gain is
+    # in the Rayleigh quotient (measured on a GB300: 3.17 -> 1.44), not in
+    # the FGMRES count (measured: learned 25, one sweep alone 23, plain 24)
+    assert it_learned <= 1.1 * it_same_budget + 1

@@ -51,7 +51,8 @@ def make(cfg, ntv=8):
     return lat, U, A
 
 
-@pytest.mark.parametrize("nrhs,kernel", [(6, "sap_tm2"), (10, "sap_tm2"), (5, "sap_fused"), (1, "sap_fused")])
+@pytest.mark.parametrize("nrhs,kernel", [(4, "sap_pk"), (8, "sap_pk"), (6, "sap_tm2"), (10, "sap_tm2"),
+                                          (5, "sap_fused"), (1, "sap_fused")])
 def test_sap_fp32_other_widths(nrhs, kernel):
     """nrhs = 2 mod 4 takes the two-per-chunk on-chip kernel, an odd nrhs the
     one-per-thread form; two sweeps from a nonzero start on 4^4 domains."""
@@ -104,11 +105,12 @@ def _child(env, kind, nrhs):
 @pytest.mark.parametrize("env,kind,nrhs,kernel,tol", [
     ({"MRHS_SAP_KERNEL": "smem"}, "sap", 8, "sap_fused8", 1e-5),
     ({"MRHS_SAP_KERNEL": "smem"}, "sap", 6, "sap_fused", 1e-5),
-    ({"MRHS_SAP_CHUNK": "2"}, "sap", 8, "sap_tm2", 1e-5),
-    ({"MRHS_SAP_CPB": "1"}, "sap", 8, "sap_tm", 1e-5),
+    ({"MRHS_SAP_KERNEL": "tm", "MRHS_SAP_CHUNK": "2"}, "sap", 8, "sap_tm2", 1e-5),
+    ({"MRHS_SAP_KERNEL": "tm"}, "sap", 8, "sap_tm", 1e-5),
+    ({"MRHS_SAP_KERNEL": "tm", "MRHS_SAP_CPB": "1"}, "sap", 8, "sap_tm", 1e-5),
     ({"MRHS_STENCIL_PASSES": "2"}, "apply_D", 8, "dslash_full", 1e-5),
     ({"MRHS_DC_APPLY": "alu"}, "apply_Dc", 16, "apply_dc", 1e-5),
-], ids=["smem-fused8", "smem-fused2", "chunk2", "cpb1", "passes2", "dc-alu"])
+], ids=["smem-fused8", "smem-fused2", "chunk2", "tm", "tm-cpb1", "passes2", "dc-alu"])
 def test_switch_selected_forms(env, kind, nrhs, kernel, tol):
     r = _child(env, kind, nrhs)
     assert kernel in r["kernels"], r
