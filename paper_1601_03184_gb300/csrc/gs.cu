@@ -312,6 +312,55 @@ __device__ __forceinline__ void st4s(double* p, const double v[4]) {
   *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
 }
 
+// Cholesky factorisation G = L L^dag of the Hermitian positive definite
+// N x N matrix G (lower triangle, in place, type T) and the upper triangular
+// M = L^-dag (L^dag M = 1, one column per thread by back substitution), by the
+// threads of the CTA; a pivot at or below rel_pivot times the diagonal dg[k]
+// of the original Gram matrix, or not finite, raises *flag (the vectors are
+// numerically dependent) and is replaced by 1 to finish safely
+template <class T, int N>
+__device__ __forceinline__ void chol_inv(cx<T>* G, cx<T>* M, const double* dg, double rel_pivot, int* flag,
+                                         int tid) {
+  __shared__ T s_rdiag[N];  // 1 / L_kk
+  for (int k = 0; k < N; ++k) {
+    if (tid == 0) {
+      T d = G[k * N + k].re;
+      if (!((double)d > rel_pivot * dg[k]) || !isfinite(d)) {
+        atomicExch(flag, 1);
+        d = 1;
+      }
+      const T l = sqrt(d);
+      G[k * N + k] = mk<T>(l, 0);
+      s_rdiag[k] = (T)1 / l;
+    }
+    __syncthreads();
+    if (tid > k && tid < N) G[tid * N + k] = scale(G[tid * N + k], s_rdiag[k]);
+    __syncthreads();
+    {
+      // thread -> column j = tid % N of rows i = tid / N + (kThreads / N) m
+      const int j = tid % N;
+      if (j > k && tid < N * (kThreads / N)) {
+        const cx<T> gjk = cnj(G[j * N + k]);
+        for (int i = tid / N; i < N; i += kThreads / N)
+          if (i >= j) G[i * N + j] = G[i * N + j] - G[i * N + k] * gjk;
+      }
+    }
+    __syncthreads();
+  }
+  for (int j = tid; j < N; j += kThreads) {
+    for (int i = N - 1; i >= 0; --i) {
+      if (i > j) {
+        M[i * N + j] = mk<T>(0, 0);
+        continue;
+      }
+      cx<T> sacc = i == j ? mk<T>(1, 0) : mk<T>(0, 0);
+      for (int k2 = i + 1; k2 <= j; ++k2) sacc = sacc - cnj(G[k2 * N + i]) * M[k2 * N + j];
+      M[i * N + j] = scale(sacc, s_rdiag[i]);
+    }
+  }
+  __syncthreads();
+}
+
 template <class S, class R, int NC, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB) k_cholqr2_reg(const S* V, S* Q, int Va, int* flag) {
   constexpr int N = NC;
@@ -396,44 +445,24 @@ __global__ void __launch_bounds__(kThreads, MINB) k_cholqr2_reg(const S* V, S* Q
     }
     for (int k = tid; k < N; k += kThreads) dg[k] = G[k * N + k].re;
     __syncthreads();
-    // ---- Cholesky G = L L^dag (lower triangle, in place); thread -> column
-    // j = tid % N of rows i = tid / N + (kThreads / N) m
-    for (int k = 0; k < N; ++k) {
-      if (tid == 0) {
-        double d = G[k * N + k].re;
-        if (!(d > rel_pivot * dg[k]) || !isfinite(d)) {
-          atomicExch(flag, 1);
-          d = 1;
-        }
-        G[k * N + k] = mk(sqrt(d), 0.0);
-      }
-      __syncthreads();
-      if (tid > k && tid < N) G[tid * N + k] = scale(G[tid * N + k], 1.0 / G[k * N + k].re);
-      __syncthreads();
-      {
-        const int j = tid % N;
-        if (j > k && tid < N * (kThreads / N)) {
-          const cx<double> gjk = cnj(G[j * N + k]);
-          for (int i = tid / N; i < N; i += kThreads / N)
-            if (i >= j) G[i * N + j] = G[i * N + j] - G[i * N + k] * gjk;
-        }
-      }
+    // ---- Cholesky G = L L^dag and M = L^-dag in the compute type R: FP64
+    // for FP64 data; FP32 for FP32 and reduced storage, where FP64 runs at a
+    // small fraction of the FP32 rate and the vectors accepted by the pivot
+    // test (pivot above 16 u32 of its diagonal, kappa below ~1/(4 sqrt(u32)))
+    // give a first-pass Q that the second pass brings to FP32 orthogonality
+    cx<R>* Gf;
+    cx<R>* Mc;
+    if constexpr (sizeof(R) == 8) {
+      Gf = reinterpret_cast<cx<R>*>(G);
+      Mc = reinterpret_cast<cx<R>*>(Md);
+    } else {
+      Gf = buf;          // the staging tile is free between the passes over the rows
+      Mc = buf + N * N;
+      for (int w = tid; w < N * N; w += kThreads) Gf[w] = mk<R>((R)G[w].re, (R)G[w].im);
       __syncthreads();
     }
-    // ---- M = L^-dag (upper triangular): L^dag M = 1, column j by back substitution
-    for (int j = tid; j < N; j += kThreads) {
-      for (int i = N - 1; i >= 0; --i) {
-        if (i > j) {
-          Md[i * N + j] = mk(0.0, 0.0);
-          continue;
-        }
-        cx<double> sacc = i == j ? mk(1.0, 0.0) : mk(0.0, 0.0);
-        for (int k2 = i + 1; k2 <= j; ++k2) sacc = sacc - cnj(G[k2 * N + i]) * Md[k2 * N + j];
-        Md[i * N + j] = scale(sacc, 1.0 / G[i * N + i].re);
-      }
-    }
-    __syncthreads();
-    for (int w = tid; w < N * N; w += kThreads) Mr[w] = mk<R>((R)Md[w].re, (R)Md[w].im);
+    chol_inv<R, N>(Gf, Mc, dg, rel_pivot, flag, tid);
+    for (int w = tid; w < N * N; w += kThreads) Mr[w] = Mc[w];
     __syncthreads();
     // ---- Q = X M
     for (int l0 = 0; l0 < L; l0 += kChunk) {

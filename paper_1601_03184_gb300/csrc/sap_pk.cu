@@ -12,7 +12,10 @@
 //                  pair, the domain's halved links [20][Va+1] float4 and the
 //                  domain-local neighbour table [8][Va];
 //   tensor memory  the running solution x_B of the thread's pair
-//                  (48 columns: 12 components x (re_a, re_b, im_a, im_b));
+//                  (48 columns: 12 components x (re_a, re_b, im_a, im_b)) and
+//                  a copy of the clover term of the thread's site (72
+//                  columns), staged once per CTA: the five applications of D
+//                  per chunk read it there instead of from global memory;
 //   registers      q = D_B rho between the reduction for alpha and the
 //                  update.
 // Per colour and chunk: r = b - D x on the domain (neighbours outside it from
@@ -30,12 +33,15 @@ namespace {
 
 constexpr int kPG = 4;        // right-hand sides per chunk (two pairs)
 constexpr int kPCols = 48;    // tensor-memory columns of one thread's x_B
+constexpr int kPClov = 72;    // tensor-memory columns of its site's clover term
+constexpr int kPWarpCols = kPCols + kPClov;
 constexpr int kPMaxT = 512;   // threads for a 256-site domain
 
 struct DomP {
   const float4* sR;  // [12][Va][2]
   const float4* sU;  // [20][Va+1]: float4 k of link mu at row mu*5 + k
   const int* sN;     // [8][Va]: neighbour inside the domain (local) or ~(device site)
+  uint32_t tclov;    // tensor-memory address of the thread's copy of its site's clover term
   int Va, l, p;
   size_t s0;
 };
@@ -133,15 +139,10 @@ __device__ __forceinline__ void apply_pk(const DomP& d, c2 o[12], const float* _
                                          const float* __restrict__ x, const float* __restrict__ U20, int N,
                                          int r0) {
   {
-    const float4* A4 = reinterpret_cast<const float4*>(Acl + (d.s0 + d.l) * 72);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       float q[36];
-#pragma unroll
-      for (int k = 0; k < 9; ++k) {
-        const float4 v = __ldg(A4 + 9 * h + k);
-        q[4 * k] = v.x, q[4 * k + 1] = v.y, q[4 * k + 2] = v.z, q[4 * k + 3] = v.w;
-      }
+      tc::tmem_ld36(d.tclov + 36 * h, q);
       c2 ps[6];
 #pragma unroll
       for (int a = 0; a < 6; ++a) ps[a] = ldR(d, 6 * h + a, d.l);
@@ -250,7 +251,30 @@ __global__ void __launch_bounds__(kPMaxT, 1) k_sap_pk(const SB* __restrict__ b, 
   tc::fence_after_sync();
   // lane quarter of the warp; warps w, w+4, w+8, w+12 share it and take
   // disjoint column ranges of kPCols
-  const uint32_t tm = s_tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * kPCols);
+  const uint32_t tm = s_tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * kPWarpCols);
+  d.tclov = tm + kPCols;
+  {
+    // the clover term of the thread's site -> tensor memory (72 columns)
+    const float4* A4 = reinterpret_cast<const float4*>(Acl + (d.s0 + d.l) * 72);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float f[16];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float4 v = __ldg(A4 + 4 * k + i);
+        f[4 * i] = v.x, f[4 * i + 1] = v.y, f[4 * i + 2] = v.z, f[4 * i + 3] = v.w;
+      }
+      tc::tmem_st16(d.tclov + 16 * k, f);
+    }
+    float f[8];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const float4 v = __ldg(A4 + 16 + i);
+      f[4 * i] = v.x, f[4 * i + 1] = v.y, f[4 * i + 2] = v.z, f[4 * i + 3] = v.w;
+    }
+    tc::tmem_st8(d.tclov + 64, f);
+    tc::tmem_wait_st();
+  }
 
   for (int r0 = (blockIdx.x % cpb) * kPG; r0 < N; r0 += cpb * kPG) {
     // stage x0: one (component c, site l) per unit, the real and imaginary
@@ -400,9 +424,10 @@ void sap_pk(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int n_swee
   const int Va = c->g.Va;
   const int T = sap_pk_threads(Va);
   const size_t smem = sap_pk_smem(Va, T);
-  // x_B: kPCols columns per thread, (T / 128) warps per lane quarter
+  // x_B and the clover copy: kPWarpCols columns per thread, (T / 128) warps
+  // per lane quarter (at most 4 x 120 = 480 of the 512 columns)
   uint32_t cols = 32;
-  while (cols < (uint32_t)(T / 128) * kPCols) cols <<= 1;
+  while (cols < (uint32_t)(T / 128) * kPWarpCols) cols <<= 1;
   const int cpb = nrhs / kPG;  // one chunk per CTA: a domain's CTAs share x and b sectors in L2
   for (int sw = 0; sw < n_sweeps; ++sw)
     for (int col = 0; col < 2; ++col) {
