@@ -53,6 +53,7 @@ class SetupParams(ctypes.Structure):
         ("coarse_tol", ctypes.c_double),
         ("coarse_restart", ctypes.c_int),
         ("coarse_maxit", ctypes.c_int),
+        ("even_odd", ctypes.c_int),
     ]
 
 
@@ -136,6 +137,15 @@ def sap(dims, agg, U, A, b, x0, n_sweeps, n_mr):
     return x
 
 
+def sap_eo(dims, agg, U, A, b, x0, n_sweeps, n_mr):
+    """x <- SAP^n_sweeps(b, x0) with even-odd preconditioned domain solves."""
+    U, A, b = _c(U), _c(A), _c(b)
+    x = _c(x0).copy()
+    nrhs = b.shape[0] if b.ndim == 3 else 1
+    _check(lib().ora_sap_eo(_i4(dims), _i4(agg), _p(U), _p(A), _p(b), _p(x), nrhs, n_sweeps, n_mr), "sap_eo")
+    return x
+
+
 def gram_schmidt(dims, agg, tv):
     tv = _c(tv)
     P = np.zeros_like(tv)
@@ -189,9 +199,9 @@ def coarse_solve(dims, agg, Dc, bc, tol, restart, maxit):
 
 
 def make_params(init_mode=0, n_init_sweeps=3, n_init_mr=4, n_refine=1, n_smooth_sweeps=4,
-                n_smooth_mr=4, coarse_tol=0.05, coarse_restart=20, coarse_maxit=200):
+                n_smooth_mr=4, coarse_tol=0.05, coarse_restart=20, coarse_maxit=200, even_odd=0):
     return SetupParams(init_mode, n_init_sweeps, n_init_mr, n_refine, n_smooth_sweeps, n_smooth_mr,
-                       float(coarse_tol), coarse_restart, coarse_maxit)
+                       float(coarse_tol), coarse_restart, coarse_maxit, int(even_odd))
 
 
 def setup_init(dims, agg, U, A, tv0, params):
@@ -218,7 +228,7 @@ def setup_refine(dims, agg, U, A, tv, P, Dc, params):
 
 
 def fgmres(dims, agg, U, A, P, Dc, b, tol=1e-10, restart=25, maxit=500, coarse_tol=0.05,
-           coarse_restart=20, coarse_maxit=200, n_sweeps=4, n_mr=4):
+           coarse_restart=20, coarse_maxit=200, n_sweeps=4, n_mr=4, even_odd=0):
     """Two-level FGMRES on D x = b. Returns (x, iterations, relative residual estimate)."""
     U, A, P, Dc, b = _c(U), _c(A), _c(P), _c(Dc), _c(b)
     x = np.zeros_like(b)
@@ -227,7 +237,7 @@ def fgmres(dims, agg, U, A, P, Dc, b, tol=1e-10, restart=25, maxit=500, coarse_t
     _check(
         lib().ora_fgmres(_i4(dims), _i4(agg), P.shape[0], _p(U), _p(A), _p(P), _p(Dc), _p(b), _p(x),
                          ctypes.c_double(tol), restart, maxit, ctypes.c_double(coarse_tol), coarse_restart,
-                         coarse_maxit, n_sweeps, n_mr, ctypes.byref(it), ctypes.byref(rr)),
+                         coarse_maxit, n_sweeps, n_mr, int(even_odd), ctypes.byref(it), ctypes.byref(rr)),
         "fgmres",
     )
     return x, it.value, rr.value

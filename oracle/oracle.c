@@ -462,6 +462,219 @@ static void sap_rhs(const geom_t* g, const int* sites, const cplx* U, const cplx
   free(r);
 }
 
+/* ------------------------------------------------------------------ */
+/* even-odd preconditioned domain solves                                 */
+/* ------------------------------------------------------------------ */
+/* On a domain B (Dirichlet), D_B = [[A_EE, H_EO], [H_OE, A_OO]] with E and O
+ * the sites of even and odd parity (x+y+z+t) and H the hopping terms, which
+ * always change the parity. D_B e = r is solved through the Schur complement
+ * on the even sites:
+ *   S = A_EE - H_EO A_OO^-1 H_OE,   S e_E = r_E - H_EO A_OO^-1 r_O,
+ *   e_O = A_OO^-1 (r_O - H_OE e_E),
+ * with n_mr minimal-residual steps on S e_E = rhat from e_E = 0 (the same MR
+ * as the plain smoother, inner products over the even sites). The result is
+ * the exact domain solve in the limit of many steps, as for the plain form. */
+
+/* 12 x 12 inverse by Gauss-Jordan elimination with partial pivoting */
+static int invert12(const cplx* a, cplx* inv) {
+  cplx m[12][24];
+  for (int i = 0; i < 12; ++i)
+    for (int j = 0; j < 24; ++j) m[i][j] = j < 12 ? a[i * 12 + j] : (j - 12 == i ? 1.0 : 0.0);
+  for (int c = 0; c < 12; ++c) {
+    int p = c;
+    for (int i = c + 1; i < 12; ++i)
+      if (cabs(m[i][c]) > cabs(m[p][c])) p = i;
+    if (cabs(m[p][c]) == 0) return -1;
+    if (p != c)
+      for (int j = 0; j < 24; ++j) {
+        cplx t = m[p][j];
+        m[p][j] = m[c][j];
+        m[c][j] = t;
+      }
+    cplx piv = m[c][c];
+    for (int j = 0; j < 24; ++j) m[c][j] /= piv;
+    for (int i = 0; i < 12; ++i) {
+      if (i == c) continue;
+      cplx f = m[i][c];
+      if (f != 0)
+        for (int j = 0; j < 24; ++j) m[i][j] -= f * m[c][j];
+    }
+  }
+  for (int i = 0; i < 12; ++i)
+    for (int j = 0; j < 12; ++j) inv[i * 12 + j] = m[i][j + 12];
+  return 0;
+}
+
+static int site_parity(const geom_t* g, int s) {
+  int x[4];
+  coords_of(g->L, s, x);
+  return (x[0] + x[1] + x[2] + x[3]) & 1;
+}
+
+/* y_s = (H psi)_s: the hopping terms of D at site s with sources in block B */
+static void hop_site(const geom_t* g, const cplx* U, const cplx* psi, cplx* y, int s, int B) {
+  cplx out[12] = {0};
+  for (int mu = 0; mu < 4; ++mu)
+    for (int dir = +1; dir >= -1; dir -= 2) {
+      int flip;
+      int n = neighbour(g, s, mu, dir, &flip);
+      if (aggregate_of(g, n, NULL) != B) continue;
+      su3 u = (dir > 0) ? link_of(U, s, mu) : dag(link_of(U, n, mu));
+      double sgn = flip ? -1.0 : 1.0;
+      cplx up[12];
+      for (int sp = 0; sp < 4; ++sp)
+        for (int ca = 0; ca < 3; ++ca) {
+          cplx c = 0;
+          for (int cb = 0; cb < 3; ++cb) c += u.m[ca][cb] * psi[(size_t)n * 12 + 3 * sp + cb];
+          up[3 * sp + ca] = c;
+        }
+      for (int sp = 0; sp < 4; ++sp)
+        for (int ca = 0; ca < 3; ++ca) {
+          cplx c = up[3 * sp + ca];
+          for (int tp = 0; tp < 4; ++tp) c -= (double)dir * GAMMA[mu][sp][tp] * up[3 * tp + ca];
+          out[3 * sp + ca] -= 0.5 * sgn * c;
+        }
+    }
+  for (int i = 0; i < 12; ++i) y[(size_t)s * 12 + i] = out[i];
+}
+
+/* y_s = M_s v_s for a 12 x 12 matrix per site */
+static void site_mul(const cplx* M, const cplx* v, cplx* y, int s) {
+  cplx out[12];
+  for (int i = 0; i < 12; ++i) {
+    cplx c = 0;
+    for (int j = 0; j < 12; ++j) c += M[(size_t)s * 144 + i * 12 + j] * v[(size_t)s * 12 + j];
+    out[i] = c;
+  }
+  for (int i = 0; i < 12; ++i) y[(size_t)s * 12 + i] = out[i];
+}
+
+/* the SAP sweeps of sap_rhs with every domain solve done on the Schur
+ * complement of its even sites (Ainv: the inverse clover term per site) */
+static void sap_rhs_eo(const geom_t* g, const int* sites, const cplx* U, const cplx* A, const cplx* Ainv,
+                       const cplx* b, cplx* x, int n_sweeps, int n_mr) {
+  size_t n = (size_t)g->V * 12;
+  cplx* r = (cplx*)malloc(sizeof(cplx) * n);
+  /* work vectors on the whole lattice; blocks of one colour touch disjoint
+   * sites, and every hop reads only sites of the other parity */
+  cplx* rho = (cplx*)calloc(n, sizeof(cplx));
+  cplx* u = (cplx*)calloc(n, sizeof(cplx));
+  cplx* q = (cplx*)calloc(n, sizeof(cplx));
+  cplx* e = (cplx*)calloc(n, sizeof(cplx));
+  cplx* t = (cplx*)calloc(n, sizeof(cplx));
+  for (int sweep = 0; sweep < n_sweeps; ++sweep)
+    for (int col = 0; col < 2; ++col) {
+#pragma omp parallel for schedule(static)
+      for (int s = 0; s < g->V; ++s) {
+        apply_D_site(g, U, A, x, r, s, -1);
+        for (int i = 0; i < 12; ++i) r[(size_t)s * 12 + i] = b[(size_t)s * 12 + i] - r[(size_t)s * 12 + i];
+      }
+#pragma omp parallel for schedule(dynamic)
+      for (int B = 0; B < g->nagg; ++B) {
+        if (aggregate_colour(g, B) != col) continue;
+        const int* bs = sites + (size_t)B * g->Va;
+        /* u_O = A_OO^-1 r_O; rho_E = rhat = r_E - H_EO u_O; e_E = 0 */
+        for (int k = 0; k < g->Va; ++k)
+          if (site_parity(g, bs[k]) == 1) site_mul(Ainv, r, u, bs[k]);
+        for (int k = 0; k < g->Va; ++k) {
+          const int s = bs[k];
+          if (site_parity(g, s) != 0) continue;
+          hop_site(g, U, u, t, s, B);
+          for (int i = 0; i < 12; ++i) {
+            rho[(size_t)s * 12 + i] = r[(size_t)s * 12 + i] - t[(size_t)s * 12 + i];
+            e[(size_t)s * 12 + i] = 0;
+          }
+        }
+        for (int it = 0; it < n_mr; ++it) {
+          /* q_E = S rho_E = A_EE rho_E - H_EO A_OO^-1 H_OE rho_E */
+          for (int k = 0; k < g->Va; ++k)
+            if (site_parity(g, bs[k]) == 1) {
+              hop_site(g, U, rho, t, bs[k], B);
+              site_mul(Ainv, t, u, bs[k]);
+            }
+          cplx qr = 0;
+          double qq = 0;
+          for (int k = 0; k < g->Va; ++k) {
+            const int s = bs[k];
+            if (site_parity(g, s) != 0) continue;
+            site_mul(A, rho, q, s);
+            hop_site(g, U, u, t, s, B);
+            for (int i = 0; i < 12; ++i) q[(size_t)s * 12 + i] -= t[(size_t)s * 12 + i];
+            qr += dotc(q + (size_t)s * 12, rho + (size_t)s * 12, 12);
+            qq += norm2(q + (size_t)s * 12, 12);
+          }
+          cplx alpha = (qq > 0) ? qr / qq : 0;
+          for (int k = 0; k < g->Va; ++k) {
+            const int s = bs[k];
+            if (site_parity(g, s) != 0) continue;
+            for (int i = 0; i < 12; ++i) {
+              e[(size_t)s * 12 + i] += alpha * rho[(size_t)s * 12 + i];
+              rho[(size_t)s * 12 + i] -= alpha * q[(size_t)s * 12 + i];
+            }
+          }
+        }
+        /* e_O = A_OO^-1 (r_O - H_OE e_E); x_B += e */
+        for (int k = 0; k < g->Va; ++k) {
+          const int s = bs[k];
+          if (site_parity(g, s) != 1) continue;
+          hop_site(g, U, e, t, s, B);
+          for (int i = 0; i < 12; ++i) t[(size_t)s * 12 + i] = r[(size_t)s * 12 + i] - t[(size_t)s * 12 + i];
+          site_mul(Ainv, t, e, s);
+        }
+        for (int k = 0; k < g->Va; ++k)
+          for (int i = 0; i < 12; ++i) x[(size_t)bs[k] * 12 + i] += e[(size_t)bs[k] * 12 + i];
+      }
+    }
+  free(rho);
+  free(u);
+  free(q);
+  free(e);
+  free(t);
+  free(r);
+}
+
+/* the inverse clover term of every site (NULL if a block is singular) */
+static cplx* clover_inverses(const geom_t* g, const cplx* A) {
+  cplx* Ainv = (cplx*)malloc(sizeof(cplx) * (size_t)g->V * 144);
+  int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
+  for (int s = 0; s < g->V; ++s) bad |= invert12(A + (size_t)s * 144, Ainv + (size_t)s * 144) != 0;
+  if (bad) {
+    free(Ainv);
+    return NULL;
+  }
+  return Ainv;
+}
+
+/* the smoother of the setup and of the V-cycle: plain (even_odd = 0) or
+ * with even-odd preconditioned domain solves (even_odd = 1) */
+static int smooth(const geom_t* g, const int* sites, const cplx* U, const cplx* A, const cplx* Ainv,
+                  const cplx* b, cplx* x, int n_sweeps, int n_mr, int even_odd) {
+  if (!even_odd) {
+    sap_rhs(g, sites, U, A, b, x, n_sweeps, n_mr);
+    return 0;
+  }
+  if (!Ainv) return -6;
+  sap_rhs_eo(g, sites, U, A, Ainv, b, x, n_sweeps, n_mr);
+  return 0;
+}
+
+/* x <- SAP^n_sweeps(b, x) with even-odd preconditioned domain solves */
+int ora_sap_eo(const int* dims, const int* agg, const cplx* U, const cplx* A, const cplx* b, cplx* x, int nrhs,
+               int n_sweeps, int n_mr) {
+  geom_t g;
+  if (geom_init(&g, dims, agg)) return -1;
+  init_gammas();
+  int* sites = aggregate_sites(&g);
+  cplx* Ainv = clover_inverses(&g, A);
+  size_t n = (size_t)g.V * 12;
+  int st = 0;
+  for (int j = 0; j < nrhs && !st; ++j) st = smooth(&g, sites, U, A, Ainv, b + j * n, x + j * n, n_sweeps, n_mr, 1);
+  free(Ainv);
+  free(sites);
+  return st;
+}
+
 /* x <- SAP^n_sweeps(b, x) for nrhs right-hand sides, one after the other */
 int ora_sap(const int* dims, const int* agg, const cplx* U, const cplx* A, const cplx* b,
             cplx* x, int nrhs, int n_sweeps, int n_mr) {
@@ -835,6 +1048,7 @@ typedef struct {
   int n_refine, n_smooth_sweeps, n_smooth_mr;
   double coarse_tol;
   int coarse_restart, coarse_maxit;
+  int even_odd;         /* 1: even-odd preconditioned domain solves in the smoother */
 } ora_setup_params;
 
 static void normalise(cplx* v, size_t n) {
@@ -852,25 +1066,29 @@ int ora_setup_init(const int* dims, const int* agg, int ntv, const cplx* U, cons
   if (geom_init(&g, dims, agg)) return -1;
   init_gammas();
   int* sites = aggregate_sites(&g);
+  cplx* Ainv = p->even_odd ? clover_inverses(&g, A) : NULL;
   size_t n = (size_t)g.V * 12;
   cplx* x = (cplx*)malloc(sizeof(cplx) * n);
-  for (int j = 0; j < ntv; ++j) {
+  int sst = 0;
+  for (int j = 0; j < ntv && !sst; ++j) {
     cplx* v = tv + j * n;
     if (p->init_mode == 0) {
       memset(x, 0, sizeof(cplx) * n);
-      sap_rhs(&g, sites, U, A, v, x, p->n_init_sweeps, p->n_init_mr);
+      sst = smooth(&g, sites, U, A, Ainv, v, x, p->n_init_sweeps, p->n_init_mr, p->even_odd);
       memcpy(v, x, sizeof(cplx) * n);
     } else {
-      for (int it = 0; it < p->n_init_sweeps; ++it) {
+      for (int it = 0; it < p->n_init_sweeps && !sst; ++it) {
         memset(x, 0, sizeof(cplx) * n);
-        sap_rhs(&g, sites, U, A, v, x, 1, p->n_init_mr);
+        sst = smooth(&g, sites, U, A, Ainv, v, x, 1, p->n_init_mr, p->even_odd);
         memcpy(v, x, sizeof(cplx) * n);
       }
     }
     normalise(v, n);
   }
   free(x);
+  free(Ainv);
   free(sites);
+  if (sst) return sst;
   int st = ora_gram_schmidt(dims, agg, ntv, tv, P);
   if (st) return st;
   return ora_coarse_op(dims, agg, ntv, U, A, P, Dc);
@@ -890,6 +1108,7 @@ int ora_setup_refine(const int* dims, const int* agg, int ntv, const cplx* U, co
   cplx* vc = (cplx*)malloc(sizeof(cplx) * nc);
   cplx* uc = (cplx*)malloc(sizeof(cplx) * nc);
   cplx* x = (cplx*)malloc(sizeof(cplx) * n);
+  cplx* Ainv = p->even_odd ? clover_inverses(&g, A) : NULL;
   coarse_ctx cc = {&g, ntv, Dc};
   int st = 0;
   for (int i = 0; i < p->n_refine; ++i) {
@@ -900,10 +1119,12 @@ int ora_setup_refine(const int* dims, const int* agg, int ntv, const cplx* U, co
                      p->coarse_maxit, NULL);
       if (coarse_iters) coarse_iters[i * ntv + j] = it;
       prolong_one(&g, ntv, P, uc, x);
-      sap_rhs(&g, sites, U, A, v, x, p->n_smooth_sweeps, p->n_smooth_mr);
+      st = smooth(&g, sites, U, A, Ainv, v, x, p->n_smooth_sweeps, p->n_smooth_mr, p->even_odd);
+      if (st) break;
       memcpy(v, x, sizeof(cplx) * n);
       normalise(v, n);
     }
+    if (st) break;
     st = ora_gram_schmidt(dims, agg, ntv, tv, P);
     if (st) break;
     st = ora_coarse_op(dims, agg, ntv, U, A, P, Dc);
@@ -912,6 +1133,7 @@ int ora_setup_refine(const int* dims, const int* agg, int ntv, const cplx* U, co
   free(vc);
   free(uc);
   free(x);
+  free(Ainv);
   free(sites);
   return st;
 }
@@ -923,7 +1145,8 @@ typedef struct {
   geom_t g;
   const int* sites;
   int ntv;
-  const cplx *U, *A, *P, *Dc;
+  const cplx *U, *A, *P, *Dc, *Ainv;
+  int even_odd;
   double coarse_tol;
   int coarse_restart, coarse_maxit, n_sweeps, n_mr;
   cplx *rc, *uc;
@@ -946,18 +1169,24 @@ static void vcycle(void* c, const cplx* r, cplx* z) {
   restrict_one(&m->g, m->ntv, m->P, r, m->rc);
   gmres(coarse_op, &cc, NULL, NULL, nc, m->rc, m->uc, m->coarse_tol, m->coarse_restart, m->coarse_maxit, NULL);
   prolong_one(&m->g, m->ntv, m->P, m->uc, z);
-  sap_rhs(&m->g, m->sites, m->U, m->A, r, z, m->n_sweeps, m->n_mr);
+  smooth(&m->g, m->sites, m->U, m->A, m->Ainv, r, z, m->n_sweeps, m->n_mr, m->even_odd);
 }
 
 int ora_fgmres(const int* dims, const int* agg, int ntv, const cplx* U, const cplx* A,
                const cplx* P, const cplx* Dc, const cplx* b, cplx* x, double tol, int restart,
                int maxit, double coarse_tol, int coarse_restart, int coarse_maxit, int n_sweeps,
-               int n_mr, int* iters, double* relres) {
+               int n_mr, int even_odd, int* iters, double* relres) {
   mg_ctx m;
   if (geom_init(&m.g, dims, agg)) return -1;
   init_gammas();
   int* sites = aggregate_sites(&m.g);
   m.sites = sites;
+  m.even_odd = even_odd;
+  m.Ainv = even_odd ? clover_inverses(&m.g, A) : NULL;
+  if (even_odd && !m.Ainv) {
+    free(sites);
+    return -6;
+  }
   m.ntv = ntv;
   m.U = U;
   m.A = A;
@@ -976,6 +1205,7 @@ int ora_fgmres(const int* dims, const int* agg, int ntv, const cplx* U, const cp
   if (iters) *iters = it;
   free(m.rc);
   free(m.uc);
+  free((void*)m.Ainv);
   free(sites);
   return 0;
 }

@@ -9,11 +9,14 @@ Per-result errors (the stated bounds):
   D_c: Frobenius norm of D_c,gpu - D_c,oracle relative to that of D_c,oracle;
   FGMRES: two-level FGMRES on D x = b to 1e-10 with the GPU setup needs
   the oracle's iteration count within +-10% (at least +-1).
-The bounds follow from the storage unit roundoff u (fp32 6e-8, fp16 4.9e-4,
-bf16 3.9e-3) carried through the smoother iterations of the setup: the
-measured errors on GB300 are about 17u (fp32), 2u (fp16) and 2u (bf16) for P
-and smaller for D_c; the bounds are 10 times the measured values:
-1e-5 (fp32), 1e-2 (fp16), 8e-2 (bf16).
+The errors scale with the storage unit roundoff u (fp32 6e-8, fp16 4.9e-4,
+bf16 3.9e-3) carried through the smoother iterations of the setup; there is
+no a-priori bound for an iterative procedure with tolerance-based coarse
+solves, so the bounds are the values measured on a GB300 (the setup is
+deterministic: the same inputs give the same bits) times 3:
+  P sine  9.7e-7 (fp32, 16u), 1.07e-3 (fp16, 2.2u), 7.8e-3 (bf16, 2.0u)
+          -> bounds 3e-6, 3.5e-3, 2.5e-2;
+  D_c     8.5e-7, 1.9e-4, 1.5e-3 -> bounded by the same numbers.
 """
 import numpy as np
 import pytest
@@ -27,7 +30,7 @@ pytestmark = pytest.mark.gpu
 
 CFG = dict(dims=(8, 8, 8, 8), agg=(4, 4, 4, 4), ntv=8, eps=0.3, m0=-0.2, csw=1.0, gseed=1201, tvseed=2201)
 SCHED = dict(init_sweeps=3, init_mr=4, n_refine=2, sweeps=4, mr=4, ctol=0.05, crestart=20, cmaxit=200)
-BOUNDS = {MRHS_PREC_FP32: 1e-5, MRHS_PREC_MIX_FP16: 1e-2, MRHS_PREC_MIX_BF16: 8e-2}
+BOUNDS = {MRHS_PREC_FP32: 3e-6, MRHS_PREC_MIX_FP16: 3.5e-3, MRHS_PREC_MIX_BF16: 2.5e-2}
 
 
 @pytest.fixture(scope="module")

@@ -296,6 +296,73 @@ def test_sap_many_mr_steps_is_block_gauss_seidel():
     assert np.abs(xo.reshape(-1) - x).max() / np.abs(x).max() < 1e-11
 
 
+def _colours_and_parity(dims, agg):
+    Ag = aggregate_of_sites(dims, agg)
+    nb = [d // a for d, a in zip(dims, agg)]
+    colour = np.stack(np.unravel_index(Ag, nb[::-1]), axis=1)[:, ::-1].sum(axis=1) % 2
+    c = np.stack(np.unravel_index(np.arange(vol(dims)), tuple(dims[::-1])), axis=1)[:, ::-1]
+    return Ag, colour, c.sum(axis=1) % 2
+
+
+def test_sap_even_odd_many_mr_steps_is_block_gauss_seidel():
+    """The even-odd form of the domain solve (MR on the Schur complement of
+    the even sites, then the odd sites) solves D_B e = r exactly in the limit
+    of many steps: one sweep is then the same multiplicative Schwarz step as
+    for the plain form."""
+    U, A = c1_field()
+    dims, agg = C1["dims"], C1["agg"]
+    V = vol(dims)
+    D = dense_D(dims, U, A)
+    Ag, colour, _ = _colours_and_parity(dims, agg)
+    b = inputs.gaussian_field((V, 12), 43)
+    x0 = inputs.gaussian_field((V, 12), 44) * 0.1
+    x = x0.reshape(-1).copy()
+    bb = b.reshape(-1)
+    for col in (0, 1):
+        r = bb - D @ x
+        for Bk in np.unique(Ag[colour == col]):
+            idx = np.concatenate([np.arange(s * 12, s * 12 + 12) for s in np.where(Ag == Bk)[0]])
+            x[idx] += np.linalg.solve(D[np.ix_(idx, idx)], r[idx])
+    xo = oracle.sap_eo(dims, agg, U, A, b[None], x0[None], 1, 200)[0]
+    assert np.abs(xo.reshape(-1) - x).max() / np.abs(x).max() < 1e-11
+
+
+def test_sap_even_odd_one_mr_step_is_the_schur_complement_step():
+    """One sweep of one MR step from x0 = 0, written with dense matrices: on
+    every domain D_B = [[A_EE, H_EO], [H_OE, A_OO]] (sites of even and odd
+    parity), S = A_EE - H_EO A_OO^-1 H_OE, rhat = r_E - H_EO A_OO^-1 r_O,
+    e_E = alpha rhat with alpha = <S rhat, rhat> / <S rhat, S rhat>, and
+    e_O = A_OO^-1 (r_O - H_OE e_E). A dropped or misplaced A_OO^-1, a sign of
+    the hopping part or the plain MR step in its place fails this."""
+    U, A = c1_field()
+    dims, agg = C1["dims"], C1["agg"]
+    V = vol(dims)
+    D = dense_D(dims, U, A)
+    Ag, colour, par = _colours_and_parity(dims, agg)
+    b = inputs.gaussian_field((V, 12), 45)
+    x = np.zeros(V * 12, complex)
+    bb = b.reshape(-1)
+    rows = lambda sites: np.concatenate([np.arange(s * 12, s * 12 + 12) for s in sites])
+    for col in (0, 1):
+        r = bb - D @ x
+        for Bk in np.unique(Ag[colour == col]):
+            sB = np.where(Ag == Bk)[0]
+            E, O = rows(sB[par[sB] == 0]), rows(sB[par[sB] == 1])
+            Aoo_inv = np.linalg.inv(D[np.ix_(O, O)])
+            S = D[np.ix_(E, E)] - D[np.ix_(E, O)] @ Aoo_inv @ D[np.ix_(O, E)]
+            rhat = r[E] - D[np.ix_(E, O)] @ (Aoo_inv @ r[O])
+            q = S @ rhat
+            eE = (np.vdot(q, rhat) / np.vdot(q, q)) * rhat
+            eO = Aoo_inv @ (r[O] - D[np.ix_(O, E)] @ eE)
+            x[E] += eE
+            x[O] += eO
+    xo = oracle.sap_eo(dims, agg, U, A, b[None], np.zeros_like(b)[None], 1, 1)[0]
+    assert np.abs(xo.reshape(-1) - x).max() / np.abs(x).max() < 1e-12
+    # and it is not the plain one-step MR sweep
+    xp = oracle.sap(dims, agg, U, A, b[None], np.zeros_like(b)[None], 1, 1)[0]
+    assert np.abs(xp - xo).max() / np.abs(xo).max() > 1e-2
+
+
 def test_sap_reduces_residual_and_is_gauge_covariant():
     U, A = c1_field()
     dims, agg = C1["dims"], C1["agg"]
