@@ -165,6 +165,21 @@ int mrhs_apply_D_block(mrhs_ctx ctx, const void* x, void* y, int nrhs, int dtype
  * of storage dtype F64 or F32. */
 int mrhs_sap(mrhs_ctx ctx, const void* b, void* x, int nrhs, int dtype, int n_sweeps, int n_mr);
 
+/* Domain solves of the SAP smoother (every use: mrhs_sap, the setup phases,
+ * the V-cycle of mrhs_solve_fgmres). even_odd = 0 (default): n_mr MR steps on
+ * D_B e = r_B. even_odd = 1: even-odd preconditioning (the Schur complement
+ * used for the coarse grid in Sec. 4 and Eq. 1, here applied to the domain
+ * solves): with E, O the sites of even and odd parity (x+y+z+t) of the domain
+ * and H its hopping terms, n_mr MR steps on
+ *   S e_E = r_E - H_EO A_OO^-1 r_O,   S = A_EE - H_EO A_OO^-1 H_OE,
+ * from e_E = 0 (inner products over the even sites), then
+ * e_O = A_OO^-1 (r_O - H_OE e_E) and x_B += e. The inverse clover term is
+ * built on the first use after each mrhs_build_clover (MRHS_ERR_NONFINITE if
+ * a block is singular). The even-odd form runs in the generic domain kernel
+ * (one CTA per domain); the on-chip kernels serve only the plain form.
+ * MRHS_ERR_ARG unless even_odd is 0 or 1. */
+int mrhs_set_smoother(mrhs_ctx ctx, int even_odd);
+
 /* ------------------------------------------------------ setup building blocks */
 
 /* copy ntv test vectors (device interleaved field, nrhs = ntv, storage

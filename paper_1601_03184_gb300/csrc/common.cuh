@@ -190,6 +190,10 @@ struct mrhs_ctx_s {
   float* U20 = nullptr;   // [V][4][20]: FP32 links padded to 80 bytes (float4-aligned records)
   double* A64 = nullptr;  // [V][2][36]
   float* A32 = nullptr;
+  double* Ainv64 = nullptr;  // [V][2][36] inverse clover term (even-odd smoother), built on first use
+  float* Ainv32 = nullptr;
+  bool have_clover_inv = false;
+  int even_odd = 0;          // 1: SAP domain solves on the Schur complement of the even sites
   bool have_gauge = false, have_clover = false;
 
   // setup state
@@ -213,7 +217,7 @@ struct mrhs_ctx_s {
   size_t hbuf_bytes = 0;
 
   // named scratch buffers, grown on demand
-  mrhs::DevBuf scratch[16];
+  mrhs::DevBuf scratch[20];
 
   mrhs::NNState* nn = nullptr;  // learned test-vector generator (nn.cu)
 
@@ -246,6 +250,8 @@ enum Scratch {
   SC_KRYLOV_F,    // FGMRES basis
   SC_MISC,
   SC_BLOCK,       // one block of test vectors (block length N_b < ntv)
+  SC_EO1,         // even-odd domain solves: rho (even sites) / A^-1 H rho (odd sites)
+  SC_EO2,         // q (even) and e (both parities), interleaved as two fields
   SC_COUNT
 };
 
@@ -298,6 +304,7 @@ void convert_scaled(mrhs_ctx c, const void* x, int dx, void* y, int dy, size_t n
 void gather_cols(mrhs_ctx c, const void* src, int ntv, void* dst, int nb, int k0, int dtype);
 void scatter_cols(mrhs_ctx c, const void* src, int ds, int nb, void* dst, int dd, int ntv, int k0, float scale);
 void sap_mixed(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int dtype, int n_sweeps, int n_mr);
+void ensure_clover_inverse(mrhs_ctx c);
 // sap.cu: the on-chip SAP (FP32 work fields)
 bool sap_fused_ok(mrhs_ctx c, int dtype);
 void sap_fused(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int n_sweeps, int n_mr);

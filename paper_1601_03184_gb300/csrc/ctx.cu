@@ -293,6 +293,62 @@ __global__ void k_clover(int V, const double* U, const int* nbr, double m0, doub
   }
 }
 
+// inverse of the clover term, per site and chirality (Gauss-Jordan with
+// partial pivoting on the 6x6 block in FP64), packed like the clover term;
+// *bad is set if a block is singular
+__global__ void k_clover_inverse(int V, const double* A64, double* I64, float* I32, int* bad) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * V) return;
+  const double* q = A64 + (size_t)t * 36;
+  cx<double> m[6][12];
+  for (int a = 0; a < 6; ++a)
+    for (int b = 0; b < 12; ++b) {
+      if (b >= 6) m[a][b] = mk(b - 6 == a ? 1.0 : 0.0, 0.0);
+      else if (a == b) m[a][b] = mk(q[a], 0.0);
+      else if (b > a) m[a][b] = mk(q[6 + 2 * herm_off(a, b)], q[6 + 2 * herm_off(a, b) + 1]);
+      else m[a][b] = mk(q[6 + 2 * herm_off(b, a)], -q[6 + 2 * herm_off(b, a) + 1]);
+    }
+  for (int c = 0; c < 6; ++c) {
+    int p = c;
+    double best = m[c][c].re * m[c][c].re + m[c][c].im * m[c][c].im;
+    for (int i = c + 1; i < 6; ++i) {
+      const double v = m[i][c].re * m[i][c].re + m[i][c].im * m[i][c].im;
+      if (v > best) best = v, p = i;
+    }
+    if (!(best > 0)) {
+      atomicExch(bad, 1);
+      return;
+    }
+    if (p != c)
+      for (int j = 0; j < 12; ++j) {
+        const cx<double> tmp = m[p][j];
+        m[p][j] = m[c][j];
+        m[c][j] = tmp;
+      }
+    // row c /= pivot: multiply by conj(pivot) / |pivot|^2
+    const cx<double> pc = scale(cnj(m[c][c]), 1.0 / best);
+    for (int j = 0; j < 12; ++j) m[c][j] = m[c][j] * pc;
+    for (int i = 0; i < 6; ++i) {
+      if (i == c) continue;
+      const cx<double> f = m[i][c];
+      for (int j = 0; j < 12; ++j) m[i][j] = m[i][j] - f * m[c][j];
+    }
+  }
+  double* o64 = I64 + (size_t)t * 36;
+  float* o32 = I32 + (size_t)t * 36;
+  for (int a = 0; a < 6; ++a) {
+    o64[a] = m[a][6 + a].re;
+    o32[a] = (float)m[a][6 + a].re;
+    for (int b = a + 1; b < 6; ++b) {
+      const int k = 6 + 2 * herm_off(a, b);
+      o64[k] = m[a][6 + b].re;
+      o64[k + 1] = m[a][6 + b].im;
+      o32[k] = (float)m[a][6 + b].re;
+      o32[k + 1] = (float)m[a][6 + b].im;
+    }
+  }
+}
+
 // packed clover -> dense canonical [V][2][6][6] complex128
 __global__ void k_clover_out(int V, const int* perm, const double* A64, double* out) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -530,6 +586,27 @@ void scatter_cols(mrhs_ctx c, const void* src, int ds, int nb, void* dst, int dd
   MRHS_DISPATCH(ds, SI, MRHS_DISPATCH(dd, SO, (k_scatter_cols<SI, SO><<<grid_for(n, 256), 256, 0, c->stream>>>((const SI*)src, nb, (SO*)dst, ntv, k0, n, scale))));
   MRHS_LAUNCH_CHECK("scatter_cols");
 }
+// the inverse clover term (for the even-odd domain solves), built once per
+// clover term on first use
+void ensure_clover_inverse(mrhs_ctx c) {
+  MRHS_REQUIRE(c->have_clover, MRHS_ERR_STATE, "even-odd smoother before mrhs_build_clover");
+  if (c->have_clover_inv) return;
+  const size_t n = (size_t)c->g.V * 72;
+  if (!c->Ainv64) {
+    c->Ainv64 = (double*)dalloc(c, n * sizeof(double));
+    c->Ainv32 = (float*)dalloc(c, n * sizeof(float));
+  }
+  MRHS_CUDA(cudaMemsetAsync(c->dflag + 4, 0, sizeof(int), c->stream));
+  Prof pr(c, "clover_inverse");
+  k_clover_inverse<<<grid_for(2 * (size_t)c->g.V, 128), 128, 0, c->stream>>>(c->g.V, c->A64, c->Ainv64, c->Ainv32,
+                                                                             c->dflag + 4);
+  MRHS_LAUNCH_CHECK("clover_inverse");
+  MRHS_CUDA(cudaMemcpyAsync(c->hflag + 4, c->dflag + 4, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  MRHS_CUDA(cudaStreamSynchronize(c->stream));
+  MRHS_REQUIRE(c->hflag[4] == 0, MRHS_ERR_NONFINITE, "clover term singular on some site (even-odd smoother)");
+  c->have_clover_inv = true;
+}
+
 }  // namespace mrhs
 
 // ------------------------------------------------------------------ ABI ----
@@ -726,6 +803,7 @@ int mrhs_build_clover(mrhs_ctx c, double m0, double csw) {
     k_clover<<<grid_for(c->g.V, 128), 128, 0, c->stream>>>(c->g.V, c->U64, c->nbr, m0, csw, c->A64, c->A32);
     MRHS_LAUNCH_CHECK("clover");
     c->have_clover = true;
+    c->have_clover_inv = false;
   });
 }
 

@@ -118,6 +118,182 @@ __global__ void k_block_mr(S* x, S* rho, S* q, const cx<R>* __restrict__ U, cons
   }
 }
 
+// Even-odd preconditioned domain solves: n_mr minimal-residual steps on the
+// Schur complement of the even sites, S = A_EE - H_EO A_OO^-1 H_OE, for
+// every aggregate in blist (one CTA per aggregate, all right-hand sides),
+// from the residual r of the colour:
+//   u_O = A_OO^-1 r_O,  rho_E = r_E - H_EO u_O,  e_E = 0;
+//   n_mr times: u_O = A_OO^-1 H_OE rho_E, q_E = A_EE rho_E - H_EO u_O,
+//               alpha = <q, rho>_E / <q, q>_E, e_E += alpha rho, rho -= alpha q;
+//   e_O = A_OO^-1 (r_O - H_OE e_E);  x_B += e.
+// H = the hopping terms inside the domain (they change the site parity, so
+// every hop reads only sites of the other parity). ru holds rho on even and
+// u on odd sites; q and e are separate fields.
+struct EoGeom {
+  int a[4], nb[4];
+};
+
+template <class S, class R>
+__device__ __forceinline__ void site_apply_packed(cx<R> out[12], const S* x, size_t row, int N, int r, const R* M) {
+  cx<R> psi[12];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) psi[c] = ld<S, R>(x, row + c, N, r);
+  clover_apply_reg<R>(out, psi, M);
+}
+
+template <class S, class R>
+__global__ void k_block_mr_eo(S* x, const S* rres, S* ru, S* q, S* e, const cx<R>* __restrict__ U,
+                              const R* __restrict__ A, const R* __restrict__ Ainv, const int* __restrict__ nbr, int N,
+                              int Va, const int* __restrict__ blist, int n_mr, EoGeom g) {
+  extern __shared__ double smem[];
+  const int lanes = blockDim.x / N;
+  const int tid = threadIdx.x;
+  const int r = tid % N;
+  const int lane = tid / N;
+  const bool active = lane < lanes;
+  double* sqr_re = smem;
+  double* sqr_im = sqr_re + lanes * N;
+  double* sqq = sqr_im + lanes * N;
+  double* salpha = sqq + lanes * N;
+  const int blk = blist[blockIdx.x];
+  const int s0 = blk * Va;
+  // parity of the aggregate's first site, then of site l inside it
+  int pb = 0;
+  {
+    int i = blk;
+    for (int m = 0; m < 4; ++m) {
+      pb += (i % g.nb[m]) * g.a[m];
+      i /= g.nb[m];
+    }
+  }
+  auto parity = [&](int l) {
+    int p = pb;
+    for (int m = 0; m < 4; ++m) {
+      p += l % g.a[m];
+      l /= g.a[m];
+    }
+    return p & 1;
+  };
+  // u_O = A_OO^-1 r_O
+  if (active)
+    for (int l = lane; l < Va; l += lanes)
+      if (parity(l) == 1) {
+        const int s = s0 + l;
+        cx<R> o[12];
+        site_apply_packed<S, R>(o, rres, (size_t)s * 12, N, r, Ainv + (size_t)s * 72);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) st<S, R>(ru, (size_t)s * 12 + c, N, r, o[c]);
+      }
+  __syncthreads();
+  // rho_E = r_E - H_EO u_O, e_E = 0
+  if (active)
+    for (int l = lane; l < Va; l += lanes)
+      if (parity(l) == 0) {
+        const int s = s0 + l;
+        cx<R> h[12];
+        dslash_site<true, S, R, false>(h, ru, s, N, r, U, A, nbr, Va);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+          st<S, R>(ru, (size_t)s * 12 + c, N, r, ld<S, R>(rres, (size_t)s * 12 + c, N, r) - h[c]);
+          st<S, R>(e, (size_t)s * 12 + c, N, r, mk<R>(0, 0));
+        }
+      }
+  __syncthreads();
+  for (int it = 0; it < n_mr; ++it) {
+    // u_O = A_OO^-1 H_OE rho_E
+    if (active)
+      for (int l = lane; l < Va; l += lanes)
+        if (parity(l) == 1) {
+          const int s = s0 + l;
+          cx<R> h[12], u[12];
+          dslash_site<true, S, R, false>(h, ru, s, N, r, U, A, nbr, Va);
+          clover_apply_reg<R>(u, h, Ainv + (size_t)s * 72);
+#pragma unroll
+          for (int c = 0; c < 12; ++c) st<S, R>(ru, (size_t)s * 12 + c, N, r, u[c]);
+        }
+    __syncthreads();
+    // q_E = A_EE rho_E - H_EO u_O and the two inner products over the even sites
+    double qr_re = 0, qr_im = 0, qq = 0;
+    if (active) {
+      for (int l = lane; l < Va; l += lanes)
+        if (parity(l) == 0) {
+          const int s = s0 + l;
+          cx<R> a[12], h[12];
+          site_apply_packed<S, R>(a, ru, (size_t)s * 12, N, r, A + (size_t)s * 72);
+          dslash_site<true, S, R, false>(h, ru, s, N, r, U, A, nbr, Va);
+          R pr = 0, pi = 0, pq = 0;
+#pragma unroll
+          for (int c = 0; c < 12; ++c) {
+            st<S, R>(q, (size_t)s * 12 + c, N, r, a[c] - h[c]);
+            const cx<R> qv = ld<S, R>(q, (size_t)s * 12 + c, N, r);  // the stored (rounded) value
+            const cx<R> rv = ld<S, R>(ru, (size_t)s * 12 + c, N, r);
+            pr += qv.re * rv.re + qv.im * rv.im;
+            pi += qv.re * rv.im - qv.im * rv.re;
+            pq += qv.re * qv.re + qv.im * qv.im;
+          }
+          qr_re += (double)pr;
+          qr_im += (double)pi;
+          qq += (double)pq;
+        }
+      sqr_re[lane * N + r] = qr_re;
+      sqr_im[lane * N + r] = qr_im;
+      sqq[lane * N + r] = qq;
+    }
+    __syncthreads();
+    if (tid < N) {
+      double a = 0, bb = 0, c = 0;
+      for (int l = 0; l < lanes; ++l) {
+        a += sqr_re[l * N + tid];
+        bb += sqr_im[l * N + tid];
+        c += sqq[l * N + tid];
+      }
+      salpha[2 * tid] = c > 0 ? a / c : 0.0;
+      salpha[2 * tid + 1] = c > 0 ? bb / c : 0.0;
+    }
+    __syncthreads();
+    // e_E += alpha rho_E, rho_E -= alpha q_E
+    if (active) {
+      const cx<R> al = mk<R>((R)salpha[2 * r], (R)salpha[2 * r + 1]);
+      for (int l = lane; l < Va; l += lanes)
+        if (parity(l) == 0) {
+          const size_t row = (size_t)(s0 + l) * 12;
+#pragma unroll
+          for (int c = 0; c < 12; ++c) {
+            cx<R> rv = ld<S, R>(ru, row + c, N, r);
+            const cx<R> qv = ld<S, R>(q, row + c, N, r);
+            cx<R> ev = ld<S, R>(e, row + c, N, r);
+            fma_(ev, al, rv);
+            fma_(rv, al, mk<R>(-qv.re, -qv.im));
+            st<S, R>(e, row + c, N, r, ev);
+            st<S, R>(ru, row + c, N, r, rv);
+          }
+        }
+    }
+    __syncthreads();
+  }
+  // e_O = A_OO^-1 (r_O - H_OE e_E)
+  if (active)
+    for (int l = lane; l < Va; l += lanes)
+      if (parity(l) == 1) {
+        const int s = s0 + l;
+        cx<R> h[12], o[12];
+        dslash_site<true, S, R, false>(h, e, s, N, r, U, A, nbr, Va);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) h[c] = ld<S, R>(rres, (size_t)s * 12 + c, N, r) - h[c];
+        clover_apply_reg<R>(o, h, Ainv + (size_t)s * 72);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) st<S, R>(e, (size_t)s * 12 + c, N, r, o[c]);
+      }
+  __syncthreads();
+  // x_B += e
+  if (active)
+    for (int l = lane; l < Va; l += lanes) {
+      const size_t row = (size_t)(s0 + l) * 12;
+#pragma unroll
+      for (int c = 0; c < 12; ++c) st<S, R>(x, row + c, N, r, ld<S, R>(x, row + c, N, r) + ld<S, R>(e, row + c, N, r));
+    }
+}
+
 // ---------------------------------------------------------------------------
 // FP32 full operator, y = D x, on packed pairs of right-hand sides: P pairs
 // per thread (2P interleaved right-hand sides, 8- or 16-byte loads), links
@@ -418,6 +594,33 @@ void block_mr_t(mrhs_ctx c, S* x, S* rho, S* q, int N, const int* blist, int nbl
   MRHS_LAUNCH_CHECK("block_mr");
 }
 
+// the even-odd domain solves of one colour: r the colour's residual, work
+// fields ru, q, e of the same size
+template <class S>
+void block_mr_eo_t(mrhs_ctx c, S* x, const S* r, S* ru, S* q, S* e, int N, const int* blist, int nblk, int n_mr) {
+  using R = typename Real<S>::type;
+  const cx<R>* U;
+  const R *A, *Ainv;
+  if constexpr (sizeof(R) == 8) {
+    U = (const cx<R>*)c->U64;
+    A = (const R*)c->A64;
+    Ainv = (const R*)c->Ainv64;
+  } else {
+    U = (const cx<R>*)c->U32;
+    A = (const R*)c->A32;
+    Ainv = (const R*)c->Ainv32;
+  }
+  int bs = 256;
+  if (N > bs) bs = ((N + 31) / 32) * 32;
+  int lanes = bs / N;
+  size_t smem = sizeof(double) * (3 * (size_t)lanes * N + 2 * N);
+  EoGeom g;
+  for (int m = 0; m < 4; ++m) g.a[m] = c->g.a[m], g.nb[m] = c->g.nb[m];
+  Prof pr(c, "sap_block_mr_eo");
+  k_block_mr_eo<S, R><<<nblk, bs, smem, c->stream>>>(x, r, ru, q, e, U, A, Ainv, c->nbr, N, c->g.Va, blist, n_mr, g);
+  MRHS_LAUNCH_CHECK("block_mr_eo");
+}
+
 }  // namespace
 
 void dslash(mrhs_ctx c, const void* x, void* y, const void* b, int nrhs, int dtype, int mode, int colour) {
@@ -459,6 +662,27 @@ static void resid_mixed(mrhs_ctx c, const void* x, void* y, const void* b, int b
 void sap_mixed(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int dtype, int n_sweeps, int n_mr) {
   MRHS_REQUIRE(c->have_clover, MRHS_ERR_STATE, "smoother used before mrhs_build_clover");
   MRHS_REQUIRE(n_sweeps >= 0 && n_mr >= 0 && nrhs >= 1, MRHS_ERR_ARG, "bad smoother parameters");
+  if (c->even_odd) {
+    // domain solves on the Schur complement of the even sites: residual
+    // kernel + one CTA per domain (no on-chip form)
+    ensure_clover_inverse(c);
+    const size_t bytes = fine_elems(c, nrhs) * dtype_size(dtype);
+    void* r = scratch(c, SC_R, bytes);
+    void* ru = scratch(c, SC_EO1, bytes);
+    char* qe = (char*)scratch(c, SC_EO2, 2 * bytes);
+    for (int sw = 0; sw < n_sweeps; ++sw)
+      for (int col = 0; col < 2; ++col) {
+        resid_mixed(c, x, r, b, bdtype, nrhs, dtype, col);
+        const int* blist = c->blocks_col + (col ? c->ncol[0] : 0);
+        if (dtype == MRHS_F64)
+          block_mr_eo_t<double>(c, (double*)x, (const double*)r, (double*)ru, (double*)qe, (double*)(qe + bytes),
+                                nrhs, blist, c->ncol[col], n_mr);
+        else
+          block_mr_eo_t<float>(c, (float*)x, (const float*)r, (float*)ru, (float*)qe, (float*)(qe + bytes), nrhs,
+                               blist, c->ncol[col], n_mr);
+      }
+    return;
+  }
   if (sap_fused_ok(c, dtype)) {
     sap_fused(c, b, bdtype, x, nrhs, n_sweeps, n_mr);
     return;
@@ -500,6 +724,14 @@ int mrhs_apply_D_block(mrhs_ctx c, const void* x, void* y, int nrhs, int dtype) 
     require_dev(c, x, "mrhs_apply_D_block x");
     require_dev(c, y, "mrhs_apply_D_block y");
     dslash(c, x, y, nullptr, nrhs, dtype, DS_BLOCK, -1);
+  });
+}
+
+int mrhs_set_smoother(mrhs_ctx c, int even_odd) {
+  return guarded(c, [&] {
+    MRHS_REQUIRE(c, MRHS_ERR_ARG, "null context");
+    MRHS_REQUIRE(even_odd == 0 || even_odd == 1, MRHS_ERR_ARG, "even_odd must be 0 or 1");
+    c->even_odd = even_odd;
   });
 }
 

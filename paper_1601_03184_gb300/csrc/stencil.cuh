@@ -135,10 +135,16 @@ __device__ __forceinline__ void clover_apply(cx<R> out[12], const S* x, size_t r
 }
 
 // D (BLOCK = false) or D_B (BLOCK = true) at device site s, right-hand side r
-template <bool BLOCK, class S, class R>
+// CLOVER = false: the hopping terms alone (out starts at zero; A unused)
+template <bool BLOCK, class S, class R, bool CLOVER = true>
 __device__ __forceinline__ void dslash_site(cx<R> out[12], const S* x, int s, int N, int r, const cx<R>* U,
                                             const R* A, const int* nbr, int Va) {
-  clover_apply<S, R>(out, x, (size_t)s * 12, N, r, A + (size_t)s * 72);
+  if constexpr (CLOVER) {
+    clover_apply<S, R>(out, x, (size_t)s * 12, N, r, A + (size_t)s * 72);
+  } else {
+#pragma unroll
+    for (int c = 0; c < 12; ++c) out[c] = mk<R>(0, 0);
+  }
   const int blk = s / Va;
   const cx<R>* Us = U + (size_t)s * 36;
 #define MRHS_HOP(MU)                                                                                   \
