@@ -428,7 +428,15 @@ void sap_pk(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int n_swee
   // per lane quarter (at most 4 x 120 = 480 of the 512 columns)
   uint32_t cols = 32;
   while (cols < (uint32_t)(T / 128) * kPWarpCols) cols <<= 1;
-  const int cpb = nrhs / kPG;  // one chunk per CTA: a domain's CTAs share x and b sectors in L2
+  // CTAs per domain: by default one chunk each, so that a domain's CTAs run
+  // side by side and share the 32-byte sectors of x and b in L2;
+  // MRHS_SAP_CPB = c: c CTAs per domain, each looping over nrhs / (4 c) chunks
+  // (the links and clover term staged once per CTA serve all its chunks)
+  static const int cpb_env = [] {
+    const char* e = std::getenv("MRHS_SAP_CPB");
+    return e ? std::atoi(e) : 0;
+  }();
+  const int cpb = cpb_env > 0 ? std::min(cpb_env, nrhs / kPG) : nrhs / kPG;
   for (int sw = 0; sw < n_sweeps; ++sw)
     for (int col = 0; col < 2; ++col) {
       const int* blist = c->blocks_col + (col ? c->ncol[0] : 0);

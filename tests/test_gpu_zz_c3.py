@@ -13,10 +13,15 @@ and .npz, written by tests/golden/c3_mixed.py from the oracle only):
   - per-result errors on the stored aggregates (the first, one inside, the
     last): the largest principal-angle sine between range(P) and the
     oracle's range per aggregate and chirality, and the relative Frobenius
-    error of the nine D_c blocks. These are reported; their bounds are
-    sanity bounds (a reduced-precision setup drifts from the FP64 one through
-    many smoother and coarse iterations and the tolerance-based coarse solves,
-    so no a-priori bound exists): 0.05 for FP32, 0.2 for bf16 and fp16.
+    error of the nine D_c blocks. A reduced-precision setup drifts from the
+    FP64 one through many smoother and coarse iterations and the
+    tolerance-based coarse solves, so no a-priori bound exists; the setup is
+    deterministic, and the bounds are the values measured on a GB300 times 3:
+      FP32  P sine 2.6e-6, D_c 1.3e-6            -> 8e-6
+      bf16  P sine 1.47e-2 (3.8u), D_c 2.5e-3    -> 4.5e-2
+      fp16  P sine 1.87e-3 (3.8u), D_c 3.0e-4    -> 6e-3
+    (u the storage unit roundoff); FGMRES: 25 iterations in all three, as
+    the oracle's setup.
 Needs about 30 GB of device memory and 30 GB of host memory.
 """
 import json
@@ -107,7 +112,7 @@ def test_c3_fp32_setup_against_oracle(problem):
     ref = GOLDEN["iterations"]
     assert r["relres"] <= 1e-10
     assert abs(r["fgmres"] - ref) <= max(1, 0.1 * ref)
-    assert r["P_sine"] < 0.05 and r["Dc_rel"] < 0.05
+    assert r["P_sine"] < 8e-6 and r["Dc_rel"] < 8e-6
 
 
 @pytest.mark.parametrize("prec", [MRHS_PREC_MIX_BF16, MRHS_PREC_MIX_FP16], ids=["bf16", "fp16"])
@@ -118,4 +123,5 @@ def test_c3_mixed_setup_against_fp32_and_oracle(problem, prec):
     r = run_setup(problem, prec)
     assert r["relres"] <= 1e-10
     assert abs(r["fgmres"] - plain) <= max(1, 0.1 * plain)
-    assert r["P_sine"] < 0.2 and r["Dc_rel"] < 0.2
+    bound = {MRHS_PREC_MIX_BF16: 4.5e-2, MRHS_PREC_MIX_FP16: 6e-3}[prec]
+    assert r["P_sine"] < bound and r["Dc_rel"] < bound
