@@ -54,6 +54,7 @@ class SetupParams(ctypes.Structure):
         ("coarse_restart", ctypes.c_int),
         ("coarse_maxit", ctypes.c_int),
         ("even_odd", ctypes.c_int),
+        ("coarse_even_odd", ctypes.c_int),
     ]
 
 
@@ -198,10 +199,22 @@ def coarse_solve(dims, agg, Dc, bc, tol, restart, maxit):
     return xc, its
 
 
+def coarse_solve_eo(dims, agg, Dc, bc, tol, restart, maxit):
+    """Coarse solve on the Schur complement of the even aggregates. Returns (xc, iterations)."""
+    Dc, bc = _c(Dc), _c(bc)
+    nrhs = bc.shape[0]
+    xc = np.zeros_like(bc)
+    its = np.zeros(nrhs, np.int32)
+    _check(lib().ora_coarse_solve_eo(_i4(dims), _i4(agg), Dc.shape[2] // 2, _p(Dc), _p(bc), _p(xc), nrhs,
+                                     ctypes.c_double(tol), restart, maxit, _p(its)), "coarse_solve_eo")
+    return xc, its
+
+
 def make_params(init_mode=0, n_init_sweeps=3, n_init_mr=4, n_refine=1, n_smooth_sweeps=4,
-                n_smooth_mr=4, coarse_tol=0.05, coarse_restart=20, coarse_maxit=200, even_odd=0):
+                n_smooth_mr=4, coarse_tol=0.05, coarse_restart=20, coarse_maxit=200, even_odd=0,
+                coarse_even_odd=0):
     return SetupParams(init_mode, n_init_sweeps, n_init_mr, n_refine, n_smooth_sweeps, n_smooth_mr,
-                       float(coarse_tol), coarse_restart, coarse_maxit, int(even_odd))
+                       float(coarse_tol), coarse_restart, coarse_maxit, int(even_odd), int(coarse_even_odd))
 
 
 def setup_init(dims, agg, U, A, tv0, params):
@@ -228,7 +241,7 @@ def setup_refine(dims, agg, U, A, tv, P, Dc, params):
 
 
 def fgmres(dims, agg, U, A, P, Dc, b, tol=1e-10, restart=25, maxit=500, coarse_tol=0.05,
-           coarse_restart=20, coarse_maxit=200, n_sweeps=4, n_mr=4, even_odd=0):
+           coarse_restart=20, coarse_maxit=200, n_sweeps=4, n_mr=4, even_odd=0, coarse_even_odd=0):
     """Two-level FGMRES on D x = b. Returns (x, iterations, relative residual estimate)."""
     U, A, P, Dc, b = _c(U), _c(A), _c(P), _c(Dc), _c(b)
     x = np.zeros_like(b)
@@ -237,7 +250,8 @@ def fgmres(dims, agg, U, A, P, Dc, b, tol=1e-10, restart=25, maxit=500, coarse_t
     _check(
         lib().ora_fgmres(_i4(dims), _i4(agg), P.shape[0], _p(U), _p(A), _p(P), _p(Dc), _p(b), _p(x),
                          ctypes.c_double(tol), restart, maxit, ctypes.c_double(coarse_tol), coarse_restart,
-                         coarse_maxit, n_sweeps, n_mr, int(even_odd), ctypes.byref(it), ctypes.byref(rr)),
+                         coarse_maxit, n_sweeps, n_mr, int(even_odd), int(coarse_even_odd), ctypes.byref(it),
+                         ctypes.byref(rr)),
         "fgmres",
     )
     return x, it.value, rr.value

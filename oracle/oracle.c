@@ -1039,6 +1039,158 @@ int ora_coarse_solve(const int* dims, const int* agg, int ntv, const cplx* Dc, c
 }
 
 /* ------------------------------------------------------------------ */
+/* even-odd preconditioned coarse solve                                  */
+/* ------------------------------------------------------------------ */
+/* The red-black colouring of the aggregates (the SAP domains) makes every
+ * hop block of D_c join aggregates of different colour, so with e the
+ * aggregates of colour 0 and o those of colour 1, D_c = [[D_ee, D_eo],
+ * [D_oe, D_oo]] with D_ee and D_oo block-diagonal (the self blocks). The
+ * coarse system is solved on the Schur complement of the even aggregates
+ * (Sec. 4 names even-odd preconditioning of the coarse grid):
+ *   S x_e = b_e - D_eo D_oo^-1 b_o,   S = D_ee - D_eo D_oo^-1 D_oe,
+ *   x_o = D_oo^-1 (b_o - D_oe x_e),
+ * GMRES(m) on S from x_e = 0 with the relative tolerance taken on the Schur
+ * system's right-hand side. Vectors keep the full coarse layout with zeros on
+ * the odd aggregates. */
+
+/* n x n inverse by Gauss-Jordan elimination with partial pivoting */
+static int invert_n(int n, const cplx* a, cplx* inv) {
+  cplx* m = (cplx*)malloc(sizeof(cplx) * (size_t)n * 2 * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < 2 * n; ++j) m[(size_t)i * 2 * n + j] = j < n ? a[(size_t)i * n + j] : (j - n == i ? 1.0 : 0.0);
+  int st = 0;
+  for (int c = 0; c < n && !st; ++c) {
+    int p = c;
+    for (int i = c + 1; i < n; ++i)
+      if (cabs(m[(size_t)i * 2 * n + c]) > cabs(m[(size_t)p * 2 * n + c])) p = i;
+    if (cabs(m[(size_t)p * 2 * n + c]) == 0) {
+      st = -6;
+      break;
+    }
+    if (p != c)
+      for (int j = 0; j < 2 * n; ++j) {
+        cplx t = m[(size_t)p * 2 * n + j];
+        m[(size_t)p * 2 * n + j] = m[(size_t)c * 2 * n + j];
+        m[(size_t)c * 2 * n + j] = t;
+      }
+    cplx piv = m[(size_t)c * 2 * n + c];
+    for (int j = 0; j < 2 * n; ++j) m[(size_t)c * 2 * n + j] /= piv;
+    for (int i = 0; i < n; ++i) {
+      if (i == c) continue;
+      cplx f = m[(size_t)i * 2 * n + c];
+      if (f != 0)
+        for (int j = 0; j < 2 * n; ++j) m[(size_t)i * 2 * n + j] -= f * m[(size_t)c * 2 * n + j];
+    }
+  }
+  for (int i = 0; i < n && !st; ++i)
+    for (int j = 0; j < n; ++j) inv[(size_t)i * n + j] = m[(size_t)i * 2 * n + n + j];
+  free(m);
+  return st;
+}
+
+typedef struct {
+  const geom_t* g;
+  int ntv;
+  const cplx* Dc;
+  const cplx* Dinv; /* [nagg][nc][nc], the inverse self blocks of the odd aggregates */
+  cplx *t, *u;      /* work vectors of the coarse size */
+} coarse_eo_ctx;
+
+/* y = D_oo^-1 x on the odd aggregates, 0 on the even ones */
+static void odd_block_inverse(const coarse_eo_ctx* e, const cplx* x, cplx* y) {
+  const int nc = 2 * e->ntv;
+  for (int A = 0; A < e->g->nagg; ++A)
+    for (int i = 0; i < nc; ++i) {
+      cplx c = 0;
+      if (aggregate_colour(e->g, A) == 1)
+        for (int j = 0; j < nc; ++j) c += e->Dinv[((size_t)A * nc + i) * nc + j] * x[(size_t)A * nc + j];
+      y[(size_t)A * nc + i] = c;
+    }
+}
+
+/* out = S in (in zero on the odd aggregates; out likewise) */
+static void coarse_schur_op(void* c, const cplx* in, cplx* out) {
+  coarse_eo_ctx* e = (coarse_eo_ctx*)c;
+  const int nc = 2 * e->ntv;
+  apply_Dc_one(e->g, e->ntv, e->Dc, in, e->t);  /* even rows: D_ee in_e; odd rows: D_oe in_e */
+  odd_block_inverse(e, e->t, e->u);              /* u_o = D_oo^-1 D_oe in_e */
+  apply_Dc_one(e->g, e->ntv, e->Dc, e->u, out);  /* even rows: D_eo u_o */
+  for (int A = 0; A < e->g->nagg; ++A)
+    for (int i = 0; i < nc; ++i) {
+      const size_t k = (size_t)A * nc + i;
+      out[k] = aggregate_colour(e->g, A) == 0 ? e->t[k] - out[k] : 0;
+    }
+}
+
+/* the inverse self blocks of the odd aggregates (NULL if one is singular) */
+static cplx* odd_self_inverses(const geom_t* g, int ntv, const cplx* Dc) {
+  const int nc = 2 * ntv;
+  cplx* Dinv = (cplx*)calloc((size_t)g->nagg * nc * nc, sizeof(cplx));
+  int bad = 0;
+  for (int A = 0; A < g->nagg && !bad; ++A)
+    if (aggregate_colour(g, A) == 1)
+      bad = invert_n(nc, Dc + (size_t)A * 9 * nc * nc, Dinv + (size_t)A * nc * nc) != 0;
+  if (bad) {
+    free(Dinv);
+    return NULL;
+  }
+  return Dinv;
+}
+
+/* x = D_c^-1 b approximately, on the Schur complement (one right-hand side);
+ * returns the GMRES iteration count, or -1 when a self block is singular */
+static int coarse_solve_eo_one(const geom_t* g, int ntv, const cplx* Dc, const cplx* Dinv, const cplx* b, cplx* x,
+                               double tol, int restart, int maxit) {
+  const int nc = 2 * ntv;
+  const size_t n = (size_t)g->nagg * nc;
+  cplx* t = (cplx*)malloc(sizeof(cplx) * n);
+  cplx* u = (cplx*)malloc(sizeof(cplx) * n);
+  cplx* bh = (cplx*)malloc(sizeof(cplx) * n);
+  cplx* s = (cplx*)malloc(sizeof(cplx) * n);
+  coarse_eo_ctx e = {g, ntv, Dc, Dinv, t, u};
+  /* bhat_e = b_e - D_eo D_oo^-1 b_o */
+  odd_block_inverse(&e, b, u);
+  apply_Dc_one(g, ntv, Dc, u, s);
+  for (int A = 0; A < g->nagg; ++A)
+    for (int i = 0; i < nc; ++i) {
+      const size_t k = (size_t)A * nc + i;
+      bh[k] = aggregate_colour(g, A) == 0 ? b[k] - s[k] : 0;
+    }
+  int it = gmres(coarse_schur_op, &e, NULL, NULL, n, bh, x, tol, restart, maxit, NULL);
+  /* x_o = D_oo^-1 (b_o - D_oe x_e) */
+  apply_Dc_one(g, ntv, Dc, x, s);
+  for (int A = 0; A < g->nagg; ++A)
+    for (int i = 0; i < nc; ++i) {
+      const size_t k = (size_t)A * nc + i;
+      s[k] = aggregate_colour(g, A) == 1 ? b[k] - s[k] : 0;
+    }
+  odd_block_inverse(&e, s, u);
+  for (int A = 0; A < g->nagg; ++A)
+    if (aggregate_colour(g, A) == 1)
+      for (int i = 0; i < nc; ++i) x[(size_t)A * nc + i] = u[(size_t)A * nc + i];
+  free(t);
+  free(u);
+  free(bh);
+  free(s);
+  return it;
+}
+
+int ora_coarse_solve_eo(const int* dims, const int* agg, int ntv, const cplx* Dc, const cplx* bc, cplx* xc,
+                        int nrhs, double tol, int restart, int maxit, int* iters) {
+  geom_t g;
+  if (geom_init(&g, dims, agg)) return -1;
+  cplx* Dinv = odd_self_inverses(&g, ntv, Dc);
+  if (!Dinv) return -6;
+  size_t nc = (size_t)g.nagg * 2 * ntv;
+  for (int r = 0; r < nrhs; ++r) {
+    int it = coarse_solve_eo_one(&g, ntv, Dc, Dinv, bc + r * nc, xc + r * nc, tol, restart, maxit);
+    if (iters) iters[r] = it;
+  }
+  free(Dinv);
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
 /* the setup (Algorithm 1 order, one test vector at a time)              */
 /* ------------------------------------------------------------------ */
 typedef struct {
@@ -1049,6 +1201,7 @@ typedef struct {
   double coarse_tol;
   int coarse_restart, coarse_maxit;
   int even_odd;         /* 1: even-odd preconditioned domain solves in the smoother */
+  int coarse_even_odd;  /* 1: coarse solves on the Schur complement of the even aggregates */
 } ora_setup_params;
 
 static void normalise(cplx* v, size_t n) {
@@ -1112,11 +1265,22 @@ int ora_setup_refine(const int* dims, const int* agg, int ntv, const cplx* U, co
   coarse_ctx cc = {&g, ntv, Dc};
   int st = 0;
   for (int i = 0; i < p->n_refine; ++i) {
+    cplx* Dinv = NULL;
+    if (p->coarse_even_odd) {
+      Dinv = odd_self_inverses(&g, ntv, Dc);
+      if (!Dinv) {
+        st = -6;
+        break;
+      }
+    }
     for (int j = 0; j < ntv; ++j) {
       cplx* v = tv + j * n;
       restrict_one(&g, ntv, P, v, vc);
-      int it = gmres(coarse_op, &cc, NULL, NULL, nc, vc, uc, p->coarse_tol, p->coarse_restart,
-                     p->coarse_maxit, NULL);
+      int it = p->coarse_even_odd
+                   ? coarse_solve_eo_one(&g, ntv, Dc, Dinv, vc, uc, p->coarse_tol, p->coarse_restart,
+                                         p->coarse_maxit)
+                   : gmres(coarse_op, &cc, NULL, NULL, nc, vc, uc, p->coarse_tol, p->coarse_restart,
+                           p->coarse_maxit, NULL);
       if (coarse_iters) coarse_iters[i * ntv + j] = it;
       prolong_one(&g, ntv, P, uc, x);
       st = smooth(&g, sites, U, A, Ainv, v, x, p->n_smooth_sweeps, p->n_smooth_mr, p->even_odd);
@@ -1124,6 +1288,7 @@ int ora_setup_refine(const int* dims, const int* agg, int ntv, const cplx* U, co
       memcpy(v, x, sizeof(cplx) * n);
       normalise(v, n);
     }
+    free(Dinv);
     if (st) break;
     st = ora_gram_schmidt(dims, agg, ntv, tv, P);
     if (st) break;
@@ -1145,8 +1310,8 @@ typedef struct {
   geom_t g;
   const int* sites;
   int ntv;
-  const cplx *U, *A, *P, *Dc, *Ainv;
-  int even_odd;
+  const cplx *U, *A, *P, *Dc, *Ainv, *Dinv;
+  int even_odd, coarse_even_odd;
   double coarse_tol;
   int coarse_restart, coarse_maxit, n_sweeps, n_mr;
   cplx *rc, *uc;
@@ -1167,7 +1332,11 @@ static void vcycle(void* c, const cplx* r, cplx* z) {
   coarse_ctx cc = {&m->g, m->ntv, m->Dc};
   size_t nc = (size_t)m->g.nagg * 2 * m->ntv;
   restrict_one(&m->g, m->ntv, m->P, r, m->rc);
-  gmres(coarse_op, &cc, NULL, NULL, nc, m->rc, m->uc, m->coarse_tol, m->coarse_restart, m->coarse_maxit, NULL);
+  if (m->coarse_even_odd)
+    coarse_solve_eo_one(&m->g, m->ntv, m->Dc, m->Dinv, m->rc, m->uc, m->coarse_tol, m->coarse_restart,
+                        m->coarse_maxit);
+  else
+    gmres(coarse_op, &cc, NULL, NULL, nc, m->rc, m->uc, m->coarse_tol, m->coarse_restart, m->coarse_maxit, NULL);
   prolong_one(&m->g, m->ntv, m->P, m->uc, z);
   smooth(&m->g, m->sites, m->U, m->A, m->Ainv, r, z, m->n_sweeps, m->n_mr, m->even_odd);
 }
@@ -1175,7 +1344,7 @@ static void vcycle(void* c, const cplx* r, cplx* z) {
 int ora_fgmres(const int* dims, const int* agg, int ntv, const cplx* U, const cplx* A,
                const cplx* P, const cplx* Dc, const cplx* b, cplx* x, double tol, int restart,
                int maxit, double coarse_tol, int coarse_restart, int coarse_maxit, int n_sweeps,
-               int n_mr, int even_odd, int* iters, double* relres) {
+               int n_mr, int even_odd, int coarse_even_odd, int* iters, double* relres) {
   mg_ctx m;
   if (geom_init(&m.g, dims, agg)) return -1;
   init_gammas();
@@ -1183,7 +1352,11 @@ int ora_fgmres(const int* dims, const int* agg, int ntv, const cplx* U, const cp
   m.sites = sites;
   m.even_odd = even_odd;
   m.Ainv = even_odd ? clover_inverses(&m.g, A) : NULL;
-  if (even_odd && !m.Ainv) {
+  m.coarse_even_odd = coarse_even_odd;
+  m.Dinv = coarse_even_odd ? odd_self_inverses(&m.g, ntv, Dc) : NULL;
+  if ((even_odd && !m.Ainv) || (coarse_even_odd && !m.Dinv)) {
+    free((void*)m.Ainv);
+    free((void*)m.Dinv);
     free(sites);
     return -6;
   }
@@ -1206,6 +1379,7 @@ int ora_fgmres(const int* dims, const int* agg, int ntv, const cplx* U, const cp
   free(m.rc);
   free(m.uc);
   free((void*)m.Ainv);
+  free((void*)m.Dinv);
   free(sites);
   return 0;
 }

@@ -556,6 +556,54 @@ def test_fgmres_first_step_is_the_preconditioned_minimal_residual_step():
     assert abs(rr - np.linalg.norm(bb - D @ ref) / np.linalg.norm(bb)) < 1e-9
 
 
+def _coarse_c1():
+    dims, agg, ntv = C1["dims"], C1["agg"], 4
+    U, A = c1_field()
+    _, P, Dc = oracle.setup_init(dims, agg, U, A, inputs.test_vectors(ntv, dims, 98), oracle.make_params())
+    Dd = dense_coarse(dims, agg, Dc)
+    nb = [d // a for d, a in zip(dims, agg)]
+    nagg = int(np.prod(nb))
+    colour = np.stack(np.unravel_index(np.arange(nagg), nb[::-1]), axis=1)[:, ::-1].sum(axis=1) % 2
+    row_colour = np.repeat(colour, 2 * ntv)
+    return dims, agg, ntv, Dc, Dd, row_colour
+
+
+def test_coarse_even_odd_solve_converges_to_the_dense_solve():
+    """The coarse solve on the Schur complement of the even aggregates, then
+    the odd ones, reaches D_c^-1 b (the hop blocks join aggregates of
+    different colour, so the even-odd split is exact)."""
+    dims, agg, ntv, Dc, Dd, _ = _coarse_c1()
+    bc = inputs.gaussian_field((2, Dd.shape[0] // (2 * ntv), 2 * ntv), 99)
+    xc, its = oracle.coarse_solve_eo(dims, agg, Dc, bc, 1e-13, 40, 4000)
+    for r in range(2):
+        xd = np.linalg.solve(Dd, bc[r].reshape(-1))
+        assert np.abs(xc[r].reshape(-1) - xd).max() < 1e-10 * np.abs(xd).max()
+    assert (its > 0).all()
+
+
+def test_coarse_even_odd_one_iteration_is_the_schur_minimal_residual_step():
+    """One GMRES iteration from zero on S = D_ee - D_eo D_oo^-1 D_oe with the
+    right side bhat = b_e - D_eo D_oo^-1 b_o gives x_e = alpha bhat, alpha
+    minimising |bhat - alpha S bhat|; then x_o = D_oo^-1 (b_o - D_oe x_e).
+    Written with the dense D_c split by aggregate colour."""
+    dims, agg, ntv, Dc, Dd, rc = _coarse_c1()
+    E, O = np.where(rc == 0)[0], np.where(rc == 1)[0]
+    assert np.abs(Dd[np.ix_(E, E)] - np.diag(np.diag(Dd[np.ix_(E, E)]))).max() > 0  # self blocks are dense
+    bc = inputs.gaussian_field((1, Dd.shape[0] // (2 * ntv), 2 * ntv), 100)
+    b = bc[0].reshape(-1)
+    Doo_inv = np.linalg.inv(Dd[np.ix_(O, O)])
+    S = Dd[np.ix_(E, E)] - Dd[np.ix_(E, O)] @ Doo_inv @ Dd[np.ix_(O, E)]
+    bh = b[E] - Dd[np.ix_(E, O)] @ (Doo_inv @ b[O])
+    q = S @ bh
+    xE = (np.vdot(q, bh) / np.vdot(q, q)) * bh
+    xO = Doo_inv @ (b[O] - Dd[np.ix_(O, E)] @ xE)
+    xc, its = oracle.coarse_solve_eo(dims, agg, Dc, bc, 0.0, 10, 1)
+    x = xc[0].reshape(-1)
+    assert its[0] == 1
+    assert np.abs(x[E] - xE).max() < 1e-12 * np.abs(xE).max()
+    assert np.abs(x[O] - xO).max() < 1e-12 * np.abs(xO).max()
+
+
 def test_setup_gauge_invariance():
     """U -> U^Om and tv -> Om tv leave D_c unchanged and map P -> Om P."""
     dims, agg, ntv = C1["dims"], C1["agg"], 4
