@@ -245,9 +245,27 @@ int mrhs_apply_Dc(mrhs_ctx ctx, const void* xc, void* yc, int nrhs, int dtype);
  * once, each with its own Krylov space; a right-hand side stops when its
  * residual estimate reaches tol*|bc| or after maxit iterations in total.
  * tol = 0 gives exactly maxit iterations. iters (host, may be NULL)
- * receives the iteration count of every right-hand side. */
+ * receives the iteration count of every right-hand side. With the even-odd
+ * coarse solver (mrhs_set_coarse_solver) the GMRES runs on the Schur
+ * complement instead and the tolerance applies to its right-hand side. */
 int mrhs_coarse_solve(mrhs_ctx ctx, const void* bc, void* xc, int nrhs, int dtype, double tol, int restart,
                       int maxit, int* iters);
+
+/* Coarse solver of every coarse solve (mrhs_coarse_solve, the refinement
+ * phase, the V-cycle of mrhs_solve_fgmres). even_odd = 0 (default): GMRES on
+ * D_c. even_odd = 1: even-odd preconditioning of the coarse system (Sec. 4,
+ * Eq. 1): the aggregates take the red-black colour of their SAP domains, so
+ * every hop block of D_c joins aggregates of different colour and D_ee, D_oo
+ * are block diagonal (the self blocks); GMRES runs on
+ *   S x_e = b_e - D_eo D_oo^-1 b_o,   S = D_ee - D_eo D_oo^-1 D_oe,
+ * from x_e = 0 (the odd rows of the Krylov vectors stay zero), then
+ * x_o = D_oo^-1 (b_o - D_oe x_e). The inverse self blocks of the odd
+ * aggregates are built in the work precision on the first solve after each
+ * build of D_c (MRHS_ERR_NONFINITE if one is singular, MRHS_ERR_SHAPE if a
+ * 2ntv x 4ntv block does not fit in shared memory). The setting does not
+ * apply to mrhs_coarse_solve_noalloc, which always solves on D_c.
+ * MRHS_ERR_ARG unless even_odd is 0 or 1. */
+int mrhs_set_coarse_solver(mrhs_ctx ctx, int even_odd);
 
 /* The same coarse solve without any allocation. The paper has no counterpart:
  * this entry point is for callers that cannot let the library call
@@ -256,7 +274,9 @@ int mrhs_coarse_solve(mrhs_ctx ctx, const void* bc, void* xc, int nrhs, int dtyp
  * a solve, or no allocation allowed after start-up). The Krylov basis, the
  * GMRES state and the reduction partials live in one fixed 64 MiB device
  * array inside the library (held by every GPU that loads the library until
- * the process exits); results equal those of mrhs_coarse_solve.
+ * the process exits); results equal those of mrhs_coarse_solve with the
+ * default coarse solver (GMRES on D_c, whatever mrhs_set_coarse_solver
+ * says).
  * - MRHS_ERR_SHAPE (with the needed size in mrhs_last_error) when the
  *   problem needs more than 64 MiB: (restart + 2) coarse fields of nrhs
  *   right-hand sides plus the GMRES state and partials.

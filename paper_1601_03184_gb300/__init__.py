@@ -64,6 +64,7 @@ _SIGS = {
     "mrhs_setup_refine": (_I, [_VP, _I, _I, _I, _D, _I, _I, _VP]),
     "mrhs_set_block_length": (_I, [_VP, _I]),
     "mrhs_set_smoother": (_I, [_VP, _I]),
+    "mrhs_set_coarse_solver": (_I, [_VP, _I]),
     "mrhs_setup_update": (_I, [_VP, _I, _I, _I, _D, _I, _I, _VP]),
     "mrhs_get_tv": (_I, [_VP, _VP, _I]),
     "mrhs_get_P": (_I, [_VP, _VP, _I]),
@@ -364,6 +365,10 @@ def mrhs_setup_update(ctx, n_iter, n_sweeps, n_mr, coarse_tol, coarse_restart, c
 
 def mrhs_set_smoother(ctx, even_odd):
     return _check(ctx, lib().mrhs_set_smoother(ctx, int(even_odd)))
+
+
+def mrhs_set_coarse_solver(ctx, even_odd):
+    return _check(ctx, lib().mrhs_set_coarse_solver(ctx, int(even_odd)))
 
 
 def mrhs_set_block_length(ctx, nb):

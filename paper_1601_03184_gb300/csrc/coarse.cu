@@ -744,11 +744,205 @@ void apply_Dc(mrhs_ctx c, const void* xc, void* yc, int nrhs, int dtype) {
   MRHS_LAUNCH_CHECK("apply_dc");
 }
 
-void coarse_solve(mrhs_ctx c, const void* bc, void* xc, int N, int dtype, double tol, int m, int maxit, int* iters) {
-  MRHS_REQUIRE(c->have_Dc, MRHS_ERR_STATE, "coarse solve before mrhs_build_Dc");
-  MRHS_REQUIRE(dtype == c->work_dtype, MRHS_ERR_ARG, "coarse solve: dtype must be the context's work type");
-  MRHS_REQUIRE(N >= 1 && N <= 256 && m >= 1 && m <= 64 && maxit >= 0 && tol >= 0, MRHS_ERR_ARG,
-               "coarse solve: need 1 <= nrhs <= 256, 1 <= restart <= 64, maxit >= 0, tol >= 0");
+// ------------------------------------------------------------------------
+// Even-odd preconditioned coarse solve. The aggregates carry the red-black
+// colour of the SAP domains and every hop block of D_c joins aggregates of
+// different colour, so D_c = [[D_ee, D_eo], [D_oe, D_oo]] with block-diagonal
+// D_ee, D_oo (the self blocks). GMRES runs on S = D_ee - D_eo D_oo^-1 D_oe
+// (even aggregates; the odd rows of every vector stay zero), then
+// x_o = D_oo^-1 (b_o - D_oe x_e).
+namespace {
+struct NbArgs {
+  int nb[4];
+};
+__device__ __forceinline__ int agg_colour(const NbArgs& g, int A) {
+  int s = 0;
+  for (int m = 0; m < 4; ++m) {
+    s += A % g.nb[m];
+    A /= g.nb[m];
+  }
+  return s & 1;
+}
+
+// the inverse of the self block of every odd aggregate (one CTA each, the
+// list of odd aggregates in blist), Gauss-Jordan with partial pivoting on
+// [D | 1] in shared memory; *bad set for a singular block
+template <class R>
+__global__ void k_self_inverse(const cx<R>* __restrict__ Dc, cx<R>* __restrict__ Dinv, const int* __restrict__ blist,
+                               int nc, int* bad) {
+  extern __shared__ double smem_d[];
+  cx<R>* m = (cx<R>*)smem_d;  // [nc][2nc]
+  __shared__ cx<R> s_f[128];
+  __shared__ int s_p;
+  const int A = blist[blockIdx.x];
+  const int w2 = 2 * nc;
+  const cx<R>* S = Dc + (size_t)A * 9 * nc * nc;
+  for (int e = threadIdx.x; e < nc * w2; e += blockDim.x) {
+    const int i = e / w2, j = e % w2;
+    m[e] = j < nc ? S[i * nc + j] : mk<R>(j - nc == i ? (R)1 : (R)0, 0);
+  }
+  __syncthreads();
+  for (int col = 0; col < nc; ++col) {
+    if (threadIdx.x == 0) {
+      int p = col;
+      R best = m[col * w2 + col].re * m[col * w2 + col].re + m[col * w2 + col].im * m[col * w2 + col].im;
+      for (int i = col + 1; i < nc; ++i) {
+        const cx<R> v = m[i * w2 + col];
+        const R a = v.re * v.re + v.im * v.im;
+        if (a > best) best = a, p = i;
+      }
+      s_p = best > 0 ? p : -1;
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (p < 0) {
+      if (threadIdx.x == 0) atomicExch(bad, 1);
+      return;
+    }
+    if (p != col)
+      for (int j = threadIdx.x; j < w2; j += blockDim.x) {
+        const cx<R> t = m[p * w2 + j];
+        m[p * w2 + j] = m[col * w2 + j];
+        m[col * w2 + j] = t;
+      }
+    __syncthreads();
+    const cx<R> piv = m[col * w2 + col];
+    const R pn = piv.re * piv.re + piv.im * piv.im;
+    const cx<R> pinv = mk<R>(piv.re / pn, -piv.im / pn);
+    __syncthreads();
+    for (int j = threadIdx.x; j < w2; j += blockDim.x) m[col * w2 + j] = m[col * w2 + j] * pinv;
+    for (int i = threadIdx.x; i < nc; i += blockDim.x) s_f[i] = m[i * w2 + col];
+    __syncthreads();
+    for (int e = threadIdx.x; e < nc * w2; e += blockDim.x) {
+      const int i = e / w2, j = e % w2;
+      if (i != col) m[e] = m[e] - s_f[i] * m[col * w2 + j];
+    }
+    __syncthreads();
+  }
+  cx<R>* out = Dinv + (size_t)A * nc * nc;
+  for (int e = threadIdx.x; e < nc * nc; e += blockDim.x) out[e] = m[(e / nc) * w2 + nc + e % nc];
+}
+
+// y[A] = D_oo^-1 x[A] on the odd aggregates, 0 on the even ones
+template <class S, class R>
+__global__ void k_odd_inverse_mul(const cx<R>* __restrict__ Dinv, const S* __restrict__ x, S* __restrict__ y, int nc,
+                                  int N, size_t nwork, NbArgs g) {
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= nwork) return;
+  const int r = (int)(t % N);
+  const size_t row = t / N;  // A * nc + i
+  const int A = (int)(row / nc), i = (int)(row % nc);
+  cx<R> acc = mk<R>(0, 0);
+  if (agg_colour(g, A) == 1) {
+    const cx<R>* M = Dinv + ((size_t)A * nc + i) * nc;
+    for (int j = 0; j < nc; ++j) fma_(acc, M[j], ld<S, R>(x, (size_t)A * nc + j, N, r));
+  }
+  st<S, R>(y, row, N, r, acc);
+}
+
+// out = a - b on the rows of aggregates of colour `keep`, 0 elsewhere
+template <class S, class R>
+__global__ void k_colour_sub(const S* __restrict__ a, const S* __restrict__ b, S* __restrict__ out, int nc, int N,
+                             int keep, size_t nwork, NbArgs g) {
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= nwork) return;
+  const int r = (int)(t % N);
+  const size_t row = t / N;
+  const int A = (int)(row / nc);
+  const cx<R> v = agg_colour(g, A) == keep ? ld<S, R>(a, row, N, r) - ld<S, R>(b, row, N, r) : mk<R>(0, 0);
+  st<S, R>(out, row, N, r, v);
+}
+
+// dst = src on the rows of odd aggregates (even rows untouched)
+template <class S>
+__global__ void k_copy_odd(const S* __restrict__ src, S* __restrict__ dst, int nc, int N, size_t nwork, NbArgs g) {
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= nwork) return;
+  const size_t row = t / (2 * N);
+  if (agg_colour(g, (int)(row / nc)) == 1) dst[t] = src[t];
+}
+}  // namespace
+
+// the inverse self blocks of the odd aggregates for the current D_c
+static void ensure_self_inverses(mrhs_ctx c) {
+  const int nc = 2 * c->ntv;
+  MRHS_REQUIRE(nc <= 128, MRHS_ERR_SHAPE, "even-odd coarse solve: 2 ntv must be at most 128");
+  if (c->dc_inv && c->dc_inv_version == c->dc_version) return;
+  const size_t es = c->work_dtype == MRHS_F64 ? sizeof(cx<double>) : sizeof(cx<float>);
+  if (!c->dc_inv) c->dc_inv = dalloc(c, (size_t)c->g.nagg * nc * nc * es);
+  const size_t smem = (size_t)nc * 2 * nc * es;
+  int optin = 0;
+  MRHS_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+  MRHS_REQUIRE(smem <= (size_t)optin, MRHS_ERR_SHAPE,
+               "even-odd coarse solve: a self block of this size does not fit in shared memory");
+  MRHS_CUDA(cudaMemsetAsync(c->dflag + 5, 0, sizeof(int), c->stream));
+  const int* odd = c->blocks_col + c->ncol[0];
+  Prof pr(c, "self_inverse");
+  if (c->work_dtype == MRHS_F64) {
+    MRHS_CUDA(cudaFuncSetAttribute(k_self_inverse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_self_inverse<double><<<c->ncol[1], 256, smem, c->stream>>>((const cx<double>*)c->Dc, (cx<double>*)c->dc_inv,
+                                                                 odd, nc, c->dflag + 5);
+  } else {
+    MRHS_CUDA(cudaFuncSetAttribute(k_self_inverse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_self_inverse<float><<<c->ncol[1], 256, smem, c->stream>>>((const cx<float>*)c->Dc, (cx<float>*)c->dc_inv, odd,
+                                                                nc, c->dflag + 5);
+  }
+  MRHS_LAUNCH_CHECK("self_inverse");
+  MRHS_CUDA(cudaMemcpyAsync(c->hflag + 5, c->dflag + 5, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  MRHS_CUDA(cudaStreamSynchronize(c->stream));
+  MRHS_REQUIRE(c->hflag[5] == 0, MRHS_ERR_NONFINITE, "even-odd coarse solve: a self block of D_c is singular");
+  c->dc_inv_version = c->dc_version;
+}
+
+namespace {
+NbArgs nb_args(mrhs_ctx c) {
+  NbArgs g;
+  for (int m = 0; m < 4; ++m) g.nb[m] = c->g.nb[m];
+  return g;
+}
+void odd_inverse_mul(mrhs_ctx c, const void* x, void* y, int N, int dtype) {
+  const int nc = 2 * c->ntv;
+  const size_t work = (size_t)c->g.nagg * nc * N;
+  if (dtype == MRHS_F64)
+    k_odd_inverse_mul<double, double><<<grid_for(work, 256), 256, 0, c->stream>>>(
+        (const cx<double>*)c->dc_inv, (const double*)x, (double*)y, nc, N, work, nb_args(c));
+  else
+    k_odd_inverse_mul<float, float><<<grid_for(work, 256), 256, 0, c->stream>>>(
+        (const cx<float>*)c->dc_inv, (const float*)x, (float*)y, nc, N, work, nb_args(c));
+  MRHS_LAUNCH_CHECK("odd_inverse_mul");
+}
+void colour_sub(mrhs_ctx c, const void* a, const void* b, void* out, int N, int dtype, int keep) {
+  const int nc = 2 * c->ntv;
+  const size_t work = (size_t)c->g.nagg * nc * N;
+  if (dtype == MRHS_F64)
+    k_colour_sub<double, double><<<grid_for(work, 256), 256, 0, c->stream>>>((const double*)a, (const double*)b,
+                                                                            (double*)out, nc, N, keep, work, nb_args(c));
+  else
+    k_colour_sub<float, float><<<grid_for(work, 256), 256, 0, c->stream>>>((const float*)a, (const float*)b,
+                                                                          (float*)out, nc, N, keep, work, nb_args(c));
+  MRHS_LAUNCH_CHECK("colour_sub");
+}
+}  // namespace
+
+// y = S x = D_ee x_e - D_eo D_oo^-1 D_oe x_e for x zero on the odd rows; t and
+// u: two work fields of the coarse size
+static void apply_schur(mrhs_ctx c, const void* x, void* y, void* t, void* u, int N, int dtype) {
+  apply_Dc(c, x, t, N, dtype);      // even rows D_ee x_e, odd rows D_oe x_e
+  odd_inverse_mul(c, t, u, N, dtype);
+  apply_Dc(c, u, y, N, dtype);      // even rows D_eo u_o
+  colour_sub(c, t, y, y, N, dtype, 0);
+}
+
+// restarted GMRES on D_c, or on the Schur complement S when tu holds its two
+// work fields (then bc and xc are zero on the odd aggregates)
+static void coarse_gmres(mrhs_ctx c, const void* bc, void* xc, int N, int dtype, double tol, int m, int maxit,
+                         int* iters, void* const* tu) {
+  auto op = [&](const void* x, void* y) {
+    if (tu)
+      apply_schur(c, x, y, tu[0], tu[1], N, dtype);
+    else
+      apply_Dc(c, x, y, N, dtype);
+  };
   const size_t rows = (size_t)c->g.nagg * 2 * c->ntv;
   const size_t fe = rows * 2 * N;  // elements of one coarse field
   const size_t es = dtype_size(dtype);
@@ -790,7 +984,7 @@ void coarse_solve(mrhs_ctx c, const void* bc, void* xc, int N, int dtype, double
   k_gm_init<<<grid_for(N, 64), 64, 0, c->stream>>>(st, N);
   MRHS_LAUNCH_CHECK("gm_init");
   for (;;) {
-    apply_Dc(c, xc, w, N, dtype);
+    op(xc, w);
     MRHS_DISPATCH(dtype, S, (k_sub_from<S><<<grid_for(fe, 256), 256, 0, c->stream>>>((const S*)bc, (S*)w, fe)));
     MRHS_LAUNCH_CHECK("sub_from");
     norms(c, w, rows, N, dtype, st.beta2);
@@ -801,7 +995,7 @@ void coarse_solve(mrhs_ctx c, const void* bc, void* xc, int N, int dtype, double
     scale_into(w, Vk(0));
     int kmax = 0;
     for (int k = 0; k < m; ++k) {
-      apply_Dc(c, Vk(k), w, N, dtype);
+      op(Vk(k), w);
       multi_dot(c, Vk(0), fe, k + 1, w, rows, N, dtype, st.h1);
       multi_axpy(c, Vk(0), fe, k + 1, w, rows, N, dtype, st.h1, -1.0);
       multi_dot(c, Vk(0), fe, k + 1, w, rows, N, dtype, st.h2);
@@ -824,6 +1018,35 @@ void coarse_solve(mrhs_ctx c, const void* bc, void* xc, int N, int dtype, double
     MRHS_CUDA(cudaStreamSynchronize(c->stream));
   }
   check_tc_timeout(c);
+}
+
+void coarse_solve(mrhs_ctx c, const void* bc, void* xc, int N, int dtype, double tol, int m, int maxit, int* iters) {
+  MRHS_REQUIRE(c->have_Dc, MRHS_ERR_STATE, "coarse solve before mrhs_build_Dc");
+  MRHS_REQUIRE(dtype == c->work_dtype, MRHS_ERR_ARG, "coarse solve: dtype must be the context's work type");
+  MRHS_REQUIRE(N >= 1 && N <= 256 && m >= 1 && m <= 64 && maxit >= 0 && tol >= 0, MRHS_ERR_ARG,
+               "coarse solve: need 1 <= nrhs <= 256, 1 <= restart <= 64, maxit >= 0, tol >= 0");
+  if (!c->coarse_eo) {
+    coarse_gmres(c, bc, xc, N, dtype, tol, m, maxit, iters, nullptr);
+    return;
+  }
+  ensure_self_inverses(c);
+  const size_t fb = (size_t)c->g.nagg * 2 * c->ntv * 2 * N * dtype_size(dtype);
+  char* wk = (char*)scratch(c, SC_COARSE_EO, 3 * fb);
+  void* tu[2] = {wk, wk + fb};
+  void* bh = wk + 2 * fb;
+  // bhat_e = b_e - D_eo D_oo^-1 b_o
+  odd_inverse_mul(c, bc, tu[1], N, dtype);
+  apply_Dc(c, tu[1], tu[0], N, dtype);
+  colour_sub(c, bc, tu[0], bh, N, dtype, 0);
+  coarse_gmres(c, bh, xc, N, dtype, tol, m, maxit, iters, tu);
+  // x_o = D_oo^-1 (b_o - D_oe x_e)
+  apply_Dc(c, xc, tu[0], N, dtype);
+  colour_sub(c, bc, tu[0], tu[0], N, dtype, 1);
+  odd_inverse_mul(c, tu[0], tu[1], N, dtype);
+  const size_t work = (size_t)c->g.nagg * 2 * c->ntv * 2 * N;
+  MRHS_DISPATCH(dtype, S, (k_copy_odd<S><<<grid_for(work, 256), 256, 0, c->stream>>>((const S*)tu[1], (S*)xc,
+                                                                                     2 * c->ntv, N, work, nb_args(c))));
+  MRHS_LAUNCH_CHECK("copy_odd");
 }
 
 // ------------------------------------------------------------------------
@@ -988,6 +1211,14 @@ int mrhs_apply_Dc(mrhs_ctx c, const void* xc, void* yc, int nrhs, int dtype) {
     require_dev(c, yc, "mrhs_apply_Dc yc");
     MRHS_REQUIRE(nrhs >= 1, MRHS_ERR_ARG, "nrhs must be >= 1");
     apply_Dc(c, xc, yc, nrhs, dtype);
+  });
+}
+
+int mrhs_set_coarse_solver(mrhs_ctx c, int even_odd) {
+  return guarded(c, [&] {
+    MRHS_REQUIRE(c, MRHS_ERR_ARG, "null context");
+    MRHS_REQUIRE(even_odd == 0 || even_odd == 1, MRHS_ERR_ARG, "even_odd must be 0 or 1");
+    c->coarse_eo = even_odd;
   });
 }
 

@@ -204,6 +204,9 @@ struct mrhs_ctx_s {
   void* dc_img = nullptr;          // D_c as tensor-core operand images (coarse_tc.cu)
   long long dc_img_version = -1;   // the D_c version the images hold
   int dc_img_split = -1;           // 1: tf32 hi + lo images, 0: tf32 only
+  void* dc_inv = nullptr;          // [nagg][2ntv][2ntv] inverse self blocks of the odd aggregates
+  long long dc_inv_version = -1;   // the D_c version dc_inv holds
+  int coarse_eo = 0;               // 1: coarse GMRES on the Schur complement of the even aggregates
   bool have_tv = false, have_P = false, have_Dc = false;
   // the setup stores its (unit-norm) test vectors multiplied by tv_scale:
   // sqrt(12 V) for fp16 storage (entries of order 1, inside the fp16 range),
@@ -252,6 +255,7 @@ enum Scratch {
   SC_BLOCK,       // one block of test vectors (block length N_b < ntv)
   SC_EO1,         // even-odd domain solves: rho (even sites) / A^-1 H rho (odd sites)
   SC_EO2,         // q (even) and e (both parities), interleaved as two fields
+  SC_COARSE_EO,   // even-odd coarse solve: two operator work fields and bhat
   SC_COUNT
 };
 

@@ -12,7 +12,8 @@ from . import (MRHS_F32, MRHS_F64, MRHS_PREC_FP64, mrhs_apply_D, mrhs_apply_D_bl
                mrhs_set_dc_engine,
                mrhs_field_bytes, mrhs_get_clover, mrhs_get_Dc, mrhs_get_P, mrhs_get_tables, mrhs_get_tv,
                mrhs_info, mrhs_load_setup, mrhs_pack, mrhs_pack_coarse, mrhs_prolong, mrhs_restrict, mrhs_sap,
-               mrhs_save_setup, mrhs_set_block_length, mrhs_set_gauge, mrhs_set_smoother,
+               mrhs_save_setup, mrhs_set_block_length, mrhs_set_coarse_solver, mrhs_set_gauge,
+               mrhs_set_smoother,
                mrhs_setup_update,
                mrhs_set_tv, mrhs_setup_init, mrhs_setup_refine, mrhs_solve_fgmres, mrhs_sync, mrhs_unpack,
                mrhs_unpack_coarse)
@@ -140,6 +141,10 @@ class Lattice:
     def set_smoother(self, even_odd):
         """1: even-odd preconditioned SAP domain solves, 0: plain"""
         mrhs_set_smoother(self.ctx, even_odd)
+
+    def set_coarse_solver(self, even_odd):
+        """1: coarse GMRES on the Schur complement of the even aggregates, 0: on D_c"""
+        mrhs_set_coarse_solver(self.ctx, even_odd)
 
     def set_block_length(self, nb):
         """N_b of Algorithm 2 for the setup phases (0: all test vectors at once)"""
