@@ -297,6 +297,8 @@ def run_ours(args, cfg, cfg_name, m0, m0_src, rank, world, local_rank):
     lat = Lattice(dims, agg, N, MRHS_PREC_FP32, stream.cuda_stream)
     lat.set_gauge(U)
     lat.build_clover(m0, cfg["csw"])
+    lat.set_smoother(args.smoother_eo)
+    lat.set_coarse_solver(args.coarse_eo)
     # test vectors: complex Gaussian, drawn on the device directly in the library layout
     gen = torch.Generator(device="cuda")
     gen.manual_seed(cfg["tvseed"] + rank)
@@ -434,6 +436,8 @@ def run_ours(args, cfg, cfg_name, m0, m0_src, rank, world, local_rank):
         "data": "synthetic",
         "config": {"workload": cfg_name, "ntv": N, "precision": "fp32 (plain setup)", "m0": round(m0, 6),
                    "m0_source": m0_src, "csw": cfg["csw"], "roughness": cfg["eps"],
+                   "smoother": "even-odd" if args.smoother_eo else "plain",
+                   "coarse_solver": "even-odd" if args.coarse_eo else "plain",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (test vectors %.1f GB)" % (nb / 1e9)},
         "roofline": roof,
@@ -552,8 +556,9 @@ def run_learned_mixed(args, cfg, U, m0, stream, plain_ms, barrier, dist=None, wo
     from paper_1601_03184_gb300 import (MRHS_F32, MRHS_PREC_FP32, MRHS_PREC_MIX_BF16, Lattice, inputs, learned)
 
     t0 = time.perf_counter()
+    widths = (4, args.learned_width, args.learned_width, 4) if args.learned_width else learned.WIDTHS
     small = Lattice((16, 16, 16, 16), cfg["agg"], 8, MRHS_PREC_FP32, stream.cuda_stream)
-    learned.attach(small, learned.WIDTHS, seed=17, noise=0.01, bf16=True)
+    learned.attach(small, widths, seed=17, noise=0.01, bf16=True)
     sched = dict(init_sweeps=SCHEDULE["init_sweeps"], init_mr=SCHEDULE["init_mr"], n_refine=1,
                  sweeps=SCHEDULE["smooth_sweeps"], mr=SCHEDULE["smooth_mr"], ctol=SCHEDULE["coarse_tol"],
                  crestart=SCHEDULE["coarse_restart"], cmaxit=SCHEDULE["coarse_maxit"])
@@ -572,7 +577,7 @@ def run_learned_mixed(args, cfg, U, m0, stream, plain_ms, barrier, dist=None, wo
     lat = Lattice(dims, cfg["agg"], N, MRHS_PREC_MIX_BF16, stream.cuda_stream)
     lat.set_gauge(U)
     lat.build_clover(m0, cfg["csw"])
-    pkg.mrhs_nn_create(lat.ctx, learned.WIDTHS, 1)
+    pkg.mrhs_nn_create(lat.ctx, widths, 1)
     pkg.mrhs_nn_set_weights(lat.ctx, weights)
     gen = torch.Generator(device="cuda")
     gen.manual_seed(cfg["tvseed"])
@@ -609,10 +614,10 @@ def run_learned_mixed(args, cfg, U, m0, stream, plain_ms, barrier, dist=None, wo
         fg = fgmres_check(lat, cfg)
     lat.close()
     return {"value": whole_job_seconds_per_setup(lm_ms, world), "unit": "s", "ratio_vs_plain": lm_ms / plain_ms,
-            "widths": list(learned.WIDTHS),
+            "widths": list(widths),
             "form": "1 SAP sweep + network (widths %s, bf16 weights) for the initial phase, bf16 test vectors and P, "
                     "FP32 smoother, D_c contraction on bf16 tensor cores with FP32 accumulation (D_c stored FP32), "
-                    "tf32 tensor-core coarse stencil, then the same refinement" % (list(learned.WIDTHS),),
+                    "tf32 tensor-core coarse stencil, then the same refinement" % (list(widths),),
             "kernels": kernels,
             "training": {"lattice": [16, 16, 16, 16], "fields": 8, "steps": step - 1, "loss_first": losses[0],
                          "loss_last": losses[-1], "seconds": round(train_s, 1)},
@@ -682,6 +687,12 @@ def main():
     ap.add_argument("--no-fgmres", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-srhs", action="store_true", help="skip the block-length (N_b) comparison")
+    ap.add_argument("--smoother-eo", type=int, default=0, choices=[0, 1],
+                    help="1: even-odd preconditioned SAP domain solves")
+    ap.add_argument("--coarse-eo", type=int, default=0, choices=[0, 1],
+                    help="1: coarse GMRES on the Schur complement of the even aggregates")
+    ap.add_argument("--learned-width", type=int, default=0,
+                    help="hidden width of the learned generator (0: the library default)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", args.gpus if args.gpus else 1))

@@ -310,9 +310,21 @@ __global__ void k_prolong(const SP* __restrict__ P, const SC* __restrict__ uc, S
   st<SU, R>(u, row, N, r, acc);
 }
 
-// y[A][row][r] = sum_k sum_col Dc[A][k][row][col] x[nbr_k(A)][col][r]
+// the launch arguments of a part of the stencil (DcPart, typed)
 template <class SC>
-__global__ void k_apply_dc(const cx<typename Real<SC>::type>* __restrict__ Dc, const SC* __restrict__ x,
+struct DcPartArgs {
+  const int* alist;
+  const int* pos;
+  int kb, ke;
+  const SC* x0;
+  const SC* xh;
+  const SC* add;
+};
+
+// y[b][row][r] = sum_{kb<=k<ke} sum_col Dc[A][k][row][col] x[nbr_k(A)][col][r]
+// (+ add[b][row][r]) for A = alist[b]
+template <class SC>
+__global__ void k_apply_dc(const cx<typename Real<SC>::type>* __restrict__ Dc, DcPartArgs<SC> pa,
                            SC* __restrict__ y, const int* __restrict__ aggnbr, int nc, int N, size_t nwork) {
   using R = typename Real<SC>::type;
   size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -320,20 +332,23 @@ __global__ void k_apply_dc(const cx<typename Real<SC>::type>* __restrict__ Dc, c
   int r = (int)(t % N);
   size_t q = t / N;
   int row = (int)(q % nc);
-  int A = (int)(q / nc);
-  cx<R> acc = mk<R>(0, 0);
-  for (int k = 0; k < 9; ++k) {
-    int B = k == 0 ? A : aggnbr[A * 8 + k - 1];
+  const int b = (int)(q / nc);
+  const int A = pa.alist ? pa.alist[b] : b;
+  cx<R> acc = pa.add ? ld<SC, R>(pa.add, (size_t)b * nc + row, N, r) : mk<R>(0, 0);
+  for (int k = pa.kb; k < pa.ke; ++k) {
+    const int B = k == 0 ? A : aggnbr[A * 8 + k - 1];
+    const SC* x = k == 0 ? pa.x0 : pa.xh;
+    const size_t rb = pa.pos ? pa.pos[B] : B;
     const cx<R>* d = Dc + (((size_t)A * 9 + k) * nc + row) * nc;
-    for (int col = 0; col < nc; ++col) fma_(acc, d[col], ld<SC, R>(x, (size_t)B * nc + col, N, r));
+    for (int col = 0; col < nc; ++col) fma_(acc, d[col], ld<SC, R>(x, rb * nc + col, N, r));
   }
-  st<SC, R>(y, (size_t)A * nc + row, N, r, acc);
+  st<SC, R>(y, (size_t)b * nc + row, N, r, acc);
 }
 
 // 8 rows x 1 right-hand side per thread; pairs of columns read as one
 // 16-byte (FP32) load per row; requires 2*ntv % 8 == 0.
 template <class SC>
-__global__ void k_apply_dc_tiled(const cx<typename Real<SC>::type>* __restrict__ Dc, const SC* __restrict__ x,
+__global__ void k_apply_dc_tiled(const cx<typename Real<SC>::type>* __restrict__ Dc, DcPartArgs<SC> pa,
                                  SC* __restrict__ y, const int* __restrict__ aggnbr, int nc, int N, size_t nwork) {
   using R = typename Real<SC>::type;
   size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -342,16 +357,19 @@ __global__ void k_apply_dc_tiled(const cx<typename Real<SC>::type>* __restrict__
   const size_t q = t / N;
   const int nrt = nc / 8;
   const int row0 = 8 * (int)(q % nrt);
-  const int A = (int)(q / nrt);
+  const int b = (int)(q / nrt);
+  const int A = pa.alist ? pa.alist[b] : b;
   cx<R> acc[8];
 #pragma unroll
-  for (int a = 0; a < 8; ++a) acc[a] = mk<R>(0, 0);
-  for (int k = 0; k < 9; ++k) {
+  for (int a = 0; a < 8; ++a) acc[a] = pa.add ? ld<SC, R>(pa.add, (size_t)b * nc + row0 + a, N, r) : mk<R>(0, 0);
+  for (int k = pa.kb; k < pa.ke; ++k) {
     const int B = k == 0 ? A : aggnbr[A * 8 + k - 1];
+    const SC* x = k == 0 ? pa.x0 : pa.xh;
+    const size_t rb = pa.pos ? pa.pos[B] : B;
     const cx<R>* d = Dc + (((size_t)A * 9 + k) * nc + row0) * nc;
     for (int col = 0; col < nc; col += 2) {
-      cx<R> x0 = ld<SC, R>(x, (size_t)B * nc + col, N, r);
-      cx<R> x1 = ld<SC, R>(x, (size_t)B * nc + col + 1, N, r);
+      cx<R> x0 = ld<SC, R>(x, rb * nc + col, N, r);
+      cx<R> x1 = ld<SC, R>(x, rb * nc + col + 1, N, r);
 #pragma unroll
       for (int a = 0; a < 8; ++a) {
         fma_(acc[a], d[(size_t)a * nc + col], x0);
@@ -360,7 +378,7 @@ __global__ void k_apply_dc_tiled(const cx<typename Real<SC>::type>* __restrict__
     }
   }
 #pragma unroll
-  for (int a = 0; a < 8; ++a) st<SC, R>(y, (size_t)A * nc + row0 + a, N, r, acc[a]);
+  for (int a = 0; a < 8; ++a) st<SC, R>(y, (size_t)b * nc + row0 + a, N, r, acc[a]);
 }
 
 // u = P uc with one thread per (site, chirality, right-hand side): 6 outputs
@@ -713,6 +731,10 @@ void prolong(mrhs_ctx c, const void* uc, void* u, int nrhs, int dtype) {
 }
 
 void apply_Dc(mrhs_ctx c, const void* xc, void* yc, int nrhs, int dtype) {
+  apply_Dc_part(c, DcPart{nullptr, c->g.nagg, nullptr, 0, 9, xc, xc, nullptr}, yc, nrhs, dtype);
+}
+
+void apply_Dc_part(mrhs_ctx c, const DcPart& pt, void* yc, int nrhs, int dtype) {
   MRHS_REQUIRE(c->have_Dc, MRHS_ERR_STATE, "D_c used before mrhs_build_Dc");
   MRHS_REQUIRE(dtype == c->work_dtype, MRHS_ERR_ARG, "D_c apply: dtype must be the context's work type");
   const int nc = 2 * c->ntv;
@@ -724,23 +746,27 @@ void apply_Dc(mrhs_ctx c, const void* xc, void* yc, int nrhs, int dtype) {
   }();
   if (c->dc_engine != MRHS_DC_ALU && dtype == MRHS_F32 && !apply_alu) {
     const bool split = c->prec == MRHS_PREC_FP32;
-    if (apply_Dc_tc(c, xc, yc, nrhs, split)) return;
+    if (apply_Dc_tc(c, pt, yc, nrhs, split)) return;
   }
   Prof pr(c, "apply_dc");
-  if (nc % 8 == 0) {
-    size_t work = (size_t)c->g.nagg * (nc / 8) * nrhs;
-    if (dtype == MRHS_F64)
-      k_apply_dc_tiled<double><<<grid_for(work, 128), 128, 0, c->stream>>>((const cx<double>*)c->Dc, (const double*)xc, (double*)yc, c->aggnbr, nc, nrhs, work);
-    else
-      k_apply_dc_tiled<float><<<grid_for(work, 128), 128, 0, c->stream>>>((const cx<float>*)c->Dc, (const float*)xc, (float*)yc, c->aggnbr, nc, nrhs, work);
-    MRHS_LAUNCH_CHECK("apply_dc");
-    return;
-  }
-  size_t work = (size_t)c->g.nagg * nc * nrhs;
+  auto launch = [&](auto* tag) {
+    using SC = std::remove_pointer_t<decltype(tag)>;
+    using R = typename Real<SC>::type;
+    const DcPartArgs<SC> pa{pt.alist, pt.pos, pt.kb, pt.ke, (const SC*)pt.x0, (const SC*)pt.xh, (const SC*)pt.add};
+    if (nc % 8 == 0) {
+      const size_t work = (size_t)pt.na * (nc / 8) * nrhs;
+      k_apply_dc_tiled<SC><<<grid_for(work, 128), 128, 0, c->stream>>>((const cx<R>*)c->Dc, pa, (SC*)yc, c->aggnbr,
+                                                                        nc, nrhs, work);
+    } else {
+      const size_t work = (size_t)pt.na * nc * nrhs;
+      k_apply_dc<SC><<<grid_for(work, 256), 256, 0, c->stream>>>((const cx<R>*)c->Dc, pa, (SC*)yc, c->aggnbr, nc,
+                                                                  nrhs, work);
+    }
+  };
   if (dtype == MRHS_F64)
-    k_apply_dc<double><<<grid_for(work, 256), 256, 0, c->stream>>>((const cx<double>*)c->Dc, (const double*)xc, (double*)yc, c->aggnbr, nc, nrhs, work);
+    launch((double*)nullptr);
   else
-    k_apply_dc<float><<<grid_for(work, 256), 256, 0, c->stream>>>((const cx<float>*)c->Dc, (const float*)xc, (float*)yc, c->aggnbr, nc, nrhs, work);
+    launch((float*)nullptr);
   MRHS_LAUNCH_CHECK("apply_dc");
 }
 
@@ -749,24 +775,14 @@ void apply_Dc(mrhs_ctx c, const void* xc, void* yc, int nrhs, int dtype) {
 // colour of the SAP domains and every hop block of D_c joins aggregates of
 // different colour, so D_c = [[D_ee, D_eo], [D_oe, D_oo]] with block-diagonal
 // D_ee, D_oo (the self blocks). GMRES runs on S = D_ee - D_eo D_oo^-1 D_oe
-// (even aggregates; the odd rows of every vector stay zero), then
-// x_o = D_oo^-1 (b_o - D_oe x_e).
+// over the even aggregates only, then x_o = D_oo^-1 (b_o - D_oe x_e). Every
+// vector of the solve is compact: the row blocks of one colour in the order
+// of that colour's aggregate list (blocks_col), so the Krylov basis and its
+// dots and updates are half the size of the plain solve's.
 namespace {
-struct NbArgs {
-  int nb[4];
-};
-__device__ __forceinline__ int agg_colour(const NbArgs& g, int A) {
-  int s = 0;
-  for (int m = 0; m < 4; ++m) {
-    s += A % g.nb[m];
-    A /= g.nb[m];
-  }
-  return s & 1;
-}
-
-// the inverse of the self block of every odd aggregate (one CTA each, the
-// list of odd aggregates in blist), Gauss-Jordan with partial pivoting on
-// [D | 1] in shared memory; *bad set for a singular block
+// the inverse self block of every odd aggregate (CTA b: aggregate
+// blist[b], stored at Dinv[b]), Gauss-Jordan with partial pivoting on [D | 1]
+// in shared memory; *bad set for a singular block
 template <class R>
 __global__ void k_self_inverse(const cx<R>* __restrict__ Dc, cx<R>* __restrict__ Dinv, const int* __restrict__ blist,
                                int nc, int* bad) {
@@ -819,47 +835,44 @@ __global__ void k_self_inverse(const cx<R>* __restrict__ Dc, cx<R>* __restrict__
     }
     __syncthreads();
   }
-  cx<R>* out = Dinv + (size_t)A * nc * nc;
+  cx<R>* out = Dinv + (size_t)blockIdx.x * nc * nc;
   for (int e = threadIdx.x; e < nc * nc; e += blockDim.x) out[e] = m[(e / nc) * w2 + nc + e % nc];
 }
 
-// y[A] = D_oo^-1 x[A] on the odd aggregates, 0 on the even ones
+// y[b] = s Dinv[b] (a[b] - c[b]) for the compact odd row blocks b (c may be null)
 template <class S, class R>
-__global__ void k_odd_inverse_mul(const cx<R>* __restrict__ Dinv, const S* __restrict__ x, S* __restrict__ y, int nc,
-                                  int N, size_t nwork, NbArgs g) {
+__global__ void k_inverse_apply(const cx<R>* __restrict__ Dinv, const S* __restrict__ a, const S* __restrict__ c,
+                                S* __restrict__ y, R s, int nc, int N, size_t nwork) {
   const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (t >= nwork) return;
   const int r = (int)(t % N);
-  const size_t row = t / N;  // A * nc + i
-  const int A = (int)(row / nc), i = (int)(row % nc);
+  const size_t row = t / N;  // b * nc + i
+  const size_t b = row / nc;
+  const cx<R>* M = Dinv + row * nc;
   cx<R> acc = mk<R>(0, 0);
-  if (agg_colour(g, A) == 1) {
-    const cx<R>* M = Dinv + ((size_t)A * nc + i) * nc;
-    for (int j = 0; j < nc; ++j) fma_(acc, M[j], ld<S, R>(x, (size_t)A * nc + j, N, r));
+  for (int j = 0; j < nc; ++j) {
+    cx<R> v = ld<S, R>(a, b * nc + j, N, r);
+    if (c) v = v - ld<S, R>(c, b * nc + j, N, r);
+    fma_(acc, M[j], v);
   }
-  st<S, R>(y, row, N, r, acc);
+  st<S, R>(y, row, N, r, scale(acc, s));
 }
 
-// out = a - b on the rows of aggregates of colour `keep`, 0 elsewhere
-template <class S, class R>
-__global__ void k_colour_sub(const S* __restrict__ a, const S* __restrict__ b, S* __restrict__ out, int nc, int N,
-                             int keep, size_t nwork, NbArgs g) {
-  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (t >= nwork) return;
-  const int r = (int)(t % N);
-  const size_t row = t / N;
-  const int A = (int)(row / nc);
-  const cx<R> v = agg_colour(g, A) == keep ? ld<S, R>(a, row, N, r) - ld<S, R>(b, row, N, r) : mk<R>(0, 0);
-  st<S, R>(out, row, N, r, v);
-}
-
-// dst = src on the rows of odd aggregates (even rows untouched)
+// compact row blocks <-> the full coarse field: part b of the colour list
+// blist is the row block blist[b] of the full field
 template <class S>
-__global__ void k_copy_odd(const S* __restrict__ src, S* __restrict__ dst, int nc, int N, size_t nwork, NbArgs g) {
+__global__ void k_colour_gather(const S* __restrict__ full, S* __restrict__ part, const int* __restrict__ blist,
+                                size_t blk, size_t nwork) {
   const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (t >= nwork) return;
-  const size_t row = t / (2 * N);
-  if (agg_colour(g, (int)(row / nc)) == 1) dst[t] = src[t];
+  part[t] = full[(size_t)blist[t / blk] * blk + t % blk];
+}
+template <class S>
+__global__ void k_colour_scatter(const S* __restrict__ part, S* __restrict__ full, const int* __restrict__ blist,
+                                 size_t blk, size_t nwork) {
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= nwork) return;
+  full[(size_t)blist[t / blk] * blk + t % blk] = part[t];
 }
 }  // namespace
 
@@ -869,12 +882,12 @@ static void ensure_self_inverses(mrhs_ctx c) {
   MRHS_REQUIRE(nc <= 128, MRHS_ERR_SHAPE, "even-odd coarse solve: 2 ntv must be at most 128");
   if (c->dc_inv && c->dc_inv_version == c->dc_version) return;
   const size_t es = c->work_dtype == MRHS_F64 ? sizeof(cx<double>) : sizeof(cx<float>);
-  if (!c->dc_inv) c->dc_inv = dalloc(c, (size_t)c->g.nagg * nc * nc * es);
   const size_t smem = (size_t)nc * 2 * nc * es;
   int optin = 0;
   MRHS_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
   MRHS_REQUIRE(smem <= (size_t)optin, MRHS_ERR_SHAPE,
                "even-odd coarse solve: a self block of this size does not fit in shared memory");
+  if (!c->dc_inv) c->dc_inv = dalloc(c, (size_t)c->ncol[1] * nc * nc * es);
   MRHS_CUDA(cudaMemsetAsync(c->dflag + 5, 0, sizeof(int), c->stream));
   const int* odd = c->blocks_col + c->ncol[0];
   Prof pr(c, "self_inverse");
@@ -895,55 +908,46 @@ static void ensure_self_inverses(mrhs_ctx c) {
 }
 
 namespace {
-NbArgs nb_args(mrhs_ctx c) {
-  NbArgs g;
-  for (int m = 0; m < 4; ++m) g.nb[m] = c->g.nb[m];
-  return g;
-}
-void odd_inverse_mul(mrhs_ctx c, const void* x, void* y, int N, int dtype) {
+// y = s D_oo^-1 (a - b) on compact odd blocks (b may be null)
+void inverse_apply(mrhs_ctx c, const void* a, const void* b, void* y, double s, int N, int dtype) {
   const int nc = 2 * c->ntv;
-  const size_t work = (size_t)c->g.nagg * nc * N;
+  const size_t work = (size_t)c->ncol[1] * nc * N;
+  Prof pr(c, "inverse_apply");
   if (dtype == MRHS_F64)
-    k_odd_inverse_mul<double, double><<<grid_for(work, 256), 256, 0, c->stream>>>(
-        (const cx<double>*)c->dc_inv, (const double*)x, (double*)y, nc, N, work, nb_args(c));
+    k_inverse_apply<double, double><<<grid_for(work, 256), 256, 0, c->stream>>>(
+        (const cx<double>*)c->dc_inv, (const double*)a, (const double*)b, (double*)y, s, nc, N, work);
   else
-    k_odd_inverse_mul<float, float><<<grid_for(work, 256), 256, 0, c->stream>>>(
-        (const cx<float>*)c->dc_inv, (const float*)x, (float*)y, nc, N, work, nb_args(c));
-  MRHS_LAUNCH_CHECK("odd_inverse_mul");
+    k_inverse_apply<float, float><<<grid_for(work, 256), 256, 0, c->stream>>>(
+        (const cx<float>*)c->dc_inv, (const float*)a, (const float*)b, (float*)y, (float)s, nc, N, work);
+  MRHS_LAUNCH_CHECK("inverse_apply");
 }
-void colour_sub(mrhs_ctx c, const void* a, const void* b, void* out, int N, int dtype, int keep) {
-  const int nc = 2 * c->ntv;
-  const size_t work = (size_t)c->g.nagg * nc * N;
-  if (dtype == MRHS_F64)
-    k_colour_sub<double, double><<<grid_for(work, 256), 256, 0, c->stream>>>((const double*)a, (const double*)b,
-                                                                            (double*)out, nc, N, keep, work, nb_args(c));
-  else
-    k_colour_sub<float, float><<<grid_for(work, 256), 256, 0, c->stream>>>((const float*)a, (const float*)b,
-                                                                          (float*)out, nc, N, keep, work, nb_args(c));
-  MRHS_LAUNCH_CHECK("colour_sub");
+void colour_copy(mrhs_ctx c, const void* src, void* dst, int colour, bool gather, int N, int dtype) {
+  const size_t blk = (size_t)2 * c->ntv * 2 * N;
+  const size_t work = (size_t)c->ncol[colour] * blk;
+  const int* bl = c->blocks_col + (colour ? c->ncol[0] : 0);
+  MRHS_DISPATCH(dtype, S, (gather ? k_colour_gather<S><<<grid_for(work, 256), 256, 0, c->stream>>>((const S*)src, (S*)dst, bl, blk, work)
+                                  : k_colour_scatter<S><<<grid_for(work, 256), 256, 0, c->stream>>>((const S*)src, (S*)dst, bl, blk, work)));
+  MRHS_LAUNCH_CHECK("colour_copy");
+}
+// the part of the stencil over the aggregates of one colour, on compact fields
+DcPart colour_part(mrhs_ctx c, int colour, int kb, const void* x0, const void* xh, const void* add) {
+  return DcPart{c->blocks_col + (colour ? c->ncol[0] : 0), c->ncol[colour], c->colpos, kb, 9, x0, xh, add};
 }
 }  // namespace
 
-// y = S x = D_ee x_e - D_eo D_oo^-1 D_oe x_e for x zero on the odd rows; t and
-// u: two work fields of the coarse size
+// y = S x on compact even fields: t_o = D_oe x, u_o = -D_oo^-1 t_o,
+// y = D_ee x + D_eo u_o (t and u: compact odd work fields)
 static void apply_schur(mrhs_ctx c, const void* x, void* y, void* t, void* u, int N, int dtype) {
-  apply_Dc(c, x, t, N, dtype);      // even rows D_ee x_e, odd rows D_oe x_e
-  odd_inverse_mul(c, t, u, N, dtype);
-  apply_Dc(c, u, y, N, dtype);      // even rows D_eo u_o
-  colour_sub(c, t, y, y, N, dtype, 0);
+  apply_Dc_part(c, colour_part(c, 1, 1, nullptr, x, nullptr), t, N, dtype);
+  inverse_apply(c, t, nullptr, u, -1.0, N, dtype);
+  apply_Dc_part(c, colour_part(c, 0, 0, x, u, nullptr), y, N, dtype);
 }
 
-// restarted GMRES on D_c, or on the Schur complement S when tu holds its two
-// work fields (then bc and xc are zero on the odd aggregates)
+// restarted GMRES on `rows` coarse rows: op(x, y) is D_c, or S on compact
+// even fields
+template <class Op>
 static void coarse_gmres(mrhs_ctx c, const void* bc, void* xc, int N, int dtype, double tol, int m, int maxit,
-                         int* iters, void* const* tu) {
-  auto op = [&](const void* x, void* y) {
-    if (tu)
-      apply_schur(c, x, y, tu[0], tu[1], N, dtype);
-    else
-      apply_Dc(c, x, y, N, dtype);
-  };
-  const size_t rows = (size_t)c->g.nagg * 2 * c->ntv;
+                         int* iters, size_t rows, Op op) {
   const size_t fe = rows * 2 * N;  // elements of one coarse field
   const size_t es = dtype_size(dtype);
   char* basis = (char*)scratch(c, SC_KRYLOV, (size_t)(m + 2) * fe * es);
@@ -1025,28 +1029,35 @@ void coarse_solve(mrhs_ctx c, const void* bc, void* xc, int N, int dtype, double
   MRHS_REQUIRE(dtype == c->work_dtype, MRHS_ERR_ARG, "coarse solve: dtype must be the context's work type");
   MRHS_REQUIRE(N >= 1 && N <= 256 && m >= 1 && m <= 64 && maxit >= 0 && tol >= 0, MRHS_ERR_ARG,
                "coarse solve: need 1 <= nrhs <= 256, 1 <= restart <= 64, maxit >= 0, tol >= 0");
+  const int nc = 2 * c->ntv;
   if (!c->coarse_eo) {
-    coarse_gmres(c, bc, xc, N, dtype, tol, m, maxit, iters, nullptr);
+    coarse_gmres(c, bc, xc, N, dtype, tol, m, maxit, iters, (size_t)c->g.nagg * nc,
+                 [&](const void* x, void* y) { apply_Dc(c, x, y, N, dtype); });
     return;
   }
   ensure_self_inverses(c);
-  const size_t fb = (size_t)c->g.nagg * 2 * c->ntv * 2 * N * dtype_size(dtype);
-  char* wk = (char*)scratch(c, SC_COARSE_EO, 3 * fb);
-  void* tu[2] = {wk, wk + fb};
-  void* bh = wk + 2 * fb;
+  // compact fields: b_e, b_o, bhat_e, x_e, and two odd work fields
+  const size_t hb = (size_t)c->ncol[0] * nc * 2 * N * dtype_size(dtype);
+  char* wk = (char*)scratch(c, SC_COARSE_EO, 6 * hb);
+  void* be = wk;
+  void* bo = wk + hb;
+  void* bh = wk + 2 * hb;
+  void* xe = wk + 3 * hb;
+  void* t = wk + 4 * hb;
+  void* u = wk + 5 * hb;
+  colour_copy(c, bc, be, 0, true, N, dtype);
+  colour_copy(c, bc, bo, 1, true, N, dtype);
   // bhat_e = b_e - D_eo D_oo^-1 b_o
-  odd_inverse_mul(c, bc, tu[1], N, dtype);
-  apply_Dc(c, tu[1], tu[0], N, dtype);
-  colour_sub(c, bc, tu[0], bh, N, dtype, 0);
-  coarse_gmres(c, bh, xc, N, dtype, tol, m, maxit, iters, tu);
+  inverse_apply(c, bo, nullptr, u, -1.0, N, dtype);
+  apply_Dc_part(c, colour_part(c, 0, 1, nullptr, u, be), bh, N, dtype);
+  // GMRES on S from x_e = 0
+  coarse_gmres(c, bh, xe, N, dtype, tol, m, maxit, iters, (size_t)c->ncol[0] * nc,
+               [&](const void* x, void* y) { apply_schur(c, x, y, t, u, N, dtype); });
   // x_o = D_oo^-1 (b_o - D_oe x_e)
-  apply_Dc(c, xc, tu[0], N, dtype);
-  colour_sub(c, bc, tu[0], tu[0], N, dtype, 1);
-  odd_inverse_mul(c, tu[0], tu[1], N, dtype);
-  const size_t work = (size_t)c->g.nagg * 2 * c->ntv * 2 * N;
-  MRHS_DISPATCH(dtype, S, (k_copy_odd<S><<<grid_for(work, 256), 256, 0, c->stream>>>((const S*)tu[1], (S*)xc,
-                                                                                     2 * c->ntv, N, work, nb_args(c))));
-  MRHS_LAUNCH_CHECK("copy_odd");
+  apply_Dc_part(c, colour_part(c, 1, 1, nullptr, xe, nullptr), t, N, dtype);
+  inverse_apply(c, bo, t, u, 1.0, N, dtype);
+  colour_copy(c, xe, xc, 0, false, N, dtype);
+  colour_copy(c, u, xc, 1, false, N, dtype);
 }
 
 // ------------------------------------------------------------------------

@@ -292,16 +292,25 @@ __global__ void __launch_bounds__(kThreads) k_coarse_op_tc(const SP* __restrict_
 // waited for; two CTAs share an SM.
 constexpr int kDcThreads = 512;  // 16 warps: the operand conversion is the CUDA cores' share
 
+// A part of the stencil (the even-odd coarse solve): CTA b takes aggregate
+// alist[b] (b without a list) and the blocks kb <= k < ke; block 0 reads x0,
+// the hop blocks xh, the row block of aggregate B at pos[B] (B without pos);
+// y (plus add, when given) is written at row block b.
 template <bool SPLIT, bool PRE>
 __global__ void __launch_bounds__(kDcThreads, 1) k_apply_dc_tc(const float* __restrict__ Dc,
-                                                               const float* __restrict__ x, float* __restrict__ y,
+                                                               const float* __restrict__ x0,
+                                                               const float* __restrict__ xh, float* __restrict__ y,
                                                                const int* __restrict__ aggnbr, int nc, int nrhs,
-                                                               uint32_t tm_cols, int* __restrict__ err) {
+                                                               uint32_t tm_cols, int* __restrict__ err,
+                                                               const int* __restrict__ alist,
+                                                               const int* __restrict__ pos, int kb, int ke,
+                                                               const float* __restrict__ add) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ uint64_t full[2], mma_done;
   __shared__ uint32_t s_tmem;
   __shared__ int s_bad;
-  const int A = blockIdx.x;
+  const int A = alist ? alist[blockIdx.x] : (int)blockIdx.x;
+  const int nk = ke - kb;                    // blocks of this launch (at least 1)
   const int NM = 2 * nrhs;                   // MMA N
   const int KG = nc / 4;                     // 16-byte K groups (tf32)
   const int a_bytes = kRows / 8 * KG * 128;  // A tile
@@ -357,34 +366,38 @@ __global__ void __launch_bounds__(kDcThreads, 1) k_apply_dc_tc(const float* __re
   }
   const uint32_t idesc = tc::instr_desc(tc::kFmtTF32, tc::kFmtTF32, kRows, NM);
 
-  // block k of the stencil: D_c[A][k] and x_c of its aggregate, one bulk copy each
-  auto fetch = [&](int k) {
-    unsigned char* raw = raw0 + (k & 1) * raw_bytes;
+  // step j: block k = kb + j of the stencil, D_c[A][k] and x_c of its
+  // aggregate, one bulk copy each
+  auto fetch = [&](int j) {
+    const int k = kb + j;
+    unsigned char* raw = raw0 + (j & 1) * raw_bytes;
     const int B = k == 0 ? A : aggnbr[A * 8 + k - 1];
-    tc::mbar_expect_tx(&full[k & 1], x_off + x_bytes);
+    const float* xs = k == 0 ? x0 : xh;
+    const int rb = pos ? pos[B] : B;
+    tc::mbar_expect_tx(&full[j & 1], x_off + x_bytes);
     if (PRE)
       tc::bulk_g2s(raw, reinterpret_cast<const unsigned char*>(Dc) + ((size_t)A * 9 + k) * img_bytes, img_bytes,
-                   &full[k & 1]);
+                   &full[j & 1]);
     else
-      tc::bulk_g2s(raw, Dc + ((size_t)A * 9 + k) * nc * nc * 2, d_bytes, &full[k & 1]);
-    tc::bulk_g2s(raw + x_off, x + (size_t)B * nc * 2 * nrhs, x_bytes, &full[k & 1]);
+      tc::bulk_g2s(raw, Dc + ((size_t)A * 9 + k) * nc * nc * 2, d_bytes, &full[j & 1]);
+    tc::bulk_g2s(raw + x_off, xs + (size_t)rb * nc * 2 * nrhs, x_bytes, &full[j & 1]);
   };
   if (tid == 0) {
     fetch(0);
-    fetch(1);
+    if (nk > 1) fetch(1);
   }
   int issued = 0;
-  for (int k = 0; k < 9; ++k) {
-    const unsigned char* raw = raw0 + (k & 1) * raw_bytes;
-    bool ok = tc::mbar_wait(&full[k & 1], (k >> 1) & 1, kWaitLimit);
-    if (k >= 1) {
-      // block k-1 done: fold its partial sum R into S before R is reused
-      ok = ok && tc::mbar_wait(&mma_done, (k - 1) & 1, kWaitLimit);
+  for (int j = 0; j < nk; ++j) {
+    const unsigned char* raw = raw0 + (j & 1) * raw_bytes;
+    bool ok = tc::mbar_wait(&full[j & 1], (j >> 1) & 1, kWaitLimit);
+    if (j >= 1) {
+      // step j-1 done: fold its partial sum R into S before R is reused
+      ok = ok && tc::mbar_wait(&mma_done, (j - 1) & 1, kWaitLimit);
       tc::fence_after_sync();
       tc::tmem_promote(t_own + NM, t_own, own);  // warp-wide; a failed wait discards the result
       tc::tmem_wait_st();
-      // PRE: the MMAs of block k-1 are done with its stage, which takes block k+1
-      if (PRE && tid == 0 && ok && k + 1 < 9) fetch(k + 1);
+      // PRE: the MMAs of step j-1 are done with its stage, which takes step j+1
+      if (PRE && tid == 0 && ok && j + 1 < nk) fetch(j + 1);
     }
     if (!ok) s_bad = 1;
     tc::fence_before_sync();
@@ -435,7 +448,7 @@ __global__ void __launch_bounds__(kDcThreads, 1) k_apply_dc_tc(const float* __re
     tc::fence_async_smem();
     __syncthreads();
     if (tid == 0) {
-      if (!PRE && k + 2 < 9) fetch(k + 2);  // the raw stage is free: every thread has converted it
+      if (!PRE && j + 2 < nk) fetch(j + 2);  // the raw stage is free: every thread has converted it
       tc::fence_after_sync();
       const uint32_t ah = PRE ? tc::smem_u32(raw) : tc::smem_u32(Ahi), bh = tc::smem_u32(Bhi),
                      al = PRE ? ah + a_bytes : tc::smem_u32(Alo), bl = tc::smem_u32(Blo);
@@ -451,7 +464,7 @@ __global__ void __launch_bounds__(kDcThreads, 1) k_apply_dc_tc(const float* __re
       }
       tc::mma_commit(&mma_done);
     }
-    issued = k + 1;
+    issued = j + 1;
   }
   if (issued > 0) {
     if (!tc::mbar_wait(&mma_done, (issued - 1) & 1, kWaitLimit)) s_bad = 1;
@@ -462,7 +475,7 @@ __global__ void __launch_bounds__(kDcThreads, 1) k_apply_dc_tc(const float* __re
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (!s_bad && issued == 9) {
+  if (!s_bad && issued == nk) {
     float* E = reinterpret_cast<float*>(smem);  // [128][NM + 1], over the (now idle) raw stages
     const int quarter = warp & 3;
     for (int col0 = slice * sw; col0 < slice * sw + own; col0 += 16) {
@@ -473,11 +486,13 @@ __global__ void __launch_bounds__(kDcThreads, 1) k_apply_dc_tc(const float* __re
       for (int i = 0; i < 16; ++i) E[row * (NM + 1) + col0 + i] = v[i];
     }
     __syncthreads();
-    float* yA = y + (size_t)A * nc * 2 * nrhs;
+    float* yA = y + (size_t)blockIdx.x * nc * 2 * nrhs;
+    const float* addA = add ? add + (size_t)blockIdx.x * nc * 2 * nrhs : nullptr;
     for (int e = tid; e < nc * 2 * nrhs; e += kDcThreads) {
       const int r = e % nrhs, p = (e / nrhs) % 2, i = e / (2 * nrhs);
-      const float v = p == 0 ? E[i * (NM + 1) + r] - E[(nc + i) * (NM + 1) + nrhs + r]
-                             : E[i * (NM + 1) + nrhs + r] + E[(nc + i) * (NM + 1) + r];
+      float v = p == 0 ? E[i * (NM + 1) + r] - E[(nc + i) * (NM + 1) + nrhs + r]
+                       : E[i * (NM + 1) + nrhs + r] + E[(nc + i) * (NM + 1) + r];
+      if (addA) v += addA[e];
       yA[e] = v;
     }
   } else {
@@ -485,7 +500,7 @@ __global__ void __launch_bounds__(kDcThreads, 1) k_apply_dc_tc(const float* __re
     // shared memory is released
     if (tid == 0) {
       atomicExch(err, 1);
-      for (int k = issued; k < 9 && k < issued + 2; ++k) tc::mbar_wait(&full[k & 1], (k >> 1) & 1, kWaitLimit);
+      for (int j = issued; j < nk && j < issued + 2; ++j) tc::mbar_wait(&full[j & 1], (j >> 1) & 1, kWaitLimit);
     }
   }
   tc::fence_before_sync();
@@ -596,7 +611,7 @@ void dc_images_build(mrhs_ctx c) {
 
 // coarse stencil on the tensor cores (FP32 coarse fields): split-tf32 (FP32
 // accuracy) or single tf32; false when the shape is outside the kernel's
-bool apply_Dc_tc(mrhs_ctx c, const void* xc, void* yc, int nrhs, bool split) {
+bool apply_Dc_tc(mrhs_ctx c, const DcPart& pt, void* yc, int nrhs, bool split) {
   const int nc = 2 * c->ntv;
   if (c->work_dtype != MRHS_F32 || nc % 8 != 0 || nc > 64 || nrhs % 16 != 0 || nrhs > 64) return false;
   const int KG = nc / 4;
@@ -625,8 +640,9 @@ bool apply_Dc_tc(mrhs_ctx c, const void* xc, void* yc, int nrhs, bool split) {
   auto kern = pre ? (split ? k_apply_dc_tc<true, true> : k_apply_dc_tc<false, true>)
                   : (split ? k_apply_dc_tc<true, false> : k_apply_dc_tc<false, false>);
   MRHS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  kern<<<c->g.nagg, kDcThreads, smem, c->stream>>>((const float*)src, (const float*)xc, (float*)yc, c->aggnbr, nc,
-                                                   nrhs, cols, err);
+  kern<<<pt.na, kDcThreads, smem, c->stream>>>((const float*)src, (const float*)pt.x0, (const float*)pt.xh,
+                                               (float*)yc, c->aggnbr, nc, nrhs, cols, err, pt.alist, pt.pos, pt.kb,
+                                               pt.ke, (const float*)pt.add);
   MRHS_LAUNCH_CHECK("apply_dc_tc");
   return true;
 }

@@ -183,6 +183,7 @@ struct mrhs_ctx_s {
   int* aggnbr = nullptr;     // [nagg][8]
   int* blocks_col = nullptr; // [2][nagg/2] aggregate ids of colour 0, then colour 1
   int ncol[2] = {0, 0};
+  int* colpos = nullptr;     // [nagg] position of every aggregate in its colour's list
 
   // gauge field and clover, device order
   double* U64 = nullptr;  // [V][4][9] complex
@@ -204,7 +205,7 @@ struct mrhs_ctx_s {
   void* dc_img = nullptr;          // D_c as tensor-core operand images (coarse_tc.cu)
   long long dc_img_version = -1;   // the D_c version the images hold
   int dc_img_split = -1;           // 1: tf32 hi + lo images, 0: tf32 only
-  void* dc_inv = nullptr;          // [nagg][2ntv][2ntv] inverse self blocks of the odd aggregates
+  void* dc_inv = nullptr;          // [nagg/2][2ntv][2ntv] inverse self blocks of the odd aggregates (list order)
   long long dc_inv_version = -1;   // the D_c version dc_inv holds
   int coarse_eo = 0;               // 1: coarse GMRES on the Schur complement of the even aggregates
   bool have_tv = false, have_P = false, have_Dc = false;
@@ -287,8 +288,25 @@ void build_Dc(mrhs_ctx c);
 // operand formats of the tensor-core contraction (tcgen05 instruction-descriptor codes)
 constexpr int tc_fmt_f16 = 0, tc_fmt_bf16 = 1, tc_fmt_tf32 = 2;
 bool build_Dc_tc(mrhs_ctx c, int fmt, bool split);
+// A part of the coarse stencil y = D_c x: the aggregates alist[0..na) in
+// that order (all aggregates in order when alist is null), the blocks
+// kb <= k < ke of each (k = 0 the self block, 1+mu / 5+mu the hops); block 0
+// reads x0 and the hop blocks xh, the row block of aggregate B at pos[B] (B
+// when pos is null); row block b of y (and of add, y = stencil + add, when
+// add is given) belongs to alist[b]. The plain stencil is {null, nagg, null,
+// 0, 9, x, x, null}.
+struct DcPart {
+  const int* alist;
+  int na;
+  const int* pos;
+  int kb, ke;
+  const void* x0;
+  const void* xh;
+  const void* add;
+};
 // coarse stencil on the tensor cores; sets dflag[3] if a pipeline wait ran out
-bool apply_Dc_tc(mrhs_ctx c, const void* xc, void* yc, int nrhs, bool split);
+bool apply_Dc_tc(mrhs_ctx c, const DcPart& part, void* yc, int nrhs, bool split);
+void apply_Dc_part(mrhs_ctx c, const DcPart& part, void* yc, int nrhs, int dtype);
 void dc_images_build(mrhs_ctx c);
 void check_tc_timeout(mrhs_ctx c);
 void restrict_(mrhs_ctx c, const void* v, void* vc, int nrhs, int dtype);

@@ -675,6 +675,11 @@ int mrhs_create(const int dims[4], const int agg[4], int ntv, int prec, void* st
       std::vector<int> all(col[0]);
       all.insert(all.end(), col[1].begin(), col[1].end());
       MRHS_CUDA(cudaMemcpyAsync(c->blocks_col, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice, c->stream));
+      std::vector<int> posv(g.nagg);
+      for (int q = 0; q < 2; ++q)
+        for (size_t i = 0; i < col[q].size(); ++i) posv[col[q][i]] = (int)i;
+      c->colpos = (int*)dalloc(c, sizeof(int) * (size_t)na);
+      MRHS_CUDA(cudaMemcpyAsync(c->colpos, posv.data(), sizeof(int) * posv.size(), cudaMemcpyHostToDevice, c->stream));
       MRHS_CUDA(cudaMemsetAsync(c->dflag, 0, sizeof(int) * 16, c->stream));
       MRHS_CUDA(cudaStreamSynchronize(c->stream));
     } catch (...) {

@@ -85,11 +85,12 @@ def test_coarse_eo_tolerance_and_residual_fp64():
     lat.close()
 
 
-def test_coarse_eo_fp32_and_dc_rebuild():
-    """FP32 context, 2ntv = 24, 32 aggregates, 8 right-hand sides; then new
-    test vectors and a new D_c: the inverse self blocks follow the new D_c."""
+@pytest.mark.parametrize("nrhs", [8, 16], ids=["cuda-cores", "tensor-cores"])
+def test_coarse_eo_fp32_and_dc_rebuild(nrhs):
+    """FP32 context, 2ntv = 24, 32 aggregates; 8 right-hand sides take the
+    CUDA-core stencil, 16 the tensor-core one (split tf32). Then new test
+    vectors and a new D_c: the inverse self blocks follow the new D_c."""
     lat, U, A, Dc = make(P4, MRHS_PREC_FP32, MRHS_F32, 4301)
-    nrhs = 8
     bc = inputs.gaussian_field((nrhs, lat.nagg, 2 * lat.ntv), 4302)
     bcd = lat.to_device(bc, MRHS_F32, coarse=True)
     xcd = lat.field(nrhs, MRHS_F32, coarse=True)
