@@ -799,15 +799,22 @@ __global__ void k_self_inverse(const cx<R>* __restrict__ Dc, cx<R>* __restrict__
   }
   __syncthreads();
   for (int col = 0; col < nc; ++col) {
-    if (threadIdx.x == 0) {
-      int p = col;
-      R best = m[col * w2 + col].re * m[col * w2 + col].re + m[col * w2 + col].im * m[col * w2 + col].im;
-      for (int i = col + 1; i < nc; ++i) {
+    if (threadIdx.x < 32) {
+      // pivot: the largest |m[i][col]|^2, i >= col (the first on ties), by warp 0
+      const int lane = threadIdx.x;
+      R best = -1;
+      int p = -1;
+      for (int i = col + lane; i < nc; i += 32) {
         const cx<R> v = m[i * w2 + col];
         const R a = v.re * v.re + v.im * v.im;
         if (a > best) best = a, p = i;
       }
-      s_p = best > 0 ? p : -1;
+      for (int off = 16; off > 0; off >>= 1) {
+        const R ob = __shfl_down_sync(0xffffffffu, best, off);
+        const int op = __shfl_down_sync(0xffffffffu, p, off);
+        if (op >= 0 && (ob > best || (ob == best && op < p))) best = ob, p = op;
+      }
+      if (lane == 0) s_p = best > 0 ? p : -1;
     }
     __syncthreads();
     const int p = s_p;
@@ -839,7 +846,33 @@ __global__ void k_self_inverse(const cx<R>* __restrict__ Dc, cx<R>* __restrict__
   for (int e = threadIdx.x; e < nc * nc; e += blockDim.x) out[e] = m[(e / nc) * w2 + nc + e % nc];
 }
 
-// y[b] = s Dinv[b] (a[b] - c[b]) for the compact odd row blocks b (c may be null)
+// y[b] = s Dinv[b] (a[b] - c[b]) for the compact odd row blocks b (c may be
+// null); 8 rows x 1 right-hand side per thread (nc % 8 = 0), so that every
+// load of a serves eight rows
+template <class S, class R>
+__global__ void k_inverse_apply8(const cx<R>* __restrict__ Dinv, const S* __restrict__ a, const S* __restrict__ c,
+                                 S* __restrict__ y, R s, int nc, int N, size_t nwork) {
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= nwork) return;
+  const int r = (int)(t % N);
+  const size_t q = t / N;
+  const int nrt = nc / 8;
+  const size_t b = q / nrt;
+  const size_t row0 = b * nc + 8 * (q % nrt);
+  cx<R> acc[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) acc[k] = mk<R>(0, 0);
+  for (int j = 0; j < nc; ++j) {
+    cx<R> v = ld<S, R>(a, b * nc + j, N, r);
+    if (c) v = v - ld<S, R>(c, b * nc + j, N, r);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) fma_(acc[k], Dinv[(row0 + k) * nc + j], v);
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) st<S, R>(y, row0 + k, N, r, scale(acc[k], s));
+}
+
+// the same with one row per thread (any nc)
 template <class S, class R>
 __global__ void k_inverse_apply(const cx<R>* __restrict__ Dinv, const S* __restrict__ a, const S* __restrict__ c,
                                 S* __restrict__ y, R s, int nc, int N, size_t nwork) {
@@ -911,8 +944,19 @@ namespace {
 // y = s D_oo^-1 (a - b) on compact odd blocks (b may be null)
 void inverse_apply(mrhs_ctx c, const void* a, const void* b, void* y, double s, int N, int dtype) {
   const int nc = 2 * c->ntv;
-  const size_t work = (size_t)c->ncol[1] * nc * N;
   Prof pr(c, "inverse_apply");
+  if (nc % 8 == 0) {
+    const size_t work = (size_t)c->ncol[1] * (nc / 8) * N;
+    if (dtype == MRHS_F64)
+      k_inverse_apply8<double, double><<<grid_for(work, 128), 128, 0, c->stream>>>(
+          (const cx<double>*)c->dc_inv, (const double*)a, (const double*)b, (double*)y, s, nc, N, work);
+    else
+      k_inverse_apply8<float, float><<<grid_for(work, 128), 128, 0, c->stream>>>(
+          (const cx<float>*)c->dc_inv, (const float*)a, (const float*)b, (float*)y, (float)s, nc, N, work);
+    MRHS_LAUNCH_CHECK("inverse_apply");
+    return;
+  }
+  const size_t work = (size_t)c->ncol[1] * nc * N;
   if (dtype == MRHS_F64)
     k_inverse_apply<double, double><<<grid_for(work, 256), 256, 0, c->stream>>>(
         (const cx<double>*)c->dc_inv, (const double*)a, (const double*)b, (double*)y, s, nc, N, work);

@@ -12,7 +12,8 @@ v|^2/|v|^2). Judging: on n_test unseen fields the learned initial phase (one
 SAP sweep + the network) against the plain one (5 sweeps), both followed by
 the same refinement: the Rayleigh quotients |Dv|/|v| of the test vectors after
 the initial phase and after the refinement, and the two-level FGMRES iteration
-count to 1e-10.
+count to 1e-10. Every coarse solve (refinement and FGMRES) runs on the
+Schur complement of the even aggregates unless coarse_eo = 0.
 
 Orchestration only: every step runs in the library's kernels through the C
 ABI; torch provides device memory and the norms of the Rayleigh quotients.
@@ -63,13 +64,14 @@ def tv_rayleigh(lat):
 
 
 def run(n_train=64, n_test=8, dims=(16, 16, 16, 32), agg=(4, 4, 4, 4), ntv=20, widths=(4, 32, 32, 4),
-        steps=25, lr=2e-3, lam=1.0, csw=1.5, m0_table=None, schedule=None, log=print):
+        steps=25, lr=2e-3, lam=1.0, csw=1.5, m0_table=None, schedule=None, coarse_eo=1, log=print):
     import torch
 
     s = dict(SCHEDULE, **(schedule or {}))
     m0_table = m0_table or {0.6: -0.6278459331791598}
     t0 = time.perf_counter()
     lat = Lattice(dims, agg, ntv, MRHS_PREC_FP32)
+    lat.set_coarse_solver(coarse_eo)
     learned.attach(lat, widths, seed=17, noise=0.01, bf16=True)
     step = 1
     first = last = None
@@ -127,7 +129,8 @@ def run(n_train=64, n_test=8, dims=(16, 16, 16, 32), agg=(4, 4, 4, 4), ntv=20, w
         tests.append(row)
     lat.close()
     agg_its = [(t["plain"]["fgmres"], t["learned"]["fgmres"]) for t in tests]
-    return {"widths": list(widths), "train_fields": n_train, "test_fields": n_test, "steps_per_field": steps,
+    return {"widths": list(widths), "coarse_solver": "even-odd" if coarse_eo else "plain",
+            "train_fields": n_train, "test_fields": n_test, "steps_per_field": steps,
             "loss_first": first, "loss_last": last, "train_s": round(train_s, 1), "tests": tests,
             "fgmres_plain_mean": float(np.mean([a for a, _ in agg_its])),
             "fgmres_learned_mean": float(np.mean([b for _, b in agg_its])),
