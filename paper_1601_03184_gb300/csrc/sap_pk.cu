@@ -24,6 +24,7 @@
 // alpha = <q, rho> / <q, q> per right-hand side, then x_B += e.
 #include <algorithm>
 #include <cstdlib>
+#include <string>
 
 #include "stencil.cuh"
 #include "tc.cuh"
@@ -31,14 +32,16 @@
 namespace mrhs {
 namespace {
 
-constexpr int kPG = 4;        // right-hand sides per chunk (two pairs)
+// PP pairs of right-hand sides per chunk: PP = 2 (512 threads for a 256-site
+// domain, one CTA per SM) or PP = 1 (256 threads, two CTAs per SM); LG: the
+// links read from global memory (through L1) instead of staged in shared
+// memory, which leaves room for the second CTA
 constexpr int kPCols = 48;    // tensor-memory columns of one thread's x_B
 constexpr int kPClov = 72;    // tensor-memory columns of its site's clover term
 constexpr int kPWarpCols = kPCols + kPClov;
-constexpr int kPMaxT = 512;   // threads for a 256-site domain
 
 struct DomP {
-  const float4* sR;  // [12][Va][2]
+  const float4* sR;  // [12][Va][PP]
   const float4* sU;  // [20][Va+1]: float4 k of link mu at row mu*5 + k
   const int* sN;     // [8][Va]: neighbour inside the domain (local) or ~(device site)
   uint32_t tclov;    // tensor-memory address of the thread's copy of its site's clover term
@@ -46,8 +49,9 @@ struct DomP {
   size_t s0;
 };
 
+template <int PP>
 __device__ __forceinline__ c2 ldR(const DomP& d, int c, int n) {
-  const float4 v = d.sR[(c * d.Va + n) * 2 + d.p];
+  const float4 v = d.sR[(c * d.Va + n) * PP + d.p];
   return mk2(make_float2(v.x, v.y), make_float2(v.z, v.w));
 }
 
@@ -55,6 +59,15 @@ __device__ __forceinline__ void ld_link(const float4* src, int stride, float u[2
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     const float4 t = src[k * stride];
+    u[4 * k] = t.x, u[4 * k + 1] = t.y, u[4 * k + 2] = t.z, u[4 * k + 3] = t.w;
+  }
+}
+// link mu of device site n from global memory (read-only path)
+__device__ __forceinline__ void ld_link_g(const float* __restrict__ U20, size_t n, int mu, float u[20]) {
+  const float4* src = reinterpret_cast<const float4*>(U20 + (n * 4 + mu) * 20);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const float4 t = __ldg(src + k);
     u[4 * k] = t.x, u[4 * k + 1] = t.y, u[4 * k + 2] = t.z, u[4 * k + 3] = t.w;
   }
 }
@@ -97,7 +110,7 @@ __device__ __forceinline__ void half_pk(c2 o[12], const c2 h[3], const float u[2
   }
 }
 
-template <int MU, int DIR, bool RESID>
+template <int MU, int DIR, bool RESID, int PP, bool LG>
 __device__ __forceinline__ void hop_pk(const DomP& d, c2 o[12], const float* __restrict__ x,
                                        const float* __restrict__ U20, int N, int r0) {
   using Tb = BTab<MU>;
@@ -106,15 +119,20 @@ __device__ __forceinline__ void hop_pk(const DomP& d, c2 o[12], const float* __r
   float u[20];
   const float* xn = nullptr;
   if (e >= 0) {
-    ld_link(d.sU + MU * 5 * (d.Va + 1) + (DIR > 0 ? d.l : e), d.Va + 1, u);
+    if (LG) ld_link_g(U20, d.s0 + (DIR > 0 ? d.l : e), MU, u);
+    else ld_link(d.sU + MU * 5 * (d.Va + 1) + (DIR > 0 ? d.l : e), d.Va + 1, u);
   } else {
     const size_t n = (size_t)(~e);
     xn = x + n * 24 * N + r0 + 2 * d.p;
-    if (DIR > 0) ld_link(d.sU + MU * 5 * (d.Va + 1) + d.l, d.Va + 1, u);
-    else ld_link(reinterpret_cast<const float4*>(U20 + (n * 4 + MU) * 20), 1, u);
+    if (DIR > 0) {
+      if (LG) ld_link_g(U20, d.s0 + d.l, MU, u);
+      else ld_link(d.sU + MU * 5 * (d.Va + 1) + d.l, d.Va + 1, u);
+    } else {
+      ld_link(reinterpret_cast<const float4*>(U20 + (n * 4 + MU) * 20), 1, u);
+    }
   }
   auto ld = [&](int comp) -> c2 {
-    if (e >= 0) return ldR(d, comp, e);
+    if (e >= 0) return ldR<PP>(d, comp, e);
     return mk2(*reinterpret_cast<const float2*>(xn + (2 * comp) * N),
                *reinterpret_cast<const float2*>(xn + (2 * comp + 1) * N));
   };
@@ -134,7 +152,7 @@ __device__ __forceinline__ void hop_pk(const DomP& d, c2 o[12], const float* __r
 
 // o = D x (RESID: x inside the domain from shared memory, outside from global
 // memory) or o = D_B rho (couplings leaving the domain dropped)
-template <bool RESID>
+template <bool RESID, int PP, bool LG>
 __device__ __forceinline__ void apply_pk(const DomP& d, c2 o[12], const float* __restrict__ Acl,
                                          const float* __restrict__ x, const float* __restrict__ U20, int N,
                                          int r0) {
@@ -145,7 +163,7 @@ __device__ __forceinline__ void apply_pk(const DomP& d, c2 o[12], const float* _
       tc::tmem_ld36(d.tclov + 36 * h, q);
       c2 ps[6];
 #pragma unroll
-      for (int a = 0; a < 6; ++a) ps[a] = ldR(d, 6 * h + a, d.l);
+      for (int a = 0; a < 6; ++a) ps[a] = ldR<PP>(d, 6 * h + a, d.l);
 #pragma unroll
       for (int a = 0; a < 6; ++a) {
         const float2 qa = bc2(q[a]);
@@ -171,14 +189,14 @@ __device__ __forceinline__ void apply_pk(const DomP& d, c2 o[12], const float* _
 #pragma unroll 1
   for (int k = 0; k < 8; ++k) {
     switch (k) {
-      case 0: hop_pk<0, +1, RESID>(d, o, x, U20, N, r0); break;
-      case 1: hop_pk<1, +1, RESID>(d, o, x, U20, N, r0); break;
-      case 2: hop_pk<2, +1, RESID>(d, o, x, U20, N, r0); break;
-      case 3: hop_pk<3, +1, RESID>(d, o, x, U20, N, r0); break;
-      case 4: hop_pk<0, -1, RESID>(d, o, x, U20, N, r0); break;
-      case 5: hop_pk<1, -1, RESID>(d, o, x, U20, N, r0); break;
-      case 6: hop_pk<2, -1, RESID>(d, o, x, U20, N, r0); break;
-      default: hop_pk<3, -1, RESID>(d, o, x, U20, N, r0); break;
+      case 0: hop_pk<0, +1, RESID, PP, LG>(d, o, x, U20, N, r0); break;
+      case 1: hop_pk<1, +1, RESID, PP, LG>(d, o, x, U20, N, r0); break;
+      case 2: hop_pk<2, +1, RESID, PP, LG>(d, o, x, U20, N, r0); break;
+      case 3: hop_pk<3, +1, RESID, PP, LG>(d, o, x, U20, N, r0); break;
+      case 4: hop_pk<0, -1, RESID, PP, LG>(d, o, x, U20, N, r0); break;
+      case 5: hop_pk<1, -1, RESID, PP, LG>(d, o, x, U20, N, r0); break;
+      case 6: hop_pk<2, -1, RESID, PP, LG>(d, o, x, U20, N, r0); break;
+      default: hop_pk<3, -1, RESID, PP, LG>(d, o, x, U20, N, r0); break;
     }
   }
 }
@@ -206,25 +224,26 @@ __device__ __forceinline__ void xb_put(uint32_t ta, const c2 v[12]) {
   }
 }
 
-template <class SB>
-__global__ void __launch_bounds__(kPMaxT, 1) k_sap_pk(const SB* __restrict__ b, float* __restrict__ x,
+template <class SB, int PP, bool LG>
+__global__ void __launch_bounds__(256 * PP, 3 - PP) k_sap_pk(const SB* __restrict__ b, float* __restrict__ x,
                                                       const float* __restrict__ U20, const float* __restrict__ Acl,
                                                       const int* __restrict__ nbr, int N, int Va,
                                                       const int* __restrict__ blist, int n_mr, uint32_t tm_cols,
                                                       int cpb) {
   extern __shared__ float4 smem4[];
   const int T = blockDim.x;
-  float4* sU = smem4;                                                 // [20][Va+1]
-  float4* sR = sU + 20 * (Va + 1);                                    // [12][Va][2]
-  float2* sred = reinterpret_cast<float2*>(sR + 24 * Va);             // [T/32][2][3]
-  int* sN = reinterpret_cast<int*>(sred + (T / 32) * 6);             // [8][Va]
+  constexpr int kG = 2 * PP;                                          // right-hand sides per chunk
+  float4* sU = smem4;                                                 // [20][Va+1] (not LG)
+  float4* sR = LG ? smem4 : sU + 20 * (Va + 1);                       // [12][Va][PP]
+  float2* sred = reinterpret_cast<float2*>(sR + 12 * PP * Va);        // [T/32][PP][3]
+  int* sN = reinterpret_cast<int*>(sred + (T / 32) * PP * 3);        // [8][Va]
   __shared__ uint32_t s_tmem;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   DomP d;
   d.Va = Va;
-  d.l = tid >> 1;
-  d.p = tid & 1;
+  d.l = tid / PP;
+  d.p = tid % PP;
   const bool valid = d.l < Va;
   if (!valid) d.l = 0;  // idle threads read site 0 and write nothing
   d.s0 = (size_t)blist[blockIdx.x / cpb] * Va;
@@ -238,7 +257,8 @@ __global__ void __launch_bounds__(kPMaxT, 1) k_sap_pk(const SB* __restrict__ b, 
   }
   {
     const float4* U4 = reinterpret_cast<const float4*>(U20) + d.s0 * 20;
-    for (int i = tid; i < 20 * Va; i += T) sU[(i % 20) * (Va + 1) + i / 20] = __ldg(U4 + i);
+    if (!LG)
+      for (int i = tid; i < 20 * Va; i += T) sU[(i % 20) * (Va + 1) + i / 20] = __ldg(U4 + i);
     for (int i = tid; i < 8 * Va; i += T) {
       const int l = i >> 3, k = i & 7;
       const int n = __ldg(nbr + (d.s0 + l) * 8 + k) & 0x3fffffff;
@@ -276,25 +296,31 @@ __global__ void __launch_bounds__(kPMaxT, 1) k_sap_pk(const SB* __restrict__ b, 
     tc::tmem_wait_st();
   }
 
-  for (int r0 = (blockIdx.x % cpb) * kPG; r0 < N; r0 += cpb * kPG) {
+  for (int r0 = (blockIdx.x % cpb) * kG; r0 < N; r0 += cpb * kG) {
     // stage x0: one (component c, site l) per unit, the real and imaginary
-    // rows of the chunk's four right-hand sides (two 16-byte loads) become
-    // the two pairs' float4 (re_a, re_b, im_a, im_b)
+    // rows of the chunk's right-hand sides become the pairs' float4
+    // (re_a, re_b, im_a, im_b)
     for (int u = tid; u < 12 * Va; u += T) {
       const int c = u / Va, l = u % Va;
       const float* xs = x + ((d.s0 + l) * 24 + 2 * c) * N + r0;
-      const float4 re = *reinterpret_cast<const float4*>(xs);
-      const float4 im = *reinterpret_cast<const float4*>(xs + N);
-      sR[(c * Va + l) * 2] = make_float4(re.x, re.y, im.x, im.y);
-      sR[(c * Va + l) * 2 + 1] = make_float4(re.z, re.w, im.z, im.w);
+      if (PP == 2) {
+        const float4 re = *reinterpret_cast<const float4*>(xs);
+        const float4 im = *reinterpret_cast<const float4*>(xs + N);
+        sR[(c * Va + l) * 2] = make_float4(re.x, re.y, im.x, im.y);
+        sR[(c * Va + l) * 2 + 1] = make_float4(re.z, re.w, im.z, im.w);
+      } else {
+        const float2 re = *reinterpret_cast<const float2*>(xs);
+        const float2 im = *reinterpret_cast<const float2*>(xs + N);
+        sR[c * Va + l] = make_float4(re.x, re.y, im.x, im.y);
+      }
     }
     __syncthreads();
     c2 o[12];
     // x_B = x0 of the thread's pair -> tensor memory; then q0 = D x0
 #pragma unroll
-    for (int c = 0; c < 12; ++c) o[c] = ldR(d, c, d.l);
+    for (int c = 0; c < 12; ++c) o[c] = ldR<PP>(d, c, d.l);
     xb_put(tm, o);
-    apply_pk<true>(d, o, Acl, x, U20, N, r0);
+    apply_pk<true, PP, LG>(d, o, Acl, x, U20, N, r0);
     tc::tmem_wait_st();
     __syncthreads();  // every read of x0 in shared memory is done
     // rho = b - D x0 at the thread's site
@@ -304,17 +330,17 @@ __global__ void __launch_bounds__(kPMaxT, 1) k_sap_pk(const SB* __restrict__ b, 
       for (int c = 0; c < 12; ++c) {
         const float2 bre = ld_pair(bs + (2 * c) * N), bim = ld_pair(bs + (2 * c + 1) * N);
         const c2 r = mk2(sub2(bre, o[c].re), sub2(bim, o[c].im));
-        sR[(c * Va + d.l) * 2 + d.p] = make_float4(r.re.x, r.re.y, r.im.x, r.im.y);
+        sR[(c * Va + d.l) * PP + d.p] = make_float4(r.re.x, r.re.y, r.im.x, r.im.y);
       }
     }
     __syncthreads();
     for (int step = 0; step < n_mr; ++step) {
       float2 pr = make_float2(0.f, 0.f), pi = pr, pq = pr;
-      apply_pk<false>(d, o, Acl, x, U20, N, r0);  // o = q = D_B rho
+      apply_pk<false, PP, LG>(d, o, Acl, x, U20, N, r0);  // o = q = D_B rho
       if (valid) {
 #pragma unroll
         for (int c = 0; c < 12; ++c) {
-          const c2 r = ldR(d, c, d.l);
+          const c2 r = ldR<PP>(d, c, d.l);
           pr = fma2(o[c].re, r.re, fma2(o[c].im, r.im, pr));
           pi = fma2(o[c].re, r.im, fma2(make_float2(-o[c].im.x, -o[c].im.y), r.re, pi));
           pq = fma2(o[c].re, o[c].re, fma2(o[c].im, o[c].im, pq));
@@ -324,7 +350,7 @@ __global__ void __launch_bounds__(kPMaxT, 1) k_sap_pk(const SB* __restrict__ b, 
       // then over the warps in order: every thread of a pair gets the same
       // alpha for both of its right-hand sides
 #pragma unroll
-      for (int s = 2; s < 32; s <<= 1) {
+      for (int s = PP; s < 32; s <<= 1) {
         pr.x += __shfl_xor_sync(0xffffffffu, pr.x, s);
         pr.y += __shfl_xor_sync(0xffffffffu, pr.y, s);
         pi.x += __shfl_xor_sync(0xffffffffu, pi.x, s);
@@ -332,15 +358,16 @@ __global__ void __launch_bounds__(kPMaxT, 1) k_sap_pk(const SB* __restrict__ b, 
         pq.x += __shfl_xor_sync(0xffffffffu, pq.x, s);
         pq.y += __shfl_xor_sync(0xffffffffu, pq.y, s);
       }
-      if (lane < 2) {
-        sred[(warp * 2 + lane) * 3] = pr;
-        sred[(warp * 2 + lane) * 3 + 1] = pi;
-        sred[(warp * 2 + lane) * 3 + 2] = pq;
+      if (lane < PP) {
+        sred[(warp * PP + lane) * 3] = pr;
+        sred[(warp * PP + lane) * 3 + 1] = pi;
+        sred[(warp * PP + lane) * 3 + 2] = pq;
       }
       __syncthreads();
       float2 a = make_float2(0.f, 0.f), bb = a, cc = a;
       for (int w = 0; w < T / 32; ++w) {
-        const float2 t0 = sred[(w * 2 + d.p) * 3], t1 = sred[(w * 2 + d.p) * 3 + 1], t2 = sred[(w * 2 + d.p) * 3 + 2];
+        const float2 t0 = sred[(w * PP + d.p) * 3], t1 = sred[(w * PP + d.p) * 3 + 1],
+                     t2 = sred[(w * PP + d.p) * 3 + 2];
         a.x += t0.x, a.y += t0.y;
         bb.x += t1.x, bb.y += t1.y;
         cc.x += t2.x, cc.y += t2.y;
@@ -359,7 +386,7 @@ __global__ void __launch_bounds__(kPMaxT, 1) k_sap_pk(const SB* __restrict__ b, 
           for (int i = 0; i < 4; ++i) {
             const int c = 4 * k + i;
             c2 xv = mk2(make_float2(f[4 * i], f[4 * i + 1]), make_float2(f[4 * i + 2], f[4 * i + 3]));
-            c2 r = ldR(d, c, d.l);
+            c2 r = ldR<PP>(d, c, d.l);
             xv.re = fma2(alr, r.re, xv.re);
             xv.re = fma2(nali, r.im, xv.re);
             xv.im = fma2(alr, r.im, xv.im);
@@ -370,7 +397,7 @@ __global__ void __launch_bounds__(kPMaxT, 1) k_sap_pk(const SB* __restrict__ b, 
             r.re = fma2(nali, nq.im, r.re);
             r.im = fma2(alr, nq.im, r.im);
             r.im = fma2(ali, nq.re, r.im);
-            sR[(c * Va + d.l) * 2 + d.p] = make_float4(r.re.x, r.re.y, r.im.x, r.im.y);
+            sR[(c * Va + d.l) * PP + d.p] = make_float4(r.re.x, r.re.y, r.im.x, r.im.y);
             f[4 * i] = xv.re.x, f[4 * i + 1] = xv.re.y, f[4 * i + 2] = xv.im.x, f[4 * i + 3] = xv.im.y;
           }
         }
@@ -405,25 +432,46 @@ __global__ void __launch_bounds__(kPMaxT, 1) k_sap_pk(const SB* __restrict__ b, 
 
 }  // namespace
 
-static int sap_pk_threads(int Va) { return 128 * ((2 * Va + 127) / 128); }
+// the form of the kernel: MRHS_SAP_PK = "2s" (default: two pairs per CTA,
+// links in shared memory), "1g" (one pair per CTA, links from global memory,
+// two CTAs per SM) or "2g"
+struct PkForm {
+  int pp;
+  bool lg;
+};
+static PkForm pk_form() {
+  static const PkForm f = [] {
+    const char* e = std::getenv("MRHS_SAP_PK");
+    const std::string v = e ? e : "";
+    if (v == "1g") return PkForm{1, true};
+    if (v == "2g") return PkForm{2, true};
+    return PkForm{2, false};
+  }();
+  return f;
+}
 
-static size_t sap_pk_smem(int Va, int T) {
-  return sizeof(float4) * (20 * (size_t)(Va + 1) + 24 * (size_t)Va) + sizeof(float2) * (T / 32) * 6 +
-         sizeof(int) * 8 * (size_t)Va;
+static int sap_pk_threads(int Va, int pp) { return 128 * ((pp * Va + 127) / 128); }
+
+static size_t sap_pk_smem(int Va, int T, PkForm f) {
+  return sizeof(float4) * ((f.lg ? 0 : 20 * (size_t)(Va + 1)) + 12 * (size_t)f.pp * Va) +
+         sizeof(float2) * (T / 32) * f.pp * 3 + sizeof(int) * 8 * (size_t)Va;
 }
 
 bool sap_pk_ok(mrhs_ctx c, int nrhs) {
   const int Va = c->g.Va;
-  if (Va > 256 || !c->U20 || nrhs % kPG != 0) return false;
+  const PkForm f = pk_form();
+  if (Va > 256 || !c->U20 || nrhs % (2 * f.pp) != 0) return false;
   int maxsm = 0;
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
-  return sap_pk_smem(Va, sap_pk_threads(Va)) <= (size_t)maxsm;
+  return sap_pk_smem(Va, sap_pk_threads(Va, f.pp), f) <= (size_t)maxsm;
 }
 
 void sap_pk(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int n_sweeps, int n_mr) {
   const int Va = c->g.Va;
-  const int T = sap_pk_threads(Va);
-  const size_t smem = sap_pk_smem(Va, T);
+  const PkForm f = pk_form();
+  const int T = sap_pk_threads(Va, f.pp);
+  const size_t smem = sap_pk_smem(Va, T, f);
+  const int kG = 2 * f.pp;
   // x_B and the clover copy: kPWarpCols columns per thread, (T / 128) warps
   // per lane quarter (at most 4 x 120 = 480 of the 512 columns)
   uint32_t cols = 32;
@@ -436,15 +484,16 @@ void sap_pk(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int n_swee
     const char* e = std::getenv("MRHS_SAP_CPB");
     return e ? std::atoi(e) : 0;
   }();
-  const int cpb = cpb_env > 0 ? std::min(cpb_env, nrhs / kPG) : nrhs / kPG;
+  const int cpb = cpb_env > 0 ? std::min(cpb_env, nrhs / kG) : nrhs / kG;
   for (int sw = 0; sw < n_sweeps; ++sw)
     for (int col = 0; col < 2; ++col) {
       const int* blist = c->blocks_col + (col ? c->ncol[0] : 0);
       Prof pr(c, "sap_pk");
       MRHS_DISPATCH(bdtype, SB, {
-        MRHS_CUDA(cudaFuncSetAttribute(k_sap_pk<SB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_sap_pk<SB><<<c->ncol[col] * cpb, T, smem, c->stream>>>((const SB*)b, (float*)x, c->U20, c->A32, c->nbr,
-                                                                 nrhs, Va, blist, n_mr, cols, cpb);
+        auto kern = f.pp == 1 ? k_sap_pk<SB, 1, true> : f.lg ? k_sap_pk<SB, 2, true> : k_sap_pk<SB, 2, false>;
+        MRHS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<c->ncol[col] * cpb, T, smem, c->stream>>>((const SB*)b, (float*)x, c->U20, c->A32, c->nbr, nrhs, Va,
+                                                         blist, n_mr, cols, cpb);
       });
       MRHS_LAUNCH_CHECK("sap_pk");
     }

@@ -110,7 +110,12 @@ def _child(env, kind, nrhs):
     ({"MRHS_SAP_KERNEL": "tm", "MRHS_SAP_CPB": "1"}, "sap", 8, "sap_tm", 1e-5),
     ({"MRHS_STENCIL_PASSES": "2"}, "apply_D", 8, "dslash_full", 1e-5),
     ({"MRHS_DC_APPLY": "alu"}, "apply_Dc", 16, "apply_dc", 1e-5),
-], ids=["smem-fused8", "smem-fused2", "chunk2", "tm", "tm-cpb1", "passes2", "dc-alu"])
+    ({"MRHS_SAP_PK": "1g"}, "sap", 8, "sap_pk", 1e-5),
+    ({"MRHS_SAP_PK": "1g"}, "sap", 6, "sap_pk", 1e-5),
+    ({"MRHS_SAP_PK": "1g", "MRHS_SAP_CPB": "2"}, "sap", 8, "sap_pk", 1e-5),
+    ({"MRHS_SAP_PK": "2g"}, "sap", 8, "sap_pk", 1e-5),
+], ids=["smem-fused8", "smem-fused2", "chunk2", "tm", "tm-cpb1", "passes2", "dc-alu", "pk1g", "pk1g-6", "pk1g-cpb2",
+        "pk2g"])
 def test_switch_selected_forms(env, kind, nrhs, kernel, tol):
     r = _child(env, kind, nrhs)
     assert kernel in r["kernels"], r
