@@ -781,31 +781,29 @@ void apply_Dc_part(mrhs_ctx c, const DcPart& pt, void* yc, int nrhs, int dtype) 
 // dots and updates are half the size of the plain solve's.
 namespace {
 // the inverse self block of every odd aggregate (CTA b: aggregate
-// blist[b], stored at Dinv[b]), Gauss-Jordan with partial pivoting on [D | 1]
-// in shared memory; *bad set for a singular block
+// blist[b], stored at Dinv[b]): Gauss-Jordan in place with partial pivoting
+// (row interchanges, undone as column interchanges in reverse order at the
+// end) on the block in shared memory; *bad set for a singular block
 template <class R>
 __global__ void k_self_inverse(const cx<R>* __restrict__ Dc, cx<R>* __restrict__ Dinv, const int* __restrict__ blist,
                                int nc, int* bad) {
   extern __shared__ double smem_d[];
-  cx<R>* m = (cx<R>*)smem_d;  // [nc][2nc]
+  cx<R>* m = (cx<R>*)smem_d;  // [nc][nc]
   __shared__ cx<R> s_f[128];
+  __shared__ int s_piv[128];
   __shared__ int s_p;
   const int A = blist[blockIdx.x];
-  const int w2 = 2 * nc;
   const cx<R>* S = Dc + (size_t)A * 9 * nc * nc;
-  for (int e = threadIdx.x; e < nc * w2; e += blockDim.x) {
-    const int i = e / w2, j = e % w2;
-    m[e] = j < nc ? S[i * nc + j] : mk<R>(j - nc == i ? (R)1 : (R)0, 0);
-  }
+  for (int e = threadIdx.x; e < nc * nc; e += blockDim.x) m[e] = S[e];
   __syncthreads();
-  for (int col = 0; col < nc; ++col) {
+  for (int k = 0; k < nc; ++k) {
     if (threadIdx.x < 32) {
-      // pivot: the largest |m[i][col]|^2, i >= col (the first on ties), by warp 0
+      // pivot: the largest |m[i][k]|^2, i >= k (the first on ties), by warp 0
       const int lane = threadIdx.x;
       R best = -1;
       int p = -1;
-      for (int i = col + lane; i < nc; i += 32) {
-        const cx<R> v = m[i * w2 + col];
+      for (int i = k + lane; i < nc; i += 32) {
+        const cx<R> v = m[i * nc + k];
         const R a = v.re * v.re + v.im * v.im;
         if (a > best) best = a, p = i;
       }
@@ -814,7 +812,10 @@ __global__ void k_self_inverse(const cx<R>* __restrict__ Dc, cx<R>* __restrict__
         const int op = __shfl_down_sync(0xffffffffu, p, off);
         if (op >= 0 && (ob > best || (ob == best && op < p))) best = ob, p = op;
       }
-      if (lane == 0) s_p = best > 0 ? p : -1;
+      if (lane == 0) {
+        s_p = best > 0 ? p : -1;
+        s_piv[k] = p;
+      }
     }
     __syncthreads();
     const int p = s_p;
@@ -822,28 +823,41 @@ __global__ void k_self_inverse(const cx<R>* __restrict__ Dc, cx<R>* __restrict__
       if (threadIdx.x == 0) atomicExch(bad, 1);
       return;
     }
-    if (p != col)
-      for (int j = threadIdx.x; j < w2; j += blockDim.x) {
-        const cx<R> t = m[p * w2 + j];
-        m[p * w2 + j] = m[col * w2 + j];
-        m[col * w2 + j] = t;
+    if (p != k)
+      for (int j = threadIdx.x; j < nc; j += blockDim.x) {
+        const cx<R> t = m[p * nc + j];
+        m[p * nc + j] = m[k * nc + j];
+        m[k * nc + j] = t;
       }
     __syncthreads();
-    const cx<R> piv = m[col * w2 + col];
+    const cx<R> piv = m[k * nc + k];
     const R pn = piv.re * piv.re + piv.im * piv.im;
-    const cx<R> pinv = mk<R>(piv.re / pn, -piv.im / pn);
+    const cx<R> d = mk<R>(piv.re / pn, -piv.im / pn);
+    for (int i = threadIdx.x; i < nc; i += blockDim.x) s_f[i] = i == k ? mk<R>(0, 0) : m[i * nc + k];
     __syncthreads();
-    for (int j = threadIdx.x; j < w2; j += blockDim.x) m[col * w2 + j] = m[col * w2 + j] * pinv;
-    for (int i = threadIdx.x; i < nc; i += blockDim.x) s_f[i] = m[i * w2 + col];
+    // row k scaled by d, with d itself in column k
+    for (int j = threadIdx.x; j < nc; j += blockDim.x) m[k * nc + j] = j == k ? d : m[k * nc + j] * d;
     __syncthreads();
-    for (int e = threadIdx.x; e < nc * w2; e += blockDim.x) {
-      const int i = e / w2, j = e % w2;
-      if (i != col) m[e] = m[e] - s_f[i] * m[col * w2 + j];
+    // every other row: minus f_i times row k; column k becomes -f_i d
+    for (int e = threadIdx.x; e < nc * nc; e += blockDim.x) {
+      const int i = e / nc, j = e % nc;
+      if (i == k) continue;
+      m[e] = j == k ? mk<R>(0, 0) - s_f[i] * d : m[e] - s_f[i] * m[k * nc + j];
     }
     __syncthreads();
   }
+  for (int k = nc - 1; k >= 0; --k) {
+    const int p = s_piv[k];
+    if (p != k)
+      for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+        const cx<R> t = m[i * nc + p];
+        m[i * nc + p] = m[i * nc + k];
+        m[i * nc + k] = t;
+      }
+    __syncthreads();
+  }
   cx<R>* out = Dinv + (size_t)blockIdx.x * nc * nc;
-  for (int e = threadIdx.x; e < nc * nc; e += blockDim.x) out[e] = m[(e / nc) * w2 + nc + e % nc];
+  for (int e = threadIdx.x; e < nc * nc; e += blockDim.x) out[e] = m[e];
 }
 
 // y[b] = s Dinv[b] (a[b] - c[b]) for the compact odd row blocks b (c may be
@@ -915,7 +929,7 @@ static void ensure_self_inverses(mrhs_ctx c) {
   MRHS_REQUIRE(nc <= 128, MRHS_ERR_SHAPE, "even-odd coarse solve: 2 ntv must be at most 128");
   if (c->dc_inv && c->dc_inv_version == c->dc_version) return;
   const size_t es = c->work_dtype == MRHS_F64 ? sizeof(cx<double>) : sizeof(cx<float>);
-  const size_t smem = (size_t)nc * 2 * nc * es;
+  const size_t smem = (size_t)nc * nc * es;
   int optin = 0;
   MRHS_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
   MRHS_REQUIRE(smem <= (size_t)optin, MRHS_ERR_SHAPE,
