@@ -9,8 +9,9 @@
 // the links and the clover term of the site are loaded once for both
 // right-hand sides of the pair.
 //   shared memory  rho [12][Va][2] float4 = (re_a, re_b, im_a, im_b) of the
-//                  pair, the domain's halved links [20][Va+1] float4 and the
-//                  domain-local neighbour table [8][Va];
+//                  pair and the domain-local neighbour table [8][Va] (the
+//                  domain's halved links [20][Va+1] float4 too in the "2s"
+//                  form; by default the links are read through L1);
 //   tensor memory  the running solution x_B of the thread's pair
 //                  (48 columns: 12 components x (re_a, re_b, im_a, im_b)) and
 //                  a copy of the clover term of the thread's site (72
@@ -432,9 +433,13 @@ __global__ void __launch_bounds__(256 * PP, 3 - PP) k_sap_pk(const SB* __restric
 
 }  // namespace
 
-// the form of the kernel: MRHS_SAP_PK = "2s" (default: two pairs per CTA,
-// links in shared memory), "1g" (one pair per CTA, links from global memory,
-// two CTAs per SM) or "2g"
+// the form of the kernel: MRHS_SAP_PK = "2g" (default: two pairs per CTA,
+// links read through L1), "2s" (links staged in shared memory) or "1g" (one
+// pair per CTA, two CTAs per SM). Measured at 48^3x96 with 32 right-hand
+// sides: 83.2 ms per colour launch (2g), 88.8 (2s), 108.7 (1g): the links of
+// a domain stay in L1 across the hops, and staging them cost more than it
+// saved; two CTAs per SM each restage the clover term and re-read the links
+// for half the right-hand sides.
 struct PkForm {
   int pp;
   bool lg;
@@ -444,8 +449,8 @@ static PkForm pk_form() {
     const char* e = std::getenv("MRHS_SAP_PK");
     const std::string v = e ? e : "";
     if (v == "1g") return PkForm{1, true};
-    if (v == "2g") return PkForm{2, true};
-    return PkForm{2, false};
+    if (v == "2s") return PkForm{2, false};
+    return PkForm{2, true};
   }();
   return f;
 }
