@@ -279,6 +279,19 @@ def nn_forward(dims, U, widths, W, bias, x, linear=False):
     return out
 
 
+def nn_forward_bf16act(dims, U, widths, W, bias, x, linear=False):
+    """nn_forward with the input of every layer rounded to bfloat16 (via FP32,
+    ties to even) before the layer."""
+    c0, c1, c2, c3 = widths
+    U, W, x = _c(U), _c(W), _c(x)
+    bias = np.ascontiguousarray(bias, dtype=np.float64)
+    nrhs = x.shape[0]
+    out = np.zeros((nrhs, _vol(dims), c3 * 3), np.complex128)
+    _check(lib().ora_nn_forward_bf16act(_i4(dims), _p(U), c0, c1, c2, c3, _p(W), _p(bias), int(linear), _p(x),
+                                        _p(out), nrhs), "nn_forward_bf16act")
+    return out
+
+
 def nn_backward(dims, U, widths, W, bias, x, dout, linear=False, want_din=False):
     """Returns (gW, gb, din) with g = dL/dRe + i dL/dIm for complex parameters."""
     c0, c1, c2, c3 = widths

@@ -31,6 +31,7 @@
  *                neighbour aggregate, 5+mu for the -mu neighbour aggregate
  */
 #include <complex.h>
+#include <stdint.h>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -1478,9 +1479,41 @@ static size_t nn_wsize(int c0, int c1, int c2, int c3) {
   return (size_t)9 * ((size_t)c1 * c0 + (size_t)c2 * c1 + (size_t)c3 * c2);
 }
 
+/* x rounded to the nearest FP32 value and then to the nearest bfloat16
+ * (8 significant bits; ties to the even bit pattern), real and imaginary
+ * parts separately: the operand precision of a bf16 tensor-core product */
+static double round_bf16(double x) {
+  float f = (float)x;
+  uint32_t u;
+  memcpy(&u, &f, sizeof u);
+  u += 0x7fffu + ((u >> 16) & 1u);
+  u &= 0xffff0000u;
+  memcpy(&f, &u, sizeof f);
+  return (double)f;
+}
+static void round_field_bf16(cplx* h, size_t n) {
+  for (size_t i = 0; i < n; ++i) h[i] = round_bf16(creal(h[i])) + I * round_bf16(cimag(h[i]));
+}
+
+static int nn_forward_impl(const int* dims, const cplx* U, int c0, int c1, int c2, int c3, const cplx* W,
+                           const double* bias, int linear, int round_in, const cplx* in, cplx* out, int nrhs);
+
 /* out = net(in) for nrhs right-hand sides; in [nrhs][V][c0*3], out [nrhs][V][c3*3] */
 int ora_nn_forward(const int* dims, const cplx* U, int c0, int c1, int c2, int c3, const cplx* W,
                    const double* bias, int linear, const cplx* in, cplx* out, int nrhs) {
+  return nn_forward_impl(dims, U, c0, c1, c2, c3, W, bias, linear, 0, in, out, nrhs);
+}
+
+/* the same with the input of every layer (the network input and the two
+ * hidden fields after modrelu) rounded to bfloat16 before the layer: the
+ * arithmetic of an inference whose layer products take bf16 operands */
+int ora_nn_forward_bf16act(const int* dims, const cplx* U, int c0, int c1, int c2, int c3, const cplx* W,
+                           const double* bias, int linear, const cplx* in, cplx* out, int nrhs) {
+  return nn_forward_impl(dims, U, c0, c1, c2, c3, W, bias, linear, 1, in, out, nrhs);
+}
+
+static int nn_forward_impl(const int* dims, const cplx* U, int c0, int c1, int c2, int c3, const cplx* W,
+                           const double* bias, int linear, int round_in, const cplx* in, cplx* out, int nrhs) {
   geom_t g;
   const int one[4] = {1, 1, 1, 1};
   if (geom_init(&g, dims, one)) return -1;
@@ -1494,19 +1527,25 @@ int ora_nn_forward(const int* dims, const cplx* U, int c0, int c1, int c2, int c
   cplx* h1 = (cplx*)malloc(sizeof(cplx) * V * c1 * 3);
   cplx* z2 = (cplx*)malloc(sizeof(cplx) * V * c2 * 3);
   cplx* h2 = (cplx*)malloc(sizeof(cplx) * V * c2 * 3);
+  cplx* h0 = (cplx*)malloc(sizeof(cplx) * V * c0 * 3);
   for (int r = 0; r < nrhs; ++r) {
-    covconv(&g, U, c0, c1, W0, in + (size_t)r * V * c0 * 3, z1);
+    memcpy(h0, in + (size_t)r * V * c0 * 3, sizeof(cplx) * V * c0 * 3);
+    if (round_in) round_field_bf16(h0, V * c0 * 3);
+    covconv(&g, U, c0, c1, W0, h0, z1);
     if (linear) memcpy(h1, z1, sizeof(cplx) * V * c1 * 3);
     else modrelu(g.V, c1, b1, z1, h1);
+    if (round_in) round_field_bf16(h1, V * c1 * 3);
     covconv(&g, U, c1, c2, W1, h1, z2);
     if (linear) memcpy(h2, z2, sizeof(cplx) * V * c2 * 3);
     else modrelu(g.V, c2, b2, z2, h2);
+    if (round_in) round_field_bf16(h2, V * c2 * 3);
     covconv(&g, U, c2, c3, W2, h2, out + (size_t)r * V * c3 * 3);
   }
   free(z1);
   free(h1);
   free(z2);
   free(h2);
+  free(h0);
   return 0;
 }
 

@@ -148,3 +148,81 @@ def test_loss_gradient_by_central_differences():
             vm[r, s, c] -= h * unit
             fd = (oracle.nn_loss(dims, agg, U, A, P, vp, lam)[0] - oracle.nn_loss(dims, agg, U, A, P, vm, lam)[0]) / (2 * h)
             assert abs(fd - part) <= 1e-6 * max(1.0, abs(fd))
+
+
+def _bf16(a):
+    """complex array rounded part by part to FP32 and then to bfloat16 by
+    torch (round to nearest, ties to even)"""
+    import torch
+    re = torch.from_numpy(np.ascontiguousarray(a.real)).float().to(torch.bfloat16).double().numpy()
+    im = torch.from_numpy(np.ascontiguousarray(a.imag)).float().to(torch.bfloat16).double().numpy()
+    return re + 1j * im
+
+
+def _identity_weights(widths=(4, 4, 4, 4), first=None):
+    nw, nb = oracle.nn_sizes(widths)
+    W = np.zeros(nw, np.complex128)
+    for layer in range(3):
+        off = layer * 9 * 16
+        if layer == 0 and first is not None:
+            W[:first.size] = first
+            continue
+        for c in range(4):
+            W[off + c * 4 + c] = 1.0
+    return W, nb
+
+
+def test_bf16_activation_rounding_is_round_to_nearest_even():
+    """The identity network with bf16-rounded layer inputs returns its input
+    rounded once to bfloat16 (rounding is idempotent), equal bit for bit to
+    torch's conversion, on Gaussian values and on exact ties between two
+    bfloat16 numbers (FP32 values whose low 16 bits are 0x8000, with even
+    and odd upper halves)."""
+    torch = pytest.importorskip("torch")
+    W, nb = _identity_weights()
+    U = inputs.gauge_field(DIMS, 0.5, 61)
+    x = inputs.gaussian_field((1, vol(DIMS), 12), 62)
+    rng = np.random.default_rng(63)
+    hi = rng.integers(0x3f00, 0x4100, size=x.size).astype(np.uint32)
+    ties = ((hi << 16) | 0x8000).astype(np.uint32).view(np.float32).astype(np.float64)
+    x = x.copy()
+    x.real.reshape(-1)[::2] = ties[::2]  # half of the real parts exact ties
+    y = oracle.nn_forward_bf16act(DIMS, U, (4, 4, 4, 4), W, np.zeros(nb), x, linear=True)
+    assert np.array_equal(y, _bf16(x))
+    assert not np.array_equal(y, x)
+    del torch
+
+
+def test_bf16_activation_rounding_placement():
+    """With layers 2 and 3 the identity and a random first layer (all nine
+    blocks), the rounded-input forward equals bf16(layer1(bf16(x))) bit for
+    bit: the network input is rounded before layer 1 and the hidden fields
+    before layers 2 and 3, and nothing else is."""
+    pytest.importorskip("torch")
+    rng = np.random.default_rng(71)
+    first = rng.standard_normal(9 * 16) + 1j * rng.standard_normal(9 * 16)
+    W, nb = _identity_weights(first=first)
+    U = inputs.gauge_field(DIMS, 0.5, 72)
+    x = inputs.gaussian_field((2, vol(DIMS), 12), 73)
+    y = oracle.nn_forward_bf16act(DIMS, U, (4, 4, 4, 4), W, np.zeros(nb), x, linear=True)
+    ref = _bf16(oracle.nn_forward(DIMS, U, (4, 4, 4, 4), W, np.zeros(nb), _bf16(x), linear=True))
+    assert np.array_equal(y, ref)
+    # and it differs from the unrounded forward by bf16-sized amounts only
+    plain = oracle.nn_forward(DIMS, U, (4, 4, 4, 4), W, np.zeros(nb), x, linear=True)
+    assert 1e-5 < np.linalg.norm(y - plain) / np.linalg.norm(plain) < 2 ** -7
+
+
+def test_bf16_activation_output_not_rounded():
+    """Layers 1 and 2 the identity, layer 3 random: the rounded-input forward
+    is the plain forward of bf16(x) bit for bit, so the output of the last
+    layer is not rounded."""
+    pytest.importorskip("torch")
+    rng = np.random.default_rng(81)
+    last = rng.standard_normal(9 * 16) + 1j * rng.standard_normal(9 * 16)
+    W, nb = _identity_weights()
+    W[2 * 9 * 16:] = last
+    U = inputs.gauge_field(DIMS, 0.5, 82)
+    x = inputs.gaussian_field((2, vol(DIMS), 12), 83)
+    y = oracle.nn_forward_bf16act(DIMS, U, (4, 4, 4, 4), W, np.zeros(nb), x, linear=True)
+    assert np.array_equal(y, oracle.nn_forward(DIMS, U, (4, 4, 4, 4), W, np.zeros(nb), _bf16(x), linear=True))
+    assert not np.array_equal(y, _bf16(y))
