@@ -80,6 +80,7 @@ _SIGS = {
     "mrhs_nn_get_grads": (_I, [_VP, _VP]),
     "mrhs_nn_zero_grads": (_I, [_VP]),
     "mrhs_nn_forward": (_I, [_VP, _VP, _VP, _I]),
+    "mrhs_nn_infer": (_I, [_VP, _VP, _VP, _I]),
     "mrhs_nn_backward": (_I, [_VP, _VP, _VP, _I]),
     "mrhs_nn_loss": (_I, [_VP, _VP, _VP, _I, _D, ctypes.POINTER(_D), _VP]),
     "mrhs_nn_adam": (_I, [_VP, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _I]),
@@ -448,6 +449,12 @@ def mrhs_nn_forward(ctx, x, y, nrhs):
     _dev(ctx, x, nrhs, MRHS_F32, 0, "mrhs_nn_forward in")
     _dev(ctx, y, nrhs, MRHS_F32, 0, "mrhs_nn_forward out")
     return _check(ctx, lib().mrhs_nn_forward(ctx, _ptr(x), _ptr(y), int(nrhs)))
+
+
+def mrhs_nn_infer(ctx, x, y, nrhs):
+    _dev(ctx, x, nrhs, MRHS_F32, 0, "mrhs_nn_infer in")
+    _dev(ctx, y, nrhs, MRHS_F32, 0, "mrhs_nn_infer out")
+    return _check(ctx, lib().mrhs_nn_infer(ctx, _ptr(x), _ptr(y), int(nrhs)))
 
 
 def mrhs_nn_backward(ctx, gout, gin, nrhs):

@@ -307,6 +307,10 @@ struct DcPart {
 // coarse stencil on the tensor cores; sets dflag[3] if a pipeline wait ran out
 bool apply_Dc_tc(mrhs_ctx c, const DcPart& part, void* yc, int nrhs, bool split);
 void apply_Dc_part(mrhs_ctx c, const DcPart& part, void* yc, int nrhs, int dtype);
+// nn_tc.cu: one network layer for inference with bf16 tensor-core mixing
+// (false: shape outside the kernel's); sets dflag[6] if a wait ran out
+bool covconv_tc(mrhs_ctx c, const float* h, float* z, const float* W, int cin, int cout, int N);
+void check_nn_tc_timeout(mrhs_ctx c);
 void dc_images_build(mrhs_ctx c);
 void check_tc_timeout(mrhs_ctx c);
 void restrict_(mrhs_ctx c, const void* v, void* vc, int nrhs, int dtype);

@@ -531,6 +531,14 @@ void refresh_compute_weights(mrhs_ctx c, NNState& s) {
 
 }  // namespace
 
+// one layer for inference: the channel mixing on the tensor cores when the
+// weights are bf16 (bf16 activations as operands), else on the CUDA cores
+void infer_layer(mrhs_ctx c, const NNState& s, const float* h, float* z, int l, int N) {
+  const float* W = s.Wc + 2 * layer_off(s, l);
+  if (s.bf16 && covconv_tc(c, h, z, W, s.C[l], s.C[l + 1], N)) return;
+  covconv(c, h, z, W, s.C[l], s.C[l + 1], N);
+}
+
 // inference only (no activations kept): right-hand sides in chunks, two
 // ping-pong buffers for the hidden layers
 void nn_infer_chunked(mrhs_ctx c, const float* in, float* out, int N, int chunk) {
@@ -548,14 +556,14 @@ void nn_infer_chunked(mrhs_ctx c, const float* in, float* out, int N, int chunk)
     const int nr = std::min(cs, N - r0);
     k_gather_rhs<<<grid_for(V * 12 * 2 * nr, 256), 256, 0, c->stream>>>(in, N, r0, xin, nr, V * 12);
     MRHS_LAUNCH_CHECK("gather_rhs");
-    covconv(c, xin, a, s.Wc + 2 * layer_off(s, 0), s.C[0], s.C[1], nr);
+    infer_layer(c, s, xin, a, 0, nr);
     k_modrelu<<<grid_for(V * s.C[1] * nr, 256), 256, 0, c->stream>>>(a, a, bias, s.C[1], nr, V * s.C[1] * nr);
     MRHS_LAUNCH_CHECK("modrelu");
-    covconv(c, a, b, s.Wc + 2 * layer_off(s, 1), s.C[1], s.C[2], nr);
+    infer_layer(c, s, a, b, 1, nr);
     k_modrelu<<<grid_for(V * s.C[2] * nr, 256), 256, 0, c->stream>>>(b, b, bias + s.C[1], s.C[2], nr,
                                                                      V * s.C[2] * nr);
     MRHS_LAUNCH_CHECK("modrelu");
-    covconv(c, b, xout, s.Wc + 2 * layer_off(s, 2), s.C[2], s.C[3], nr);
+    infer_layer(c, s, b, xout, 2, nr);
     k_scatter_rhs<<<grid_for(V * 12 * 2 * nr, 256), 256, 0, c->stream>>>(xout, nr, out, N, r0, V * 12);
     MRHS_LAUNCH_CHECK("scatter_rhs");
   }
@@ -577,6 +585,7 @@ void nn_infer(mrhs_ctx c, const float* in, float* out, int N) {
   int chunk = 8;
   while (chunk > 1 && (size_t)chunk * per_rhs > avail / 2) --chunk;
   nn_infer_chunked(c, in, out, N, chunk);
+  check_nn_tc_timeout(c);
 }
 }  // namespace mrhs
 
@@ -668,6 +677,16 @@ int mrhs_nn_forward(mrhs_ctx c, const void* in, void* out, int nrhs) {
     require_dev(c, out, "mrhs_nn_forward out");
     MRHS_REQUIRE(c->have_gauge, MRHS_ERR_STATE, "nn forward before mrhs_set_gauge");
     nn_forward_impl(c, (const float*)in, (float*)out, nrhs);
+  });
+}
+
+int mrhs_nn_infer(mrhs_ctx c, const void* in, void* out, int nrhs) {
+  return guarded(c, [&] {
+    MRHS_REQUIRE(c && in && out && nrhs >= 1, MRHS_ERR_ARG, "bad argument");
+    require_dev(c, in, "mrhs_nn_infer in");
+    require_dev(c, out, "mrhs_nn_infer out");
+    MRHS_REQUIRE(c->have_gauge, MRHS_ERR_STATE, "nn inference before mrhs_set_gauge");
+    nn_infer(c, (const float*)in, (float*)out, nrhs);
   });
 }
 
