@@ -280,8 +280,9 @@ def nn_forward(dims, U, widths, W, bias, x, linear=False):
 
 
 def nn_forward_bf16act(dims, U, widths, W, bias, x, linear=False):
-    """nn_forward with the input of every layer rounded to bfloat16 (via FP32,
-    ties to even) before the layer."""
+    """nn_forward with the operands of every layer's channel mixing in
+    bfloat16: each transported input triplet rounded (via FP32, ties to even)
+    before it meets the weights."""
     c0, c1, c2, c3 = widths
     U, W, x = _c(U), _c(W), _c(x)
     bias = np.ascontiguousarray(bias, dtype=np.float64)

@@ -1428,7 +1428,23 @@ double ora_relres(const int* dims, const cplx* U, const cplx* A, const cplx* b, 
  * Gradients use G = dL/dRe(p) + i dL/dIm(p) for complex parameters p and
  * dL/db for the biases. */
 
-static void covconv(const geom_t* g, const cplx* U, int cin, int cout, const cplx* W, const cplx* h, cplx* z) {
+/* x rounded to the nearest FP32 value and then to the nearest bfloat16
+ * (8 significant bits; ties to the even bit pattern), real and imaginary
+ * parts separately: the operand precision of a bf16 tensor-core product */
+static double round_bf16(double x) {
+  float f = (float)x;
+  uint32_t u;
+  memcpy(&u, &f, sizeof u);
+  u += 0x7fffu + ((u >> 16) & 1u);
+  u &= 0xffff0000u;
+  memcpy(&f, &u, sizeof f);
+  return (double)f;
+}
+
+/* one layer; round_t != 0: every transported input triplet s_k T_k h(n_k)[c']
+ * rounded to bfloat16 (part by part) before the channel mixing */
+static void covconv_r(const geom_t* g, const cplx* U, int cin, int cout, const cplx* W, const cplx* h, cplx* z,
+                      int round_t) {
 #pragma omp parallel for schedule(static)
   for (int s = 0; s < g->V; ++s) {
     cplx* zs = z + (size_t)s * cout * 3;
@@ -1454,6 +1470,7 @@ static void covconv(const geom_t* g, const cplx* U, int cin, int cout, const cpl
           t[a] = 0;
           for (int b = 0; b < 3; ++b) t[a] += T.m[a][b] * hn[cp * 3 + b];
           t[a] *= sg;
+          if (round_t) t[a] = round_bf16(creal(t[a])) + I * round_bf16(cimag(t[a]));
         }
         for (int c = 0; c < cout; ++c) {
           cplx w = W[((size_t)k * cout + c) * cin + cp];
@@ -1462,6 +1479,10 @@ static void covconv(const geom_t* g, const cplx* U, int cin, int cout, const cpl
       }
     }
   }
+}
+
+static void covconv(const geom_t* g, const cplx* U, int cin, int cout, const cplx* W, const cplx* h, cplx* z) {
+  covconv_r(g, U, cin, cout, W, h, z, 0);
 }
 
 static void modrelu(int V, int C, const double* bias, const cplx* z, cplx* h) {
@@ -1479,22 +1500,6 @@ static size_t nn_wsize(int c0, int c1, int c2, int c3) {
   return (size_t)9 * ((size_t)c1 * c0 + (size_t)c2 * c1 + (size_t)c3 * c2);
 }
 
-/* x rounded to the nearest FP32 value and then to the nearest bfloat16
- * (8 significant bits; ties to the even bit pattern), real and imaginary
- * parts separately: the operand precision of a bf16 tensor-core product */
-static double round_bf16(double x) {
-  float f = (float)x;
-  uint32_t u;
-  memcpy(&u, &f, sizeof u);
-  u += 0x7fffu + ((u >> 16) & 1u);
-  u &= 0xffff0000u;
-  memcpy(&f, &u, sizeof f);
-  return (double)f;
-}
-static void round_field_bf16(cplx* h, size_t n) {
-  for (size_t i = 0; i < n; ++i) h[i] = round_bf16(creal(h[i])) + I * round_bf16(cimag(h[i]));
-}
-
 static int nn_forward_impl(const int* dims, const cplx* U, int c0, int c1, int c2, int c3, const cplx* W,
                            const double* bias, int linear, int round_in, const cplx* in, cplx* out, int nrhs);
 
@@ -1504,9 +1509,10 @@ int ora_nn_forward(const int* dims, const cplx* U, int c0, int c1, int c2, int c
   return nn_forward_impl(dims, U, c0, c1, c2, c3, W, bias, linear, 0, in, out, nrhs);
 }
 
-/* the same with the input of every layer (the network input and the two
- * hidden fields after modrelu) rounded to bfloat16 before the layer: the
- * arithmetic of an inference whose layer products take bf16 operands */
+/* the same with the operands of every layer's channel mixing in bfloat16:
+ * each transported input triplet s_k T_k(x) h(n_k(x))[c'] (the transport in
+ * full precision) rounded to bfloat16 before it is multiplied by the weights,
+ * the arithmetic of an inference whose layer products take bf16 operands */
 int ora_nn_forward_bf16act(const int* dims, const cplx* U, int c0, int c1, int c2, int c3, const cplx* W,
                            const double* bias, int linear, const cplx* in, cplx* out, int nrhs) {
   return nn_forward_impl(dims, U, c0, c1, c2, c3, W, bias, linear, 1, in, out, nrhs);
@@ -1527,25 +1533,19 @@ static int nn_forward_impl(const int* dims, const cplx* U, int c0, int c1, int c
   cplx* h1 = (cplx*)malloc(sizeof(cplx) * V * c1 * 3);
   cplx* z2 = (cplx*)malloc(sizeof(cplx) * V * c2 * 3);
   cplx* h2 = (cplx*)malloc(sizeof(cplx) * V * c2 * 3);
-  cplx* h0 = (cplx*)malloc(sizeof(cplx) * V * c0 * 3);
   for (int r = 0; r < nrhs; ++r) {
-    memcpy(h0, in + (size_t)r * V * c0 * 3, sizeof(cplx) * V * c0 * 3);
-    if (round_in) round_field_bf16(h0, V * c0 * 3);
-    covconv(&g, U, c0, c1, W0, h0, z1);
+    covconv_r(&g, U, c0, c1, W0, in + (size_t)r * V * c0 * 3, z1, round_in);
     if (linear) memcpy(h1, z1, sizeof(cplx) * V * c1 * 3);
     else modrelu(g.V, c1, b1, z1, h1);
-    if (round_in) round_field_bf16(h1, V * c1 * 3);
-    covconv(&g, U, c1, c2, W1, h1, z2);
+    covconv_r(&g, U, c1, c2, W1, h1, z2, round_in);
     if (linear) memcpy(h2, z2, sizeof(cplx) * V * c2 * 3);
     else modrelu(g.V, c2, b2, z2, h2);
-    if (round_in) round_field_bf16(h2, V * c2 * 3);
-    covconv(&g, U, c2, c3, W2, h2, out + (size_t)r * V * c3 * 3);
+    covconv_r(&g, U, c2, c3, W2, h2, out + (size_t)r * V * c3 * 3, round_in);
   }
   free(z1);
   free(h1);
   free(z2);
   free(h2);
-  free(h0);
   return 0;
 }
 

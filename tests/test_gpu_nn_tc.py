@@ -1,7 +1,8 @@
 """Inference of the learned generator with the channel mixing on the tensor
 cores (mrhs_nn_infer with bf16 weights: bf16 operands, FP32 products and
-sums) against the oracle's forward with every layer input rounded to bf16
-(oracle.nn_forward_bf16act, pinned in tests/test_oracle_nn.py).
+sums) against the oracle's forward with every transported operand rounded to
+bf16 before it meets the weights (oracle.nn_forward_bf16act, pinned in
+tests/test_oracle_nn.py).
 
 - Exact case: links that are monomial matrices with entries in {±1, ±i},
   weights with few bits (multiples of 1/2, most of them zero), inputs in
@@ -10,10 +11,10 @@ sums) against the oracle's forward with every layer input rounded to bf16
   so both sides take the same bf16 rounding decisions and the outputs agree
   bit for bit; a wrong index, sign, transpose or rounding place changes them.
 - Generic case: a rough SU(3) field, Gaussian inputs, random weights and
-  biases. FP32 sums against FP64 sums move some bf16 rounding decisions of the
-  hidden fields; measured with the oracle alone, a relative change of 1e-6 in
-  the input moves the output by 5e-4, while rounding the layer inputs at all
-  moves it by 2.9e-3. Bound: 1e-3.
+  biases. FP32 transports and sums against FP64 ones move some bf16 rounding
+  decisions; measured with the oracle alone, a relative change of 1e-6 in the
+  input moves the output by 5.4e-4, while rounding the operands at all moves
+  it by 2.9e-3. Bound: 1.5e-3.
 - FP32 weights take the CUDA-core layer: against the unrounded oracle at 1e-4.
 """
 import numpy as np
@@ -110,7 +111,7 @@ def test_infer_tensor_cores_generic(widths, nrhs, scale):
     y, ran = infer(lat, x, nrhs)
     assert "nn_covconv_tc" in ran, ran
     ref = oracle.nn_forward_bf16act(DIMS, U, widths, W, b, x)
-    assert rel(y, ref) < 1e-3
+    assert rel(y, ref) < 1.5e-3
     lat.close()
 
 

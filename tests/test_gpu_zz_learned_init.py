@@ -12,11 +12,11 @@ perturbation of the vectors to P about one to one, and to D_c reduced
 (measured with the oracle on these inputs: 1e-5 on the vectors gives 1.4e-5 on
 P and 9e-7 on D_c).
 bf16 weights: the tensor-core layers with bf16 operands, against the oracle's
-forward with bf16-rounded layer inputs. The network input is the FP32 smoother
+forward with bf16-rounded operands. The network input is the FP32 smoother
 output, which differs from the oracle's by up to 1e-5 relative, and that
 moves some bf16 rounding decisions: measured with the oracle on these inputs,
-1e-6 and 1e-5 relative noise on the network input move the vectors by 5.0e-4
-and 1.4e-3, P by 5.1e-4 and 1.4e-3, D_c by 3.4e-5 and 9.3e-5. Bounds: 3e-3 on
+1e-6 and 1e-5 relative noise on the network input move the vectors by 5.8e-4
+and 1.4e-3, P by 5.8e-4 and 1.4e-3, D_c by 3.9e-5 and 9.5e-5. Bounds: 3e-3 on
 the vectors and P, 3e-4 on D_c. (The tensor-core layer itself is checked bit
 for bit in tests/test_gpu_nn_tc.py.)"""
 import numpy as np

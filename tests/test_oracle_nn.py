@@ -173,7 +173,7 @@ def _identity_weights(widths=(4, 4, 4, 4), first=None):
 
 
 def test_bf16_activation_rounding_is_round_to_nearest_even():
-    """The identity network with bf16-rounded layer inputs returns its input
+    """The identity network with bf16 operands returns its input
     rounded once to bfloat16 (rounding is idempotent), equal bit for bit to
     torch's conversion, on Gaussian values and on exact ties between two
     bfloat16 numbers (FP32 values whose low 16 bits are 0x8000, with even
@@ -193,16 +193,48 @@ def test_bf16_activation_rounding_is_round_to_nearest_even():
     del torch
 
 
+def _monomial_links(seed):
+    """[V][4][3][3] matrices P diag(p), P a permutation, p in {±1, ±i}: the
+    transport by them is exact and commutes with any rounding"""
+    rng = np.random.default_rng(seed)
+    U = np.zeros((vol(DIMS), 4, 3, 3), np.complex128)
+    ph = np.array([1, 1j, -1, -1j])
+    for s in range(vol(DIMS)):
+        for mu in range(4):
+            U[s, mu, np.arange(3), rng.permutation(3)] = ph[rng.integers(0, 4, 3)]
+    return U
+
+
+def test_bf16_rounding_after_the_transport():
+    """The rounded operand is the transported triplet s_k T_k h(n_k), not the
+    layer input: with layer 1 the identity on the +x hop only (k = 1) and
+    layers 2 and 3 the identity at the site, a rough SU(3) field gives
+    bf16(layer1(x)) bit for bit, which differs from rounding x first."""
+    pytest.importorskip("torch")
+    first = np.zeros(9 * 16, np.complex128)
+    for c in range(4):
+        first[1 * 16 + c * 4 + c] = 1.0  # k = 1 block of layer 1
+    W, nb = _identity_weights(first=first)
+    U = inputs.gauge_field(DIMS, 0.5, 91)
+    x = inputs.gaussian_field((2, vol(DIMS), 12), 92)
+    y = oracle.nn_forward_bf16act(DIMS, U, (4, 4, 4, 4), W, np.zeros(nb), x, linear=True)
+    hop = oracle.nn_forward(DIMS, U, (4, 4, 4, 4), W, np.zeros(nb), x, linear=True)
+    assert np.array_equal(y, _bf16(hop))
+    before = _bf16(oracle.nn_forward(DIMS, U, (4, 4, 4, 4), W, np.zeros(nb), _bf16(x), linear=True))
+    assert not np.array_equal(y, before)
+
+
 def test_bf16_activation_rounding_placement():
-    """With layers 2 and 3 the identity and a random first layer (all nine
-    blocks), the rounded-input forward equals bf16(layer1(bf16(x))) bit for
-    bit: the network input is rounded before layer 1 and the hidden fields
-    before layers 2 and 3, and nothing else is."""
+    """With layers 2 and 3 the identity, a random first layer (all nine
+    blocks) and links whose transport commutes with rounding, the
+    bf16-operand forward equals bf16(layer1(bf16(x))) bit for bit: the
+    operands of layer 1 and of layers 2 and 3 are rounded, and nothing else
+    is."""
     pytest.importorskip("torch")
     rng = np.random.default_rng(71)
     first = rng.standard_normal(9 * 16) + 1j * rng.standard_normal(9 * 16)
     W, nb = _identity_weights(first=first)
-    U = inputs.gauge_field(DIMS, 0.5, 72)
+    U = _monomial_links(72)
     x = inputs.gaussian_field((2, vol(DIMS), 12), 73)
     y = oracle.nn_forward_bf16act(DIMS, U, (4, 4, 4, 4), W, np.zeros(nb), x, linear=True)
     ref = _bf16(oracle.nn_forward(DIMS, U, (4, 4, 4, 4), W, np.zeros(nb), _bf16(x), linear=True))
@@ -213,15 +245,15 @@ def test_bf16_activation_rounding_placement():
 
 
 def test_bf16_activation_output_not_rounded():
-    """Layers 1 and 2 the identity, layer 3 random: the rounded-input forward
-    is the plain forward of bf16(x) bit for bit, so the output of the last
-    layer is not rounded."""
+    """Layers 1 and 2 the identity, layer 3 random, links whose transport
+    commutes with rounding: the bf16-operand forward is the plain forward of
+    bf16(x) bit for bit, so the output of the last layer is not rounded."""
     pytest.importorskip("torch")
     rng = np.random.default_rng(81)
     last = rng.standard_normal(9 * 16) + 1j * rng.standard_normal(9 * 16)
     W, nb = _identity_weights()
     W[2 * 9 * 16:] = last
-    U = inputs.gauge_field(DIMS, 0.5, 82)
+    U = _monomial_links(82)
     x = inputs.gaussian_field((2, vol(DIMS), 12), 83)
     y = oracle.nn_forward_bf16act(DIMS, U, (4, 4, 4, 4), W, np.zeros(nb), x, linear=True)
     assert np.array_equal(y, oracle.nn_forward(DIMS, U, (4, 4, 4, 4), W, np.zeros(nb), _bf16(x), linear=True))
