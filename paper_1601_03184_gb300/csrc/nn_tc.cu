@@ -15,8 +15,9 @@
 // Persistent CTAs of 16 warps: the nine A_k sit in shared memory for the
 // whole launch; the CUDA cores build B_{k+1} (colour transport, sign, bf16
 // rounding) into the other buffer while the tensor core multiplies B_k; the
-// step's transports of the tile's sites are staged in shared memory first,
-// and every thread issues the loads of four operand items together. The
+// transports of the tile's sites for all nine steps are staged in shared
+// memory at the start of the tile, and the inputs of step k+1 are loaded into
+// registers while step k is computed. The
 // operands are bf16: the weights are the bf16-rounded compute copy (exact),
 // the activations are rounded once to bf16 when they enter B; products and
 // sums are FP32.
@@ -32,8 +33,8 @@ constexpr int kNnThreads = 512;
 constexpr int kNnRows = 128;        // MMA M
 constexpr int kNnCols = 192;        // MMA N: 3 colours x (sites x rhs) of a tile, padded
 constexpr uint32_t kNnWait = 1u << 20;
-constexpr int kNnMaxS = 64;         // sites per tile (64 / rhs)
-constexpr int kNnUnroll = 4;        // operand items per thread whose loads are issued together
+constexpr int kNnMaxS = 32;         // sites per tile: min(32, 64 / rhs)
+constexpr int kNnItems = 4;         // operand items per thread and step (S x C_in x rhs <= 2048)
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
@@ -57,10 +58,10 @@ __global__ void __launch_bounds__(kNnThreads, 1) k_covconv_tc(const float* __res
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* sA = smem;                         // [9] A_k
   unsigned char* sB = smem + 9 * ABYTES;            // [2] B buffers
-  // the step's transport of every site of the tile: s_k T_k(x) (sign folded
-  // in) as 18 floats (padded to 20) and the neighbour n_k(x)
-  float* sT = reinterpret_cast<float*>(sB + 2 * BBYTES);   // [kNnMaxS][20]
-  int* sNb = reinterpret_cast<int*>(sT + kNnMaxS * 20);     // [kNnMaxS]
+  // the transports of the tile's sites for all nine steps: s_k T_k(x) (sign
+  // folded in) as 18 floats (padded to 20) and the neighbour n_k(x)
+  float* sT = reinterpret_cast<float*>(sB + 2 * BBYTES);   // [9][kNnMaxS][20]
+  int* sNb = reinterpret_cast<int*>(sT + 9 * kNnMaxS * 20); // [9][kNnMaxS]
   __shared__ uint64_t bar[2];
   __shared__ uint32_t s_tmem;
   __shared__ int s_bad;
@@ -68,7 +69,7 @@ __global__ void __launch_bounds__(kNnThreads, 1) k_covconv_tc(const float* __res
 
   // zero everything once: padding rows of A, padding K entries and padding
   // columns of B stay zero for the whole launch
-  for (int i = tid; i < (9 * ABYTES + 2 * BBYTES + kNnMaxS * 21 * 4) / 16; i += kNnThreads)
+  for (int i = tid; i < (9 * ABYTES + 2 * BBYTES + 9 * kNnMaxS * 21 * 4) / 16; i += kNnThreads)
     reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
   __syncthreads();
   for (int e = tid; e < 9 * cout * cin; e += kNnThreads) {
@@ -97,76 +98,80 @@ __global__ void __launch_bounds__(kNnThreads, 1) k_covconv_tc(const float* __res
   const int items = S * cin * N;                    // (site, input channel, rhs) of one step
   uint32_t st = 0;                                  // steps issued by this CTA
 
+  // the operand items of thread tid at one step: i = tid + j * threads
+  auto load_items = [&](int k, int ns, float (&hb)[kNnItems][6]) {
+#pragma unroll
+    for (int j = 0; j < kNnItems; ++j) {
+      const int i = tid + j * kNnThreads;
+      const int r = i % N, c = (i / N) % cin, s = i / (N * cin);
+      const bool on = i < items && s < ns;
+      const size_t n = on ? (size_t)sNb[k * kNnMaxS + s] : 0;
+#pragma unroll
+      for (int bb = 0; bb < 3; ++bb) {
+        const size_t row = (n * cin + c) * 3 + bb;
+        hb[j][2 * bb] = on ? __ldg(h + fidx(row, 0, N, r)) : 0.f;
+        hb[j][2 * bb + 1] = on ? __ldg(h + fidx(row, 1, N, r)) : 0.f;
+      }
+    }
+  };
+
   for (int tile = blockIdx.x; tile < ntiles && !s_bad; tile += gridDim.x) {
     const int s0 = tile * S;
     const int ns = min(S, V - s0);
+    // the transports of all nine steps, one (step, site) per thread
+    for (int u = tid; u < 9 * S; u += kNnThreads) {
+      const int k = u / S, s = u % S;
+      float* T = sT + (k * kNnMaxS + s) * 20;
+      int n = 0;
+      if (s < ns) {
+        const size_t x = (size_t)s0 + s;
+        if (k == 0) {
+          n = (int)x;
+#pragma unroll
+          for (int q = 0; q < 18; ++q) T[q] = (q == 0 || q == 8 || q == 16) ? 1.f : 0.f;
+        } else {
+          const int mu = (k - 1) & 3;
+          const int e = __ldg(nbr + x * 8 + (k <= 4 ? 0 : 4) + mu);
+          n = e & 0x3fffffff;
+          const float sg = (e & 0x40000000) ? -1.f : 1.f;
+          const float* uu = U32 + ((k <= 4 ? x : (size_t)n) * 4 + mu) * 18;
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int bb = 0; bb < 3; ++bb) {
+              // T = U forward, U^dag backward: T[a][bb] at 2 (3a + bb)
+              const int q = k <= 4 ? a * 3 + bb : bb * 3 + a;
+              T[2 * (a * 3 + bb)] = sg * __ldg(uu + 2 * q);
+              T[2 * (a * 3 + bb) + 1] = sg * (k <= 4 ? __ldg(uu + 2 * q + 1) : -__ldg(uu + 2 * q + 1));
+            }
+        }
+      }
+      sNb[k * kNnMaxS + s] = n;
+    }
+    __syncthreads();
+    // the inputs of step k+1 are loaded while step k is computed
+    float hc[kNnItems][6], hn[kNnItems][6];
+    load_items(0, ns, hc);
     for (int k = 0; k < 9; ++k, ++st) {
       const int b = st & 1;
       unsigned char* Bb = sB + b * BBYTES;
+      if (k < 8) load_items(k + 1, ns, hn);
       // the MMAs of step st-2 read this buffer
       if (st >= 2 && !tc::mbar_wait(&bar[b], ((st - 2) >> 1) & 1, kNnWait)) s_bad = 1;
-      // the transports of the step (one thread per site of the tile)
-      if (tid < S) {
-        const int s = tid;
-        float* T = sT + s * 20;
-        int n = 0;
-        if (s < ns) {
-          const size_t x = (size_t)s0 + s;
-          if (k == 0) {
-            n = (int)x;
 #pragma unroll
-            for (int q = 0; q < 18; ++q) T[q] = (q == 0 || q == 8 || q == 16) ? 1.f : 0.f;
-          } else {
-            const int mu = (k - 1) & 3;
-            const int e = __ldg(nbr + x * 8 + (k <= 4 ? 0 : 4) + mu);
-            n = e & 0x3fffffff;
-            const float sg = (e & 0x40000000) ? -1.f : 1.f;
-            const float* u = U32 + ((k <= 4 ? x : (size_t)n) * 4 + mu) * 18;
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-#pragma unroll
-              for (int bb = 0; bb < 3; ++bb) {
-                // T = U forward, U^dag backward: T[a][bb] at 2 (3a + bb)
-                const int q = k <= 4 ? a * 3 + bb : bb * 3 + a;
-                T[2 * (a * 3 + bb)] = sg * __ldg(u + 2 * q);
-                T[2 * (a * 3 + bb) + 1] = sg * (k <= 4 ? __ldg(u + 2 * q + 1) : -__ldg(u + 2 * q + 1));
-              }
-          }
-        }
-        sNb[s] = n;
-      }
-      __syncthreads();
-      // items (site s, input channel c, rhs r), kNnUnroll per thread with
-      // their loads issued together
-      for (int i0 = tid; i0 < items; i0 += kNnUnroll * kNnThreads) {
-        float hr[kNnUnroll][3], hi[kNnUnroll][3];
-#pragma unroll
-        for (int j = 0; j < kNnUnroll; ++j) {
-          const int i = i0 + j * kNnThreads;
+      for (int j = 0; j < kNnItems; ++j) {
+        const int i = tid + j * kNnThreads;
+        if (i < items) {
           const int r = i % N, c = (i / N) % cin, s = i / (N * cin);
-          const bool on = i < items && s < ns;
-          const size_t n = on ? (size_t)sNb[s] : 0;
-#pragma unroll
-          for (int bb = 0; bb < 3; ++bb) {
-            const size_t row = (n * cin + c) * 3 + bb;
-            hr[j][bb] = on ? __ldg(h + fidx(row, 0, N, r)) : 0.f;
-            hi[j][bb] = on ? __ldg(h + fidx(row, 1, N, r)) : 0.f;
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < kNnUnroll; ++j) {
-          const int i = i0 + j * kNnThreads;
-          if (i >= items) break;
-          const int r = i % N, c = (i / N) % cin, s = i / (N * cin);
-          const float* T = sT + s * 20;
+          const float* T = sT + (k * kNnMaxS + s) * 20;
 #pragma unroll
           for (int a = 0; a < 3; ++a) {
             float sr = 0.f, si = 0.f;
 #pragma unroll
             for (int bb = 0; bb < 3; ++bb) {
               const float ur = T[2 * (a * 3 + bb)], ui = T[2 * (a * 3 + bb) + 1];
-              sr = fmaf(ur, hr[j][bb], fmaf(-ui, hi[j][bb], sr));
-              si = fmaf(ur, hi[j][bb], fmaf(ui, hr[j][bb], si));
+              sr = fmaf(ur, hc[j][2 * bb], fmaf(-ui, hc[j][2 * bb + 1], sr));
+              si = fmaf(ur, hc[j][2 * bb + 1], fmaf(ui, hc[j][2 * bb], si));
             }
             put_bf16(Bb, (s * 3 + a) * N + r, 2 * c, sr, si, KG);
           }
@@ -185,6 +190,10 @@ __global__ void __launch_bounds__(kNnThreads, 1) k_covconv_tc(const float* __res
                       idesc, (k > 0 || ks > 0) ? 1u : 0u);
         tc::mma_commit(&bar[b]);
       }
+#pragma unroll
+      for (int j = 0; j < kNnItems; ++j)
+#pragma unroll
+        for (int q = 0; q < 6; ++q) hc[j][q] = hn[j][q];
     }
     if (s_bad) break;
     // the tile's last step done: every MMA of the tile is
@@ -229,11 +238,11 @@ __global__ void __launch_bounds__(kNnThreads, 1) k_covconv_tc(const float* __res
 
 template <int KC>
 void launch_tc(mrhs_ctx c, const float* h, float* z, const float* W, int cin, int cout, int N) {
-  const int S = std::max(1, 64 / N);
+  const int S = std::min(kNnMaxS, std::max(1, 64 / N));
   const int V = c->g.V;
   const int ntiles = (V + S - 1) / S;
-  const size_t smem = 9 * (size_t)kNnRows * KC * 2 + 2 * (size_t)kNnCols * KC * 2 + kNnMaxS * 20 * sizeof(float) +
-                      kNnMaxS * sizeof(int);
+  const size_t smem = 9 * (size_t)kNnRows * KC * 2 + 2 * (size_t)kNnCols * KC * 2 +
+                      9 * kNnMaxS * 20 * sizeof(float) + 9 * kNnMaxS * sizeof(int);
   const int grid = std::min(ntiles, c->num_sms);
   MRHS_CUDA(cudaFuncSetAttribute(k_covconv_tc<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_covconv_tc<KC><<<grid, kNnThreads, smem, c->stream>>>(h, z, W, c->U32, c->nbr, cin, cout, N, S, V, ntiles,
