@@ -98,22 +98,39 @@ __global__ void __launch_bounds__(kNnThreads, 1) k_covconv_tc(const float* __res
   const int items = S * cin * N;                    // (site, input channel, rhs) of one step
   uint32_t st = 0;                                  // steps issued by this CTA
 
-  // the operand items of thread tid at one step: i = tid + j * threads
+  // the operand items of thread tid, the same at every step and tile:
+  // item i = tid + j * threads is (site s, input channel c, rhs r); its
+  // input rows sit at n * 6 C_in N + it_h (+ (2 bb + part) N) for the
+  // neighbour n, its three colours go to B rows (s*3 + a) N + r, K = 2c
+  int it_s[kNnItems], it_h[kNnItems];
+  uint32_t it_b[kNnItems][3];
+#pragma unroll
+  for (int j = 0; j < kNnItems; ++j) {
+    const int i = tid + j * kNnThreads;
+    const int r = i % N, c = (i / N) % cin;
+    it_s[j] = i < items ? i / (N * cin) : kNnMaxS;  // kNnMaxS: no item
+    it_h[j] = c * 6 * N + r;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) it_b[j][a] = tc::kmajor_offset(((i / (N * cin)) * 3 + a) * N + r, 2 * c, 2, KG);
+  }
+  const size_t nstride = (size_t)6 * cin * N;       // floats per site of h
   auto load_items = [&](int k, int ns, float (&hb)[kNnItems][6]) {
 #pragma unroll
     for (int j = 0; j < kNnItems; ++j) {
-      const int i = tid + j * kNnThreads;
-      const int r = i % N, c = (i / N) % cin, s = i / (N * cin);
-      const bool on = i < items && s < ns;
-      const size_t n = on ? (size_t)sNb[k * kNnMaxS + s] : 0;
+      const bool on = it_s[j] < ns;
+      const float* hp = h + (on ? (size_t)sNb[k * kNnMaxS + it_s[j]] * nstride + it_h[j] : 0);
 #pragma unroll
-      for (int bb = 0; bb < 3; ++bb) {
-        const size_t row = (n * cin + c) * 3 + bb;
-        hb[j][2 * bb] = on ? __ldg(h + fidx(row, 0, N, r)) : 0.f;
-        hb[j][2 * bb + 1] = on ? __ldg(h + fidx(row, 1, N, r)) : 0.f;
-      }
+      for (int q = 0; q < 6; ++q) hb[j][q] = on ? __ldg(hp + q * N) : 0.f;
     }
   };
+  // epilogue: column n of the accumulator is (site, colour, rhs); its offset
+  // in z from the tile's first site, without the row's channel and part
+  int* s_col = sNb + 9 * kNnMaxS;                   // [kNnCols]
+  for (int n = tid; n < kNnCols; n += kNnThreads) {
+    const int r = n % N, a = (n / N) % 3, ss = n / (3 * N);
+    s_col[n] = (ss * cout * 3 + a) * 2 * N + r;
+  }
+  __syncthreads();
 
   for (int tile = blockIdx.x; tile < ntiles && !s_bad; tile += gridDim.x) {
     const int s0 = tile * S;
@@ -160,10 +177,9 @@ __global__ void __launch_bounds__(kNnThreads, 1) k_covconv_tc(const float* __res
       if (st >= 2 && !tc::mbar_wait(&bar[b], ((st - 2) >> 1) & 1, kNnWait)) s_bad = 1;
 #pragma unroll
       for (int j = 0; j < kNnItems; ++j) {
-        const int i = tid + j * kNnThreads;
-        if (i < items) {
-          const int r = i % N, c = (i / N) % cin, s = i / (N * cin);
-          const float* T = sT + (k * kNnMaxS + s) * 20;
+        if (it_s[j] < kNnMaxS) {
+          // rows of absent sites get zeros (their inputs were loaded as 0)
+          const float* T = sT + (k * kNnMaxS + it_s[j]) * 20;
 #pragma unroll
           for (int a = 0; a < 3; ++a) {
             float sr = 0.f, si = 0.f;
@@ -173,7 +189,7 @@ __global__ void __launch_bounds__(kNnThreads, 1) k_covconv_tc(const float* __res
               sr = fmaf(ur, hc[j][2 * bb], fmaf(-ui, hc[j][2 * bb + 1], sr));
               si = fmaf(ur, hc[j][2 * bb + 1], fmaf(ui, hc[j][2 * bb], si));
             }
-            put_bf16(Bb, (s * 3 + a) * N + r, 2 * c, sr, si, KG);
+            *reinterpret_cast<uint32_t*>(Bb + it_b[j][a]) = pack_bf16(sr, si);
           }
         }
       }
@@ -206,6 +222,7 @@ __global__ void __launch_bounds__(kNnThreads, 1) k_covconv_tc(const float* __res
       const bool live = row < 2 * cout;
       const int part = live ? row / cout : 0, o = live ? row % cout : 0;
       const int ncols = 3 * ns * N;
+      float* zt = z + (size_t)s0 * cout * 6 * N + (size_t)o * 6 * N + (size_t)part * N;
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         float v[16];
@@ -214,10 +231,7 @@ __global__ void __launch_bounds__(kNnThreads, 1) k_covconv_tc(const float* __res
 #pragma unroll
           for (int q = 0; q < 16; ++q) {
             const int n = col0 + 16 * j + q;
-            if (n < ncols) {
-              const int r = n % N, a = (n / N) % 3, s = n / (3 * N);
-              z[fidx(((size_t)(s0 + s) * cout + o) * 3 + a, part, N, r)] = v[q];
-            }
+            if (n < ncols) zt[s_col[n]] = v[q];
           }
         }
       }
@@ -242,7 +256,7 @@ void launch_tc(mrhs_ctx c, const float* h, float* z, const float* W, int cin, in
   const int V = c->g.V;
   const int ntiles = (V + S - 1) / S;
   const size_t smem = 9 * (size_t)kNnRows * KC * 2 + 2 * (size_t)kNnCols * KC * 2 +
-                      9 * kNnMaxS * 20 * sizeof(float) + 9 * kNnMaxS * sizeof(int);
+                      9 * kNnMaxS * 20 * sizeof(float) + 9 * kNnMaxS * sizeof(int) + kNnCols * sizeof(int);
   const int grid = std::min(ntiles, c->num_sms);
   MRHS_CUDA(cudaFuncSetAttribute(k_covconv_tc<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_covconv_tc<KC><<<grid, kNnThreads, smem, c->stream>>>(h, z, W, c->U32, c->nbr, cin, cout, N, S, V, ntiles,
