@@ -357,12 +357,13 @@ int mrhs_nn_zero_grads(mrhs_ctx ctx);
 /* out = net(in); keeps the activations for mrhs_nn_backward */
 int mrhs_nn_forward(mrhs_ctx ctx, const void* in, void* out, int nrhs);
 /* out = net(in) for inference (no activations kept; the right-hand sides in
- * chunks of at most 8). With bf16 weights every layer's channel mixing runs
- * on the tensor cores (tcgen05, kind::f16): every transported input
+ * chunks of at most 8). With bf16 weights the channel mixing of every layer
+ * with 16 or more channels on one side runs on the tensor cores (tcgen05,
+ * kind::f16): every transported input
  * triplet s_k T_k h(n_k) (the transport in FP32) is rounded once to bf16
  * (round to nearest even) when it enters the product, the weights are the
- * bf16 compute copy, products and sums are FP32; with FP32 weights
- * the CUDA-core layer of mrhs_nn_forward. This is the network
+ * bf16 compute copy, products and sums are FP32; narrower layers and FP32
+ * weights take the CUDA-core layer of mrhs_nn_forward. This is the network
  * mrhs_setup_init_learned applies. MRHS_ERR_TIMEOUT if a bounded wait of
  * the tensor-core pipeline ran out. */
 int mrhs_nn_infer(mrhs_ctx ctx, const void* in, void* out, int nrhs);

@@ -15,7 +15,8 @@ tests/test_oracle_nn.py).
   decisions; measured with the oracle alone, a relative change of 1e-6 in the
   input moves the output by 5.4e-4, while rounding the operands at all moves
   it by 2.9e-3. Bound: 1.5e-3.
-- FP32 weights take the CUDA-core layer: against the unrounded oracle at 1e-4.
+- Layers with fewer than 16 channels on both sides, and FP32 weights, take
+  the CUDA-core layer: against the unrounded oracle at 1e-4.
 """
 import numpy as np
 import pytest
@@ -72,14 +73,14 @@ def infer(lat, x, nrhs):
     return lat.to_host(y, nrhs, MRHS_F32), ran
 
 
-@pytest.mark.parametrize("widths,nrhs,rounds", [((4, 32, 32, 4), 13, True), ((4, 11, 7, 4), 6, False)],
+@pytest.mark.parametrize("widths,nrhs,rounds", [((4, 32, 32, 4), 13, True), ((4, 16, 21, 4), 6, True)],
                          ids=["32-wide", "ragged"])
 def test_infer_tensor_cores_exact(widths, nrhs, rounds):
     """13 right-hand sides run as chunks of 8 and 5 (tiles of 8 and 12
     sites; 512 = 42 x 12 + 8 leaves a ragged last tile); 6 as one chunk of
-    tiles of 10 sites. The 32-wide case's hidden values need more than 8
-    significant bits, so the bf16 rounding of the hidden fields shows in its
-    output; the narrow case's values all fit in bf16."""
+    tiles of 10 sites, with 16 and 21 hidden channels (operand K of 32 and 48
+    per step). The hidden values need more than 8 significant bits, so the
+    bf16 rounding of the operands shows in the output."""
     rng = np.random.default_rng(5301)
     nw, nb = oracle.nn_sizes(widths)
     mask = rng.random(nw) < 0.25
@@ -99,8 +100,8 @@ def test_infer_tensor_cores_exact(widths, nrhs, rounds):
     lat.close()
 
 
-@pytest.mark.parametrize("widths,nrhs,scale", [((4, 32, 32, 4), 13, 0.15), ((4, 11, 11, 4), 3, 0.25),
-                                               ((4, 3, 5, 4), 1, 0.4)], ids=["32-wide", "11-wide", "narrow"])
+@pytest.mark.parametrize("widths,nrhs,scale", [((4, 32, 32, 4), 13, 0.15), ((4, 24, 16, 4), 1, 0.25)],
+                         ids=["32-wide", "24-16"])
 def test_infer_tensor_cores_generic(widths, nrhs, scale):
     rng = np.random.default_rng(5201)
     nw, nb = oracle.nn_sizes(widths)
@@ -115,13 +116,15 @@ def test_infer_tensor_cores_generic(widths, nrhs, scale):
     lat.close()
 
 
-def test_infer_fp32_weights_take_the_cuda_cores():
-    widths, nrhs = (4, 8, 6, 4), 3
+@pytest.mark.parametrize("widths,bf16", [((4, 8, 6, 4), 0), ((4, 32, 32, 4), 0), ((4, 11, 11, 4), 1)],
+                         ids=["fp32-weights", "fp32-weights-32", "bf16-11-wide"])
+def test_infer_cuda_core_layers(widths, bf16):
+    nrhs = 3
     rng = np.random.default_rng(5401)
     nw, nb = oracle.nn_sizes(widths)
-    flat = np.concatenate([0.4 * rng.standard_normal(2 * nw), 0.3 * rng.standard_normal(nb)])
+    flat = np.concatenate([0.25 * rng.standard_normal(2 * nw), 0.3 * rng.standard_normal(nb)])
     U = inputs.gauge_field(DIMS, 0.4, 5402)
-    lat, W, b = make(U, widths, flat, bf16=0)
+    lat, W, b = make(U, widths, flat, bf16=bf16)
     x = inputs.gaussian_field((nrhs, lat.V, 12), 5403)
     y, ran = infer(lat, x, nrhs)
     assert "nn_covconv" in ran and "nn_covconv_tc" not in ran, ran
