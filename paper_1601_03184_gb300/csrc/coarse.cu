@@ -291,6 +291,50 @@ __global__ void __launch_bounds__(256) k_restrict_tiled(const SP* __restrict__ P
   }
 }
 
+// FP32 restriction streamed through registers: one thread per (aggregate A,
+// chirality h, four rows i0..i0+3, four right-hand sides r0..r0+3), the sum
+// over the aggregate's sites and the chirality's six components in the
+// thread's registers (no staging, no barrier): every 16-byte load of P or v
+// feeds 16 complex products. Nt % 4 = 0, N % 4 = 0.
+__global__ void __launch_bounds__(128) k_restrict_stream(const float* __restrict__ P, const float* __restrict__ v,
+                                                         float* __restrict__ vc, int Nt, int N, int Va) {
+  const int A = blockIdx.x;
+  const int nq = N / 4, ni = Nt / 4;
+  const int t = threadIdx.x;
+  if (t >= 2 * ni * nq) return;
+  const int r0 = 4 * (t % nq), i0 = 4 * ((t / nq) % ni), h = t / (nq * ni);
+  float are[4][4], aim[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) are[a][b] = aim[a][b] = 0.f;
+  const size_t row0 = (size_t)A * Va * 12 + 6 * h;
+#pragma unroll 2
+  for (int q = 0; q < Va * 6; ++q) {
+    const size_t row = row0 + (size_t)(q / 6) * 12 + q % 6;
+    const float4 pr = __ldg(reinterpret_cast<const float4*>(P + row * 2 * Nt + i0));
+    const float4 pi = __ldg(reinterpret_cast<const float4*>(P + (row * 2 + 1) * Nt + i0));
+    const float4 xr = __ldg(reinterpret_cast<const float4*>(v + row * 2 * N + r0));
+    const float4 xi = __ldg(reinterpret_cast<const float4*>(v + (row * 2 + 1) * N + r0));
+    const float Pr[4] = {pr.x, pr.y, pr.z, pr.w}, Pi[4] = {pi.x, pi.y, pi.z, pi.w};
+    const float Xr[4] = {xr.x, xr.y, xr.z, xr.w}, Xi[4] = {xi.x, xi.y, xi.z, xi.w};
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        // conj(p) x: re = pr xr + pi xi, im = pr xi - pi xr
+        are[a][b] = fmaf(Pi[a], Xi[b], fmaf(Pr[a], Xr[b], are[a][b]));
+        aim[a][b] = fmaf(-Pi[a], Xr[b], fmaf(Pr[a], Xi[b], aim[a][b]));
+      }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const size_t crow = (size_t)A * 2 * Nt + h * Nt + i0 + a;
+    *reinterpret_cast<float4*>(vc + fidx(crow, 0, N, r0)) = make_float4(are[a][0], are[a][1], are[a][2], are[a][3]);
+    *reinterpret_cast<float4*>(vc + fidx(crow, 1, N, r0)) = make_float4(aim[a][0], aim[a][1], aim[a][2], aim[a][3]);
+  }
+}
+
 // u(x,c,r) = sum_j P_j(x,c) uc[A(x)][(h(c), j)][r]
 template <class SP, class SC, class SU>
 __global__ void k_prolong(const SP* __restrict__ P, const SC* __restrict__ uc, SU* __restrict__ u, int Nt, int N,
@@ -671,6 +715,17 @@ void restrict_typed(mrhs_ctx c, const void* v, int dv, void* vc, int dc, int N) 
   MRHS_REQUIRE(threads <= 1024, MRHS_ERR_SHAPE, "restriction: ntv*nrhs too large");
   MRHS_REQUIRE(dc == MRHS_F64 || dc == MRHS_F32, MRHS_ERR_ARG, "coarse fields are F64 or F32");
   Prof pr(c, "restrict");
+  static const bool stream_off = [] {
+    const char* e = std::getenv("MRHS_RESTRICT");
+    return e && std::string(e) == "tiled";
+  }();
+  if (!stream_off && c->tv_dtype == MRHS_F32 && dv == MRHS_F32 && dc == MRHS_F32 && Nt % 4 == 0 && N % 4 == 0 &&
+      2 * (Nt / 4) * (N / 4) <= 128) {
+    k_restrict_stream<<<c->g.nagg, 128, 0, c->stream>>>((const float*)c->P, (const float*)v, (float*)vc, Nt, N,
+                                                        c->g.Va);
+    MRHS_LAUNCH_CHECK("restrict_stream");
+    return;
+  }
   const bool tiled = Nt % 4 == 0 && N % 2 == 0 && (nc / 4) * (N / 2) <= 256;
   MRHS_DISPATCH(c->tv_dtype, SP, MRHS_DISPATCH(dv, SV, {
     if (tiled) {

@@ -115,8 +115,11 @@ def _child(env, kind, nrhs):
     ({"MRHS_SAP_PK": "1g", "MRHS_SAP_CPB": "2"}, "sap", 8, "sap_pk", 1e-5),
     ({"MRHS_SAP_PK": "2s"}, "sap", 8, "sap_pk", 1e-5),
     ({"MRHS_SAP_PK": "2s", "MRHS_SAP_CPB": "1"}, "sap", 8, "sap_pk", 1e-5),
+    ({}, "restrict", 8, "restrict", 1e-5),
+    ({}, "restrict", 6, "restrict", 1e-5),
+    ({"MRHS_RESTRICT": "tiled"}, "restrict", 8, "restrict", 1e-5),
 ], ids=["smem-fused8", "smem-fused2", "chunk2", "tm", "tm-cpb1", "passes2", "dc-alu", "pk1g", "pk1g-6", "pk1g-cpb2",
-        "pk2s", "pk2s-cpb1"])
+        "pk2s", "pk2s-cpb1", "restrict-stream", "restrict-tiled-6", "restrict-tiled"])
 def test_switch_selected_forms(env, kind, nrhs, kernel, tol):
     r = _child(env, kind, nrhs)
     assert kernel in r["kernels"], r

@@ -4,7 +4,7 @@ switches once per process). Prints one JSON line {"rel": ..., "kernels": [...]}
 with the relative 2-norm error against the FP64 oracle and the kernel classes
 the library timed, so that the caller can also see which form ran.
 
-Usage: python tests/variant_check.py sap|apply_D|apply_Dc NRHS
+Usage: python tests/variant_check.py sap|apply_D|apply_Dc|restrict NRHS
 """
 import json
 import os
@@ -58,6 +58,15 @@ def main(kind, nrhs):
         yd = lat.field(nrhs, MRHS_F32, coarse=True)
         lat.apply_Dc(lat.to_device(xc, MRHS_F32, coarse=True), yd, nrhs, MRHS_F32)
         err = rel(lat.to_host(yd, nrhs, MRHS_F32, coarse=True), oracle.apply_Dc(cfg["dims"], cfg["agg"], Dc, xc))
+    elif kind == "restrict":
+        tv = inputs.test_vectors(ntv, cfg["dims"], 761)
+        lat.set_tv(lat.to_device(tv, MRHS_F32), MRHS_F32)
+        lat.build_P()
+        P = oracle.gram_schmidt(cfg["dims"], cfg["agg"], tv)
+        v = inputs.gaussian_field((nrhs, lat.V, 12), 762)
+        vc = lat.field(nrhs, MRHS_F32, coarse=True)
+        lat.restrict(lat.to_device(v, MRHS_F32), vc, nrhs, MRHS_F32)
+        err = rel(lat.to_host(vc, nrhs, MRHS_F32, coarse=True), oracle.restrict(cfg["dims"], cfg["agg"], P, v))
     else:
         raise SystemExit("unknown check " + kind)
     kernels = sorted(pkg.mrhs_profile_read(lat.ctx))
