@@ -324,9 +324,94 @@ void multi_axpy(mrhs_ctx c, const void* X, size_t stride, int K, void* Y, size_t
 }
 
 // normalise every right-hand side of X to unit 2-norm
+namespace {
+// |X[., r]|^2 of a fine FP32 field (N / 4 divides 256, 16-byte aligned rows):
+// thread (quad of right-hand sides, lane) over a grid-stride range of rows,
+// FP32 sums over 64 rows at a time added into FP64; the lanes of a quad summed
+// in a fixed order, then the CTAs (k_norm2_sum)
+constexpr int kNormCtas = 608;
+__global__ void __launch_bounds__(kBlock) k_norm2_4(const float* __restrict__ X, size_t rows, int N,
+                                                    double* __restrict__ part) {
+  __shared__ double sh[kBlock * 4];
+  const int nq = N / 4, lanes = kBlock / nq;
+  const int q = threadIdx.x % nq, lane = threadIdx.x / nq;
+  double acc[4] = {0, 0, 0, 0};
+  float f[4] = {0.f, 0.f, 0.f, 0.f};
+  int cnt = 0;
+  for (size_t row = (size_t)blockIdx.x * lanes + lane; row < rows; row += (size_t)gridDim.x * lanes) {
+    const float4 re = __ldg(reinterpret_cast<const float4*>(X + row * 2 * N + 4 * q));
+    const float4 im = __ldg(reinterpret_cast<const float4*>(X + row * 2 * N + N + 4 * q));
+    f[0] = fmaf(re.x, re.x, fmaf(im.x, im.x, f[0]));
+    f[1] = fmaf(re.y, re.y, fmaf(im.y, im.y, f[1]));
+    f[2] = fmaf(re.z, re.z, fmaf(im.z, im.z, f[2]));
+    f[3] = fmaf(re.w, re.w, fmaf(im.w, im.w, f[3]));
+    if (++cnt == 64) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[e] += f[e], f[e] = 0.f;
+      cnt = 0;
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < 4; ++e) sh[lane * N + 4 * q + e] = acc[e] + f[e];
+  __syncthreads();
+  if (threadIdx.x < N) {
+    double t = 0;
+    for (int l = 0; l < lanes; ++l) t += sh[l * N + threadIdx.x];
+    part[(size_t)blockIdx.x * N + threadIdx.x] = t;
+  }
+}
+__global__ void k_norm2_sum(const double* part, int nblk, int N, double* out) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  double t = 0;
+  for (int b = 0; b < nblk; ++b) t += part[(size_t)b * N + r];
+  out[2 * r] = t;
+  out[2 * r + 1] = 0;
+}
+
+// tv = (X[., r] * s[r]) * scale in the storage type of tv: the normalised
+// vectors converted in one pass (the same two roundings as scaling X in
+// place and converting it)
+template <class SI, class SO>
+__global__ void k_scale_convert(const SI* __restrict__ X, SO* __restrict__ T, size_t rows, int N,
+                                const double* __restrict__ s, float scale) {
+  using R = typename Real<SI>::type;
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= rows * 2 * N) return;
+  const int r = (int)(t % N);
+  const R v = (R)(to_r(X[t]) * (R)s[r]);
+  T[t] = from_r<SO>(v * (R)scale);
+}
+
+void norms_of_field(mrhs_ctx c, const void* X, size_t rows, int N, int dtype, double* nrm) {
+  if (dtype == MRHS_F32 && N % 4 == 0 && kBlock % (N / 4) == 0 && aligned16(X)) {
+    double* part = (double*)scratch(c, SC_RED, sizeof(double) * kNormCtas * (size_t)N);
+    Prof pr(c, "norms");
+    k_norm2_4<<<kNormCtas, kBlock, 0, c->stream>>>((const float*)X, rows, N, part);
+    MRHS_LAUNCH_CHECK("norm2_4");
+    k_norm2_sum<<<grid_for(N, 64), 64, 0, c->stream>>>(part, kNormCtas, N, nrm);
+    MRHS_LAUNCH_CHECK("norm2_sum");
+    return;
+  }
+  norms(c, X, rows, N, dtype, nrm);
+}
+}  // namespace
+
+// T = X / |X[., r]| * scale in T's storage type (X unchanged)
+void normalise_into(mrhs_ctx c, const void* X, int dx, void* T, int dt, size_t rows, int N, float scale) {
+  double* nrm = (double*)scratch(c, SC_MISC, sizeof(double) * 3 * N);
+  norms_of_field(c, X, rows, N, dx, nrm);
+  k_inv_sqrt<<<grid_for(N, 64), 64, 0, c->stream>>>(nrm, nrm + 2 * N, N);
+  MRHS_LAUNCH_CHECK("inv_sqrt");
+  const size_t work = rows * 2 * N;
+  Prof pr(c, "normalise");
+  MRHS_DISPATCH(dx, SI, MRHS_DISPATCH(dt, SO, (k_scale_convert<SI, SO><<<grid_for(work, kBlock), kBlock, 0, c->stream>>>((const SI*)X, (SO*)T, rows, N, nrm + 2 * N, scale))));
+  MRHS_LAUNCH_CHECK("scale_convert");
+}
+
 void normalise_rhs(mrhs_ctx c, void* X, size_t rows, int N, int dtype) {
   double* nrm = (double*)scratch(c, SC_MISC, sizeof(double) * 3 * N);
-  norms(c, X, rows, N, dtype, nrm);
+  norms_of_field(c, X, rows, N, dtype, nrm);
   k_inv_sqrt<<<grid_for(N, 64), 64, 0, c->stream>>>(nrm, nrm + 2 * N, N);
   MRHS_LAUNCH_CHECK("inv_sqrt");
   size_t work = rows * N;

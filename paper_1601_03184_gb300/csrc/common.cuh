@@ -325,6 +325,8 @@ void multi_dot(mrhs_ctx c, const void* X, size_t stride, int K, const void* Y, s
 void norms(mrhs_ctx c, const void* X, size_t rows, int N, int dtype, double* out /* device [N] (squared) */);
 void convert(mrhs_ctx c, const void* x, int dx, void* y, int dy, size_t n);
 void convert_scaled(mrhs_ctx c, const void* x, int dx, void* y, int dy, size_t n, float scale);
+// blas.cu: T = X[., r] / |X[., r]| * scale in T's storage type, one pass after the norms
+void normalise_into(mrhs_ctx c, const void* X, int dx, void* T, int dt, size_t rows, int N, float scale);
 // columns k0 .. k0+nb-1 of a fine field of ntv right-hand sides to a field of
 // nb (same storage type), and back with conversion and a scale factor
 void gather_cols(mrhs_ctx c, const void* src, int ntv, void* dst, int nb, int k0, int dtype);

@@ -42,10 +42,13 @@ void init_block(mrhs_ctx c, int k0, int nb, int init_mode, int n_sweeps, int n_m
       if (it + 1 < n_sweeps) convert(c, x, wd, v, c->tv_dtype, n);
     }
   }
-  normalise_rhs(c, x, (size_t)c->g.V * 12, nb, wd);
   const float scale = (float)(c->tv_dtype == MRHS_F16 ? std::sqrt(12.0 * c->g.V) : 1.0);
-  if (nb < N) scatter_cols(c, x, wd, nb, c->tv, c->tv_dtype, N, k0, scale);
-  else convert_scaled(c, x, wd, c->tv, c->tv_dtype, n, scale);
+  if (nb < N) {
+    normalise_rhs(c, x, (size_t)c->g.V * 12, nb, wd);
+    scatter_cols(c, x, wd, nb, c->tv, c->tv_dtype, N, k0, scale);
+  } else {
+    normalise_into(c, x, wd, c->tv, c->tv_dtype, (size_t)c->g.V * 12, N, scale);
+  }
 }
 
 void setup_init(mrhs_ctx c, const void* tv0, int dtype, int init_mode, int n_sweeps, int n_mr) {
@@ -87,9 +90,8 @@ void setup_init_learned(mrhs_ctx c, const void* tv0, int dtype, int n_sweeps, in
     MRHS_CUDA(cudaMemcpyAsync(x, y, n * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
   }
   nn_infer(c, (const float*)x, (float*)y, N);
-  normalise_rhs(c, y, (size_t)c->g.V * 12, N, MRHS_F32);
   c->tv_scale = c->tv_dtype == MRHS_F16 ? std::sqrt(12.0 * c->g.V) : 1.0;
-  convert_scaled(c, y, MRHS_F32, c->tv, c->tv_dtype, n, (float)c->tv_scale);
+  normalise_into(c, y, MRHS_F32, c->tv, c->tv_dtype, (size_t)c->g.V * 12, N, (float)c->tv_scale);
   c->have_tv = true;
   build_P(c);
   build_Dc(c);
@@ -128,9 +130,12 @@ void setup_refine(mrhs_ctx c, int n_iter, int n_sweeps, int n_mr, double ctol, i
       // smoother with the coarse-grid result as starting guess
       sap_mixed(c, vb, c->tv_dtype, x, m, wd, n_sweeps, n_mr);
       // replace the block's test vectors by the result
-      normalise_rhs(c, x, (size_t)c->g.V * 12, m, wd);
-      if (m < N) scatter_cols(c, x, wd, m, c->tv, c->tv_dtype, N, k0, scale);
-      else convert_scaled(c, x, wd, c->tv, c->tv_dtype, n, scale);
+      if (m < N) {
+        normalise_rhs(c, x, (size_t)c->g.V * 12, m, wd);
+        scatter_cols(c, x, wd, m, c->tv, c->tv_dtype, N, k0, scale);
+      } else {
+        normalise_into(c, x, wd, c->tv, c->tv_dtype, (size_t)c->g.V * 12, N, scale);
+      }
     }
     c->tv_scale = scale;
     // rebuild R = P^dag and D_c from the new test vectors

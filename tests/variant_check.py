@@ -4,7 +4,7 @@ switches once per process). Prints one JSON line {"rel": ..., "kernels": [...]}
 with the relative 2-norm error against the FP64 oracle and the kernel classes
 the library timed, so that the caller can also see which form ran.
 
-Usage: python tests/variant_check.py sap|apply_D|apply_Dc|restrict NRHS
+Usage: python tests/variant_check.py sap|apply_D|apply_Dc|restrict|prolong NRHS
 """
 import json
 import os
@@ -67,6 +67,15 @@ def main(kind, nrhs):
         vc = lat.field(nrhs, MRHS_F32, coarse=True)
         lat.restrict(lat.to_device(v, MRHS_F32), vc, nrhs, MRHS_F32)
         err = rel(lat.to_host(vc, nrhs, MRHS_F32, coarse=True), oracle.restrict(cfg["dims"], cfg["agg"], P, v))
+    elif kind == "prolong":
+        tv = inputs.test_vectors(ntv, cfg["dims"], 771)
+        lat.set_tv(lat.to_device(tv, MRHS_F32), MRHS_F32)
+        lat.build_P()
+        P = oracle.gram_schmidt(cfg["dims"], cfg["agg"], tv)
+        uc = inputs.gaussian_field((nrhs, lat.nagg, 2 * ntv), 772)
+        u = lat.field(nrhs, MRHS_F32)
+        lat.prolong(lat.to_device(uc, MRHS_F32, coarse=True), u, nrhs, MRHS_F32)
+        err = rel(lat.to_host(u, nrhs, MRHS_F32), oracle.prolong(cfg["dims"], cfg["agg"], P, uc))
     else:
         raise SystemExit("unknown check " + kind)
     kernels = sorted(pkg.mrhs_profile_read(lat.ctx))
