@@ -300,6 +300,7 @@ def run_ours(args, cfg, cfg_name, m0, m0_src, rank, world, local_rank):
     lat.build_clover(m0, cfg["csw"])
     lat.set_smoother(args.smoother_eo)
     lat.set_coarse_solver(args.coarse_eo)
+    lat.set_dc_engine(args.dc_engine)
     # test vectors: complex Gaussian, drawn on the device directly in the library layout
     gen = torch.Generator(device="cuda")
     gen.manual_seed(cfg["tvseed"] + rank)
@@ -695,6 +696,8 @@ def main():
     ap.add_argument("--coarse-eo", type=int, default=1, choices=[0, 1],
                     help="1 (default): coarse GMRES on the Schur complement of the even aggregates (Sec. 4); "
                          "0: GMRES on D_c")
+    ap.add_argument("--dc-engine", type=int, default=0,
+                    help="D_c contraction engine of the FP32 setup (mrhs_set_dc_engine; 0 = auto)")
     ap.add_argument("--learned-width", type=int, default=0,
                     help="hidden width of the learned generator (0: the library default)")
     args = ap.parse_args()

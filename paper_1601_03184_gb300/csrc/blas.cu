@@ -383,6 +383,39 @@ __global__ void k_scale_convert(const SI* __restrict__ X, SO* __restrict__ T, si
   T[t] = from_r<SO>(v * (R)scale);
 }
 
+// the same four values at a time for FP32 X (N % 4 == 0, 16-byte aligned)
+template <class SO>
+__device__ __forceinline__ void store4(SO* p, float a, float b, float c, float d);
+template <>
+__device__ __forceinline__ void store4<float>(float* p, float a, float b, float c, float d) {
+  *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+}
+template <>
+__device__ __forceinline__ void store4<double>(double* p, float a, float b, float c, float d) {
+  p[0] = a, p[1] = b, p[2] = c, p[3] = d;
+}
+template <>
+__device__ __forceinline__ void store4<__nv_bfloat16>(__nv_bfloat16* p, float a, float b, float c, float d) {
+  __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
+  *reinterpret_cast<uint2*>(p) = make_uint2(*reinterpret_cast<uint32_t*>(&lo), *reinterpret_cast<uint32_t*>(&hi));
+}
+template <>
+__device__ __forceinline__ void store4<__half>(__half* p, float a, float b, float c, float d) {
+  __half2 lo = __floats2half2_rn(a, b), hi = __floats2half2_rn(c, d);
+  *reinterpret_cast<uint2*>(p) = make_uint2(*reinterpret_cast<uint32_t*>(&lo), *reinterpret_cast<uint32_t*>(&hi));
+}
+template <class SO>
+__global__ void k_scale_convert4(const float* __restrict__ X, SO* __restrict__ T, size_t n4, int N,
+                                 const double* __restrict__ s, float scale) {
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= n4) return;
+  const int r = (int)((4 * t) % N);
+  const float4 v = __ldg(reinterpret_cast<const float4*>(X) + t);
+  const float a = (v.x * (float)s[r]) * scale, b = (v.y * (float)s[r + 1]) * scale;
+  const float c = (v.z * (float)s[r + 2]) * scale, d = (v.w * (float)s[r + 3]) * scale;
+  store4<SO>(T + 4 * t, a, b, c, d);
+}
+
 void norms_of_field(mrhs_ctx c, const void* X, size_t rows, int N, int dtype, double* nrm) {
   if (dtype == MRHS_F32 && N % 4 == 0 && kBlock % (N / 4) == 0 && aligned16(X)) {
     double* part = (double*)scratch(c, SC_RED, sizeof(double) * kNormCtas * (size_t)N);
@@ -405,6 +438,12 @@ void normalise_into(mrhs_ctx c, const void* X, int dx, void* T, int dt, size_t r
   MRHS_LAUNCH_CHECK("inv_sqrt");
   const size_t work = rows * 2 * N;
   Prof pr(c, "normalise");
+  if (dx == MRHS_F32 && dt != MRHS_F64 && N % 4 == 0 && aligned16(X) && aligned16(T)) {
+    const size_t n4 = work / 4;
+    MRHS_DISPATCH(dt, SO, (k_scale_convert4<SO><<<grid_for(n4, kBlock), kBlock, 0, c->stream>>>((const float*)X, (SO*)T, n4, N, nrm + 2 * N, scale)));
+    MRHS_LAUNCH_CHECK("scale_convert4");
+    return;
+  }
   MRHS_DISPATCH(dx, SI, MRHS_DISPATCH(dt, SO, (k_scale_convert<SI, SO><<<grid_for(work, kBlock), kBlock, 0, c->stream>>>((const SI*)X, (SO*)T, rows, N, nrm + 2 * N, scale))));
   MRHS_LAUNCH_CHECK("scale_convert");
 }

@@ -494,57 +494,6 @@ __global__ void k_prolong6x4(const SP* __restrict__ P, const float* __restrict__
   }
 }
 
-// the same for FP32 P with Nt % 4 == 0: four coarse rows j per step, the P
-// entries of a (component, Re/Im) row read as one 16-byte load
-__global__ void k_prolong6x4v(const float* __restrict__ P, const float* __restrict__ uc, float* __restrict__ u,
-                              int Nt, int N, int Va, size_t nwork) {
-  const int Q = N / 4;
-  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (t >= nwork) return;
-  const int r0 = 4 * (int)(t % Q);
-  const size_t q = t / Q;
-  const int h = (int)(q % 2);
-  const size_t s = q / 2;
-  const size_t A = s / Va;
-  float are[6][4], aim[6][4];
-#pragma unroll
-  for (int cc = 0; cc < 6; ++cc)
-#pragma unroll
-    for (int e = 0; e < 4; ++e) are[cc][e] = aim[cc][e] = 0.f;
-  for (int j0 = 0; j0 < Nt; j0 += 4) {
-    float4 pr[6], pi[6];
-#pragma unroll
-    for (int cc = 0; cc < 6; ++cc) {
-      const size_t row = s * 12 + 6 * h + cc;
-      pr[cc] = __ldg(reinterpret_cast<const float4*>(P + (row * 2) * Nt + j0));
-      pi[cc] = __ldg(reinterpret_cast<const float4*>(P + (row * 2 + 1) * Nt + j0));
-    }
-#pragma unroll
-    for (int jj = 0; jj < 4; ++jj) {
-      const size_t crow = A * 2 * Nt + h * Nt + j0 + jj;
-      const float4 w0 = __ldg(reinterpret_cast<const float4*>(uc + fidx(crow, 0, N, r0)));
-      const float4 w1 = __ldg(reinterpret_cast<const float4*>(uc + fidx(crow, 1, N, r0)));
-      const float wr[4] = {w0.x, w0.y, w0.z, w0.w}, wi[4] = {w1.x, w1.y, w1.z, w1.w};
-#pragma unroll
-      for (int cc = 0; cc < 6; ++cc) {
-        const float a = jj == 0 ? pr[cc].x : jj == 1 ? pr[cc].y : jj == 2 ? pr[cc].z : pr[cc].w;
-        const float b = jj == 0 ? pi[cc].x : jj == 1 ? pi[cc].y : jj == 2 ? pi[cc].z : pi[cc].w;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          are[cc][e] = fmaf(-b, wi[e], fmaf(a, wr[e], are[cc][e]));
-          aim[cc][e] = fmaf(b, wr[e], fmaf(a, wi[e], aim[cc][e]));
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int cc = 0; cc < 6; ++cc) {
-    const size_t row = s * 12 + 6 * h + cc;
-    *reinterpret_cast<float4*>(u + fidx(row, 0, N, r0)) = make_float4(are[cc][0], are[cc][1], are[cc][2], are[cc][3]);
-    *reinterpret_cast<float4*>(u + fidx(row, 1, N, r0)) = make_float4(aim[cc][0], aim[cc][1], aim[cc][2], aim[cc][3]);
-  }
-}
-
 template <class S>
 __global__ void k_sub_from(const S* b, S* w, size_t n) {  // w = b - w
   size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -813,16 +762,6 @@ void prolong_typed(mrhs_ctx c, const void* uc, int dc, void* u, int du, int N) {
   Prof pr(c, "prolong");
   if (dc == MRHS_F32 && du == MRHS_F32 && N % 4 == 0 && ((uintptr_t)uc & 15) == 0 && ((uintptr_t)u & 15) == 0) {
     const size_t w4 = (size_t)c->g.V * 2 * (N / 4);
-    static const bool scalar_p = [] {
-      const char* e = std::getenv("MRHS_PROLONG");
-      return e && std::string(e) == "scalar";
-    }();
-    if (!scalar_p && c->tv_dtype == MRHS_F32 && c->ntv % 4 == 0) {
-      k_prolong6x4v<<<grid_for(w4, 256), 256, 0, c->stream>>>((const float*)c->P, (const float*)uc, (float*)u,
-                                                              c->ntv, N, c->g.Va, w4);
-      MRHS_LAUNCH_CHECK("prolong");
-      return;
-    }
     MRHS_DISPATCH(c->tv_dtype, SP, (k_prolong6x4<SP><<<grid_for(w4, 256), 256, 0, c->stream>>>((const SP*)c->P, (const float*)uc, (float*)u, c->ntv, N, c->g.Va, w4)));
     MRHS_LAUNCH_CHECK("prolong");
     return;

@@ -98,9 +98,12 @@ __global__ void __launch_bounds__(kThreads) k_coarse_op_tc(const SP* __restrict_
                                                            int Nt, Agg4 ag, int Va, cx<float>* __restrict__ Dc,
                                                            int* __restrict__ err) {
   constexpr int ES = Elem<FMT>::size;
-  // 16-byte K groups per chunk: 12, or 6 for split tf32 so that two CTAs
-  // (four tiles per stage each) still share an SM
-  constexpr int KGT = SPLIT ? kKG / 2 : kKG;
+  // 16-byte K groups per chunk: 12. Split tf32 keeps one stage of four tiles
+  // (96 KB, two CTAs per SM): its chunk waits for the previous chunk's MMAs
+  // before it overwrites the operands, which cost less than the chunks of
+  // half the size that two stages would leave room for
+  constexpr int KGT = kKG;
+  constexpr bool ONE = SPLIT;                  // a single stage
   constexpr int TB = kRows / 8 * KGT * 128;    // bytes of one tile
   constexpr int Q = KGT * 16 / ES / 12;        // sites per chunk: 8 (2-byte), 4 (tf32), 2 (split tf32)
   constexpr int KSTEP_BYTES = 256;            // two core matrices along K per MMA
@@ -120,7 +123,7 @@ __global__ void __launch_bounds__(kThreads) k_coarse_op_tc(const SP* __restrict_
 
   // zero both stages once: padding rows and off-chirality entries of A stay zero
   constexpr int NT = SPLIT ? 4 : 2;  // tiles per stage: A, B (and their low parts)
-  for (int i = threadIdx.x; i < 2 * NT * TB / 16; i += kThreads)
+  for (int i = threadIdx.x; i < (ONE ? 1 : 2) * NT * TB / 16; i += kThreads)
     reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
   if (threadIdx.x == 0) {
     tc::mbar_init(&mbar[0], 1);
@@ -153,9 +156,18 @@ __global__ void __launch_bounds__(kThreads) k_coarse_op_tc(const SP* __restrict_
   const int nchunk = (nsite + Q - 1) / Q;
   int issued = 0;
   for (int t = 0; t < nchunk; ++t) {
-    const int st = t & 1;
-    // stage st was last read by the MMAs of chunk t-2, complete since the
-    // previous iteration waited for chunk t-1
+    const int st = ONE ? 0 : t & 1;
+    // stage st was last read by the MMAs of chunk t-2 (two stages), complete
+    // since the previous iteration waited for chunk t-1; with one stage, wait
+    // for chunk t-1 here and fold its partial sum before the operands change
+    if (ONE && t >= 1) {
+      if (!tc::mbar_wait(&mbar[0], (t - 1) & 1, kWaitLimit)) s_bad = 1;
+      tc::fence_after_sync();
+      tc::tmem_promote(t_own + 128, t_own, own_cols);
+      tc::tmem_wait_st();
+      tc::fence_before_sync();
+      __syncthreads();
+    }
     if (s_bad) break;
     const int q0 = t * Q;
     const int nq = min(Q, nsite - q0);
@@ -206,7 +218,7 @@ __global__ void __launch_bounds__(kThreads) k_coarse_op_tc(const SP* __restrict_
     }
     tc::fence_async_smem();
     // chunk t-1 done: fold its partial sum R into S before R is reused
-    if (t >= 1) {
+    if (!ONE && t >= 1) {
       if (!tc::mbar_wait(&mbar[0], (t - 1) & 1, kWaitLimit)) s_bad = 1;
       tc::fence_after_sync();
       tc::tmem_promote(t_own + 128, t_own, own_cols);
@@ -551,7 +563,7 @@ bool build_Dc_tc(mrhs_ctx c, int fmt, bool split) {
   Agg4 ag;
   for (int m = 0; m < 4; ++m) ag.a[m] = c->g.a[m];
   split = split && fmt == tc::kFmtTF32;
-  const size_t smem = 4 * (size_t)kTileBytes;  // two stages of 2 tiles, or of 4 half-size tiles (split)
+  const size_t smem = 4 * (size_t)kTileBytes;  // two stages of 2 tiles, or one of 4 tiles (split)
   const cx<float>* U = (const cx<float>*)c->U32;
   const float* Acl = (const float*)c->A32;
   int* err = c->dflag + 2;

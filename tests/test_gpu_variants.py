@@ -119,11 +119,9 @@ def _child(env, kind, nrhs):
     ({}, "restrict", 6, "restrict", 1e-5),
     ({"MRHS_RESTRICT": "tiled"}, "restrict", 8, "restrict", 1e-5),
     ({}, "prolong", 8, "prolong", 1e-5),
-    ({"MRHS_PROLONG": "scalar"}, "prolong", 8, "prolong", 1e-5),
     ({}, "prolong", 6, "prolong", 1e-5),
 ], ids=["smem-fused8", "smem-fused2", "chunk2", "tm", "tm-cpb1", "passes2", "dc-alu", "pk1g", "pk1g-6", "pk1g-cpb2",
-        "pk2s", "pk2s-cpb1", "restrict-stream", "restrict-tiled-6", "restrict-tiled", "prolong-vec", "prolong-scalar",
-        "prolong-6"])
+        "pk2s", "pk2s-cpb1", "restrict-stream", "restrict-tiled-6", "restrict-tiled", "prolong-4", "prolong-6"])
 def test_switch_selected_forms(env, kind, nrhs, kernel, tol):
     r = _child(env, kind, nrhs)
     assert kernel in r["kernels"], r
