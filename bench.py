@@ -483,8 +483,8 @@ def run_ours(args, cfg, cfg_name, m0, m0_src, rank, world, local_rank):
 # times separately (Sec. 7): smoother, coarse grid, projections, setup of R
 # and D_c, and the copies that move a block of test vectors in and out
 PHASES = {"smoother": ("sap_pk", "sap_tm", "sap_tm2", "sap_fused", "sap_fused8", "sap_block_mr", "dslash_resid"),
-          "coarse_grid": ("apply_dc_tc", "apply_dc", "multi_dot", "multi_axpy"),
-          "projections": ("restrict", "prolong"),
+          "coarse_grid": ("apply_dc_tc", "apply_dc", "multi_dot", "multi_axpy", "inverse_apply", "self_inverse"),
+          "projections": ("restrict", "prolong", "normalise", "norms"),
           "R_and_Dc": ("gs_cholqr2", "coarse_op", "coarse_op_tc", "format_dc"),
           "block_copies": ("block_gather",)}
 

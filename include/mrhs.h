@@ -202,9 +202,10 @@ int mrhs_build_P(mrhs_ctx ctx);
 int mrhs_build_Dc(mrhs_ctx ctx);
 
 /* Engine of the contraction P^dag (D P) inside mrhs_build_Dc (the dense
- * 2ntv x 2ntv coarse-link products). AUTO: CUDA cores for the FP64 and FP32
- * contexts; tensor cores (tcgen05, FP32 accumulation) for the mixed ones:
- * bf16 operands for MIX_BF16, tf32 for MIX_FP16. ALU:
+ * 2ntv x 2ntv coarse-link products). AUTO: CUDA cores for FP64 contexts;
+ * tensor cores (tcgen05, FP32 accumulation) otherwise: split tf32 for FP32
+ * (as TC_TF32X3; the CUDA cores when 2*ntv > 64), bf16 operands for
+ * MIX_BF16, tf32 for MIX_FP16. ALU:
  * always the CUDA cores. TC_BF16 / TC_F16 / TC_TF32: the tensor cores with
  * that operand type (P and D P rounded to it); TC_TF32X3: split tf32 (every
  * operand as hi + lo tf32 parts, products hi*hi + hi*lo + lo*hi, FP32
