@@ -3,9 +3,9 @@
 One step = the whole setup on one lattice: initial phase (SAP on all N_tv
 test vectors from x0 = 0, normalisation, P by aggregate-wise Gram-Schmidt,
 D_c = P^dag D P) followed by the refinement iterations of Algorithm 2 with
-block length N_b = N_tv (restriction, coarse GMRES to 0.05, prolongation,
-SAP, normalisation, P, D_c), all in the library's CUDA kernels through its C
-ABI. Inputs (gauge field, clover, test vectors) are resident in HBM when the
+block length N_b = N_tv (restriction, coarse GMRES to 0.05 on the Schur
+complement of the even aggregates, prolongation, SAP, normalisation, P, D_c),
+all in the library's CUDA kernels through its C ABI. Inputs (gauge field, clover, test vectors) are resident in HBM when the
 timed region starts.
 
 Prints one JSON line. `--impl reference` times the FP64 CPU oracle (the
