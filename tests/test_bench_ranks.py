@@ -72,13 +72,13 @@ def test_reference_arm_runs_on_rank_zero_only(capsys, monkeypatch):
 def test_reference_arm_line_on_rank_zero(capsys, monkeypatch):
     calls = []
 
-    def fake_sample(cfg, m0):
+    def fake_sample(cfg, m0, coarse_eo=1):
         calls.append(m0)
         return 1.0, 40.0 + len(calls), 16, "fake sample"
 
     monkeypatch.setattr(bench, "cpu_sample", fake_sample)
     monkeypatch.delenv("OMP_NUM_THREADS", raising=False)  # restored after the test
-    args = argparse.Namespace(steps=2, warmup=3)
+    args = argparse.Namespace(steps=2, warmup=3, coarse_eo=1)
     cfg = bench.CONFIGS[bench.DEFAULT_CONFIG]
     bench.run_reference(args, cfg, bench.DEFAULT_CONFIG, -0.4, "test", rank=0, world=2)
     import json
@@ -97,13 +97,13 @@ def test_reference_arm_on_rank_zero_uses_every_host_core(capsys, monkeypatch):
     rank 0 works, so it lifts that limit before the oracle library loads."""
     seen = []
 
-    def fake_sample(cfg, m0):
+    def fake_sample(cfg, m0, coarse_eo=1):
         seen.append(os.environ.get("OMP_NUM_THREADS"))
         return 1.0, 1.0, int(seen[-1]), "fake sample"
 
     monkeypatch.setenv("OMP_NUM_THREADS", "1")
     monkeypatch.setattr(bench, "cpu_sample", fake_sample)
-    args = argparse.Namespace(steps=1, warmup=0)
+    args = argparse.Namespace(steps=1, warmup=0, coarse_eo=1)
     cfg = bench.CONFIGS[bench.DEFAULT_CONFIG]
     bench.run_reference(args, cfg, bench.DEFAULT_CONFIG, -0.4, "test", rank=0, world=2)
     capsys.readouterr()
