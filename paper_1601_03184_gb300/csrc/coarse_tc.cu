@@ -92,7 +92,7 @@ __device__ __forceinline__ void put2_split(unsigned char* thi, unsigned char* tl
   *reinterpret_cast<uint2*>(tlo + off) = make_uint2(la, lb);
 }
 
-template <int FMT, class SP, bool SPLIT, int KGS = kKG>
+template <int FMT, class SP, bool SPLIT>
 __global__ void __launch_bounds__(kThreads) k_coarse_op_tc(const SP* __restrict__ P, const cx<float>* __restrict__ U,
                                                            const float* __restrict__ Acl, const int* __restrict__ nbr,
                                                            int Nt, Agg4 ag, int Va, cx<float>* __restrict__ Dc,
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kThreads) k_coarse_op_tc(const SP* __restrict_
   // (96 KB, two CTAs per SM): its chunk waits for the previous chunk's MMAs
   // before it overwrites the operands, which cost less than the chunks of
   // half the size that two stages would leave room for
-  constexpr int KGT = KGS;                     // kKG, or twice that (8-site chunks of split tf32)
+  constexpr int KGT = kKG;
   constexpr bool ONE = SPLIT;                  // a single stage
   constexpr int TB = kRows / 8 * KGT * 128;    // bytes of one tile
   constexpr int Q = KGT * 16 / ES / 12;        // sites per chunk: 8 (2-byte), 4 (tf32), 2 (split tf32)
@@ -563,14 +563,10 @@ bool build_Dc_tc(mrhs_ctx c, int fmt, bool split) {
   Agg4 ag;
   for (int m = 0; m < 4; ++m) ag.a[m] = c->g.a[m];
   split = split && fmt == tc::kFmtTF32;
-  // two stages of 2 tiles, or one of 4 tiles (split); MRHS_DC_CHUNK=8: split
-  // tf32 in chunks of 8 sites (one stage of 4 double-size tiles, one CTA per SM)
-  static const bool big = [] {
-    const char* e = std::getenv("MRHS_DC_CHUNK");
-    return e && std::atoi(e) == 8;
-  }();
-  const bool big_split = big && split;
-  const size_t smem = (big_split ? 8 : 4) * (size_t)kTileBytes;
+  // two stages of 2 tiles, or one stage of 4 tiles (split; chunks of eight
+  // sites in one stage of 196 KB per CTA measured slower: 270 against 184 ms
+  // per build at 48^3x96)
+  const size_t smem = 4 * (size_t)kTileBytes;
   const cx<float>* U = (const cx<float>*)c->U32;
   const float* Acl = (const float*)c->A32;
   int* err = c->dflag + 2;
@@ -579,7 +575,6 @@ bool build_Dc_tc(mrhs_ctx c, int fmt, bool split) {
   MRHS_DISPATCH(c->tv_dtype, SP, {
     auto kern = fmt == tc::kFmtBF16 ? k_coarse_op_tc<tc::kFmtBF16, SP, false>
                 : fmt == tc::kFmtF16 ? k_coarse_op_tc<tc::kFmtF16, SP, false>
-                : big_split          ? k_coarse_op_tc<tc::kFmtTF32, SP, true, 2 * kKG>
                 : split              ? k_coarse_op_tc<tc::kFmtTF32, SP, true>
                                      : k_coarse_op_tc<tc::kFmtTF32, SP, false>;
     MRHS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
