@@ -1,6 +1,6 @@
 """Training and judging protocol of the learned test-vector generator on the
 16^3 x 32 workload (a project form beside the paper's method; the paper's
-setup, Sec. 2, is its fallback and its judge).
+setup, Sec. 2, is its fallback and its reference).
 
 Training data: n_train seeded gauge fields (roughness drawn uniformly in
 [0.4, 0.7], m0 near critical for that roughness), each with the N_tv = 20

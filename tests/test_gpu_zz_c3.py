@@ -7,7 +7,7 @@ the FGMRES residual in FP64; beside them the plain FP32 setup.
 
 Against the FP64 oracle's setup of the same inputs (tests/golden/c3_mixed.json
 and .npz, written by tests/golden/c3_mixed.py from the oracle only):
-  - the FGMRES iteration count at relative residual 1e-10 (the judge):
+  - the FGMRES iteration count at relative residual 1e-10 (the measure of setup quality):
     FP32 within +-10 % (at least +-1) of the oracle's count, bf16 and fp16
     within +-10 % of the plain FP32 GPU setup's count;
   - per-result errors on the stored aggregates (the first, one inside, the
