@@ -176,8 +176,11 @@ int mrhs_sap(mrhs_ctx ctx, const void* b, void* x, int nrhs, int dtype, int n_sw
  * e_O = A_OO^-1 (r_O - H_OE e_E) and x_B += e. The inverse clover term is
  * built on the first use after each mrhs_build_clover (MRHS_ERR_NONFINITE if
  * a block is singular). The even-odd form runs in the generic domain kernel
- * (one CTA per domain); the on-chip kernels serve only the plain form.
- * MRHS_ERR_ARG unless even_odd is 0 or 1. */
+ * (one CTA per domain); the on-chip kernels serve only the plain form. It
+ * needs three more FP32 work fields of the smoothed vectors and the inverse
+ * clover term (about 110 GB more at 48^3x96 with 32 vectors, which does not
+ * fit next to the setup's other fields on one GPU; the allocation then fails
+ * with MRHS_ERR_OOM). MRHS_ERR_ARG unless even_odd is 0 or 1. */
 int mrhs_set_smoother(mrhs_ctx ctx, int even_odd);
 
 /* ------------------------------------------------------ setup building blocks */
