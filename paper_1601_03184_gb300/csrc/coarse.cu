@@ -943,6 +943,36 @@ __global__ void k_inverse_apply8(const cx<R>* __restrict__ Dinv, const S* __rest
   for (int k = 0; k < 8; ++k) st<S, R>(y, row0 + k, N, r, scale(acc[k], s));
 }
 
+// the same with one CTA per compact odd block: its inverse (nc x nc) staged
+// in shared memory once, read there by every (8-row group, rhs) item of the
+// block; the same sums in the same order as k_inverse_apply8
+template <class S, class R>
+__global__ void __launch_bounds__(256) k_inverse_apply_blk(const cx<R>* __restrict__ Dinv, const S* __restrict__ a,
+                                                           const S* __restrict__ c, S* __restrict__ y, R s, int nc,
+                                                           int N) {
+  extern __shared__ double smem_iv[];
+  cx<R>* M = reinterpret_cast<cx<R>*>(smem_iv);  // [nc][nc]
+  const size_t b = blockIdx.x;
+  for (int e = threadIdx.x; e < nc * nc; e += blockDim.x) M[e] = Dinv[b * nc * nc + e];
+  __syncthreads();
+  const int nrt = nc / 8;
+  for (int w = threadIdx.x; w < nrt * N; w += blockDim.x) {
+    const int r = w % N, g = w / N;
+    const size_t row0 = b * nc + 8 * g;
+    cx<R> acc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = mk<R>(0, 0);
+    for (int j = 0; j < nc; ++j) {
+      cx<R> v = ld<S, R>(a, b * nc + j, N, r);
+      if (c) v = v - ld<S, R>(c, b * nc + j, N, r);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) fma_(acc[k], M[(8 * g + k) * nc + j], v);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) st<S, R>(y, row0 + k, N, r, scale(acc[k], s));
+  }
+}
+
 // the same with one row per thread (any nc)
 template <class S, class R>
 __global__ void k_inverse_apply(const cx<R>* __restrict__ Dinv, const S* __restrict__ a, const S* __restrict__ c,
@@ -1016,6 +1046,18 @@ namespace {
 void inverse_apply(mrhs_ctx c, const void* a, const void* b, void* y, double s, int N, int dtype) {
   const int nc = 2 * c->ntv;
   Prof pr(c, "inverse_apply");
+  const size_t es = dtype == MRHS_F64 ? sizeof(cx<double>) : sizeof(cx<float>);
+  const size_t smem = (size_t)nc * nc * es;
+  if (nc % 8 == 0 && smem <= 48 * 1024) {
+    if (dtype == MRHS_F64)
+      k_inverse_apply_blk<double, double><<<c->ncol[1], 256, smem, c->stream>>>(
+          (const cx<double>*)c->dc_inv, (const double*)a, (const double*)b, (double*)y, s, nc, N);
+    else
+      k_inverse_apply_blk<float, float><<<c->ncol[1], 256, smem, c->stream>>>(
+          (const cx<float>*)c->dc_inv, (const float*)a, (const float*)b, (float*)y, (float)s, nc, N);
+    MRHS_LAUNCH_CHECK("inverse_apply");
+    return;
+  }
   if (nc % 8 == 0) {
     const size_t work = (size_t)c->ncol[1] * (nc / 8) * N;
     if (dtype == MRHS_F64)
