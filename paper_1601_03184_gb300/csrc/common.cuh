@@ -331,14 +331,17 @@ void normalise_into(mrhs_ctx c, const void* X, int dx, void* T, int dt, size_t r
 // nb (same storage type), and back with conversion and a scale factor
 void gather_cols(mrhs_ctx c, const void* src, int ntv, void* dst, int nb, int k0, int dtype);
 void scatter_cols(mrhs_ctx c, const void* src, int ds, int nb, void* dst, int dd, int ntv, int k0, float scale);
-void sap_mixed(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int dtype, int n_sweeps, int n_mr);
+// x0_zero: the caller promises x = 0 on entry (the first domain solves then
+// skip the product with the starting guess)
+void sap_mixed(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int dtype, int n_sweeps, int n_mr,
+               bool x0_zero = false);
 void ensure_clover_inverse(mrhs_ctx c);
 // sap.cu: the on-chip SAP (FP32 work fields)
 bool sap_fused_ok(mrhs_ctx c, int dtype);
-void sap_fused(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int n_sweeps, int n_mr);
+void sap_fused(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int n_sweeps, int n_mr, bool x0_zero = false);
 bool sap_tm_ok(mrhs_ctx c, int nrhs);
 bool sap_pk_ok(mrhs_ctx c, int nrhs);
-void sap_pk(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int n_sweeps, int n_mr);
+void sap_pk(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int n_sweeps, int n_mr, bool x0_zero = false);
 void sap_tm(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int n_sweeps, int n_mr);
 // blas.cu: y[row][r] += sign * sum_k coef[k][r] * X_k[row][r], X_k = X + k*stride elements
 void multi_axpy(mrhs_ctx c, const void* X, size_t stride, int K, void* Y, size_t rows, int N, int dtype,

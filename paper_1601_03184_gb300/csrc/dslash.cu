@@ -659,7 +659,7 @@ static void resid_mixed(mrhs_ctx c, const void* x, void* y, const void* b, int b
 }
 
 // SAP with b stored in bdtype (possibly reduced precision) and x in dtype
-void sap_mixed(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int dtype, int n_sweeps, int n_mr) {
+void sap_mixed(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int dtype, int n_sweeps, int n_mr, bool x0_zero) {
   MRHS_REQUIRE(c->have_clover, MRHS_ERR_STATE, "smoother used before mrhs_build_clover");
   MRHS_REQUIRE(n_sweeps >= 0 && n_mr >= 0 && nrhs >= 1, MRHS_ERR_ARG, "bad smoother parameters");
   if (c->even_odd) {
@@ -684,7 +684,7 @@ void sap_mixed(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int dty
     return;
   }
   if (sap_fused_ok(c, dtype)) {
-    sap_fused(c, b, bdtype, x, nrhs, n_sweeps, n_mr);
+    sap_fused(c, b, bdtype, x, nrhs, n_sweeps, n_mr, x0_zero);
     return;
   }
   size_t bytes = fine_elems(c, nrhs) * dtype_size(dtype);

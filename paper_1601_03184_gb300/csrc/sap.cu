@@ -503,7 +503,7 @@ bool sap_fused_ok(mrhs_ctx c, int dtype) {
   return need <= (size_t)maxsm;
 }
 
-void sap_fused(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int n_sweeps, int n_mr) {
+void sap_fused(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int n_sweeps, int n_mr, bool x0_zero) {
   // the on-chip forms (tensor memory for the running solution): packed pairs
   // of right-hand sides per thread when nrhs % 4 == 0, else one (site, rhs)
   // item per thread; MRHS_SAP_KERNEL=tm asks for the item form always,
@@ -515,7 +515,7 @@ void sap_fused(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int n_s
   }();
   const bool tm_off = mode == 2;
   if (mode == 0 && sap_pk_ok(c, nrhs)) {
-    sap_pk(c, b, bdtype, x, nrhs, n_sweeps, n_mr);
+    sap_pk(c, b, bdtype, x, nrhs, n_sweeps, n_mr, x0_zero);
     return;
   }
   if (!tm_off && sap_tm_ok(c, nrhs)) {

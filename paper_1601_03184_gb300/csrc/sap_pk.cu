@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(256 * PP, 3 - PP) k_sap_pk(const SB* __restric
                                                       const float* __restrict__ U20, const float* __restrict__ Acl,
                                                       const int* __restrict__ nbr, int N, int Va,
                                                       const int* __restrict__ blist, int n_mr, uint32_t tm_cols,
-                                                      int cpb) {
+                                                      int cpb, int x0z) {
   extern __shared__ float4 smem4[];
   const int T = blockDim.x;
   constexpr int kG = 2 * PP;                                          // right-hand sides per chunk
@@ -301,7 +301,8 @@ __global__ void __launch_bounds__(256 * PP, 3 - PP) k_sap_pk(const SB* __restric
     // stage x0: one (component c, site l) per unit, the real and imaginary
     // rows of the chunk's right-hand sides become the pairs' float4
     // (re_a, re_b, im_a, im_b)
-    for (int u = tid; u < 12 * Va; u += T) {
+    // (x0z: x = 0 everywhere, the stage and D x0 are skipped)
+    for (int u = x0z ? 12 * Va : tid; u < 12 * Va; u += T) {
       const int c = u / Va, l = u % Va;
       const float* xs = x + ((d.s0 + l) * 24 + 2 * c) * N + r0;
       if (PP == 2) {
@@ -319,9 +320,9 @@ __global__ void __launch_bounds__(256 * PP, 3 - PP) k_sap_pk(const SB* __restric
     c2 o[12];
     // x_B = x0 of the thread's pair -> tensor memory; then q0 = D x0
 #pragma unroll
-    for (int c = 0; c < 12; ++c) o[c] = ldR<PP>(d, c, d.l);
+    for (int c = 0; c < 12; ++c) o[c] = x0z ? mk2(make_float2(0.f, 0.f), make_float2(0.f, 0.f)) : ldR<PP>(d, c, d.l);
     xb_put(tm, o);
-    apply_pk<true, PP, LG>(d, o, Acl, x, U20, N, r0);
+    if (!x0z) apply_pk<true, PP, LG>(d, o, Acl, x, U20, N, r0);
     tc::tmem_wait_st();
     __syncthreads();  // every read of x0 in shared memory is done
     // rho = b - D x0 at the thread's site
@@ -471,7 +472,7 @@ bool sap_pk_ok(mrhs_ctx c, int nrhs) {
   return sap_pk_smem(Va, sap_pk_threads(Va, f.pp), f) <= (size_t)maxsm;
 }
 
-void sap_pk(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int n_sweeps, int n_mr) {
+void sap_pk(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int n_sweeps, int n_mr, bool x0_zero) {
   const int Va = c->g.Va;
   const PkForm f = pk_form();
   const int T = sap_pk_threads(Va, f.pp);
@@ -498,7 +499,7 @@ void sap_pk(mrhs_ctx c, const void* b, int bdtype, void* x, int nrhs, int n_swee
         auto kern = f.pp == 1 ? k_sap_pk<SB, 1, true> : f.lg ? k_sap_pk<SB, 2, true> : k_sap_pk<SB, 2, false>;
         MRHS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kern<<<c->ncol[col] * cpb, T, smem, c->stream>>>((const SB*)b, (float*)x, c->U20, c->A32, c->nbr, nrhs, Va,
-                                                         blist, n_mr, cols, cpb);
+                                                         blist, n_mr, cols, cpb, x0_zero && sw == 0 && col == 0);
       });
       MRHS_LAUNCH_CHECK("sap_pk");
     }

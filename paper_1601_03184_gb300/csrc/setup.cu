@@ -22,7 +22,9 @@ int block_length(mrhs_ctx c) { return c->block_len > 0 && c->block_len < c->ntv 
 // The initial phase on the test vectors k0 .. k0+nb-1 (all of them when
 // nb = ntv): x = SAP^n_sweeps(b = v, x0 = 0) (init_mode 0) or n_sweeps times
 // v <- SAP(b = v, x0 = 0) (init_mode 1); the normalised x replaces v.
-void init_block(mrhs_ctx c, int k0, int nb, int init_mode, int n_sweeps, int n_mr) {
+// b_src (init_mode 0 with the whole set, may be null): the vectors to smooth
+// in the storage type, read in place of the stored test vectors.
+void init_block(mrhs_ctx c, int k0, int nb, int init_mode, int n_sweeps, int n_mr, const void* b_src = nullptr) {
   const int N = c->ntv;
   const int wd = c->work_dtype;
   const size_t n = fine_elems(c, nb);
@@ -34,11 +36,11 @@ void init_block(mrhs_ctx c, int k0, int nb, int init_mode, int n_sweeps, int n_m
   }
   if (init_mode == 0) {
     MRHS_CUDA(cudaMemsetAsync(x, 0, n * dtype_size(wd), c->stream));
-    sap_mixed(c, v, c->tv_dtype, x, nb, wd, n_sweeps, n_mr);
+    sap_mixed(c, b_src ? b_src : v, c->tv_dtype, x, nb, wd, n_sweeps, n_mr, true);
   } else {
     for (int it = 0; it < n_sweeps; ++it) {
       MRHS_CUDA(cudaMemsetAsync(x, 0, n * dtype_size(wd), c->stream));
-      sap_mixed(c, v, c->tv_dtype, x, nb, wd, 1, n_mr);
+      sap_mixed(c, v, c->tv_dtype, x, nb, wd, 1, n_mr, true);
       if (it + 1 < n_sweeps) convert(c, x, wd, v, c->tv_dtype, n);
     }
   }
@@ -58,13 +60,17 @@ void setup_init(mrhs_ctx c, const void* tv0, int dtype, int init_mode, int n_swe
   const int N = c->ntv;
   const size_t n = fine_elems(c, N);
   if (!c->tv) c->tv = dalloc(c, n * dtype_size(c->tv_dtype));
-  convert(c, tv0, dtype, c->tv, c->tv_dtype, n);
+  const int nb = block_length(c);
+  // one smoother call on the whole set reads tv0 in place when it has the
+  // storage type; otherwise tv0 is converted into the stored vectors first
+  const bool direct = init_mode == 0 && nb == N && dtype == c->tv_dtype;
+  if (!direct) convert(c, tv0, dtype, c->tv, c->tv_dtype, n);
   c->have_tv = true;
   c->have_P = c->have_Dc = false;
   // blocks of N_b test vectors in order; the last one holds the remainder
   // when N_b does not divide ntv (Alg. 2 and its remainder rule)
-  const int nb = block_length(c);
-  for (int k0 = 0; k0 < N; k0 += nb) init_block(c, k0, std::min(nb, N - k0), init_mode, n_sweeps, n_mr);
+  for (int k0 = 0; k0 < N; k0 += nb)
+    init_block(c, k0, std::min(nb, N - k0), init_mode, n_sweeps, n_mr, direct ? tv0 : nullptr);
   c->tv_scale = c->tv_dtype == MRHS_F16 ? std::sqrt(12.0 * c->g.V) : 1.0;
   build_P(c);
   build_Dc(c);
@@ -85,7 +91,7 @@ void setup_init_learned(mrhs_ctx c, const void* tv0, int dtype, int n_sweeps, in
   convert(c, tv0, dtype, y, MRHS_F32, n);
   if (n_sweeps > 0) {
     MRHS_CUDA(cudaMemsetAsync(x, 0, n * sizeof(float), c->stream));
-    sap_mixed(c, y, MRHS_F32, x, N, MRHS_F32, n_sweeps, n_mr);
+    sap_mixed(c, y, MRHS_F32, x, N, MRHS_F32, n_sweeps, n_mr, true);
   } else {
     MRHS_CUDA(cudaMemcpyAsync(x, y, n * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
   }
