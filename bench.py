@@ -159,7 +159,7 @@ class ClockSampler:
 NCU_TRAFFIC = {
     "sap_tm": {"bytes": 903.34e6, "sites": 16 * 16 * 16 * 32, "ntv": 32,
                "profile": "profiles/k_sap_tm_16x16x16x32_ntv32.md"},
-    "sap_pk": {"bytes": 922.04e6, "sites": 16 * 16 * 16 * 32, "ntv": 32,
+    "sap_pk": {"bytes": 917.06e6, "sites": 16 * 16 * 16 * 32, "ntv": 32,
                "profile": "profiles/k_sap_pk_16x16x16x32_ntv32.md"},
 }
 
