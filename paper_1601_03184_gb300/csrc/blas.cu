@@ -4,6 +4,7 @@
 // Arrays are `rows` complex rows of [2][N]: element (row, re/im, rhs).
 // Reductions use a fixed two-level tree (per-CTA partials, then a fixed-order
 // sum), so results are bitwise reproducible.
+#include <algorithm>
 #include <cstdint>
 
 #include "common.cuh"
@@ -404,16 +405,40 @@ __device__ __forceinline__ void store4<__half>(__half* p, float a, float b, floa
   __half2 lo = __floats2half2_rn(a, b), hi = __floats2half2_rn(c, d);
   *reinterpret_cast<uint2*>(p) = make_uint2(*reinterpret_cast<uint32_t*>(&lo), *reinterpret_cast<uint32_t*>(&hi));
 }
+// resident CTAs per SM of k_scale_convert4 (256 threads each)
+constexpr int kScaleCtasPerSm = 8;
+// loads in flight per thread in k_scale_convert4
+constexpr int kScaleUnroll = 4;
+
+// the same four values at a time for FP32 X on a persistent grid: the
+// grid-stride step is a multiple of N/4 float4, so a thread keeps the same
+// four right-hand sides (and their factors) throughout, and it keeps
+// kScaleUnroll loads in flight; the products are those of k_scale_convert
 template <class SO>
-__global__ void k_scale_convert4(const float* __restrict__ X, SO* __restrict__ T, size_t n4, int N,
-                                 const double* __restrict__ s, float scale) {
-  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (t >= n4) return;
-  const int r = (int)((4 * t) % N);
-  const float4 v = __ldg(reinterpret_cast<const float4*>(X) + t);
-  const float a = (v.x * (float)s[r]) * scale, b = (v.y * (float)s[r + 1]) * scale;
-  const float c = (v.z * (float)s[r + 2]) * scale, d = (v.w * (float)s[r + 3]) * scale;
-  store4<SO>(T + 4 * t, a, b, c, d);
+__global__ void __launch_bounds__(kBlock) k_scale_convert4(const float* __restrict__ X, SO* __restrict__ T, size_t n4,
+                                                           int N, const double* __restrict__ s, float scale) {
+  const int nq = N / 4;
+  const size_t G = (size_t)gridDim.x * blockDim.x;
+  const size_t step = G - G % (size_t)nq;
+  const size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t0 >= step) return;
+  const int r = 4 * (int)(t0 % (size_t)nq);
+  const float s0 = (float)s[r], s1 = (float)s[r + 1], s2 = (float)s[r + 2], s3 = (float)s[r + 3];
+  const float4* X4 = reinterpret_cast<const float4*>(X);
+  size_t t = t0;
+  for (; t + (kScaleUnroll - 1) * step < n4; t += kScaleUnroll * step) {
+    float4 v[kScaleUnroll];
+#pragma unroll
+    for (int u = 0; u < kScaleUnroll; ++u) v[u] = __ldg(X4 + t + u * step);
+#pragma unroll
+    for (int u = 0; u < kScaleUnroll; ++u)
+      store4<SO>(T + 4 * (t + u * step), (v[u].x * s0) * scale, (v[u].y * s1) * scale, (v[u].z * s2) * scale,
+                 (v[u].w * s3) * scale);
+  }
+  for (; t < n4; t += step) {
+    const float4 v = __ldg(X4 + t);
+    store4<SO>(T + 4 * t, (v.x * s0) * scale, (v.y * s1) * scale, (v.z * s2) * scale, (v.w * s3) * scale);
+  }
 }
 
 void norms_of_field(mrhs_ctx c, const void* X, size_t rows, int N, int dtype, double* nrm) {
@@ -438,9 +463,12 @@ void normalise_into(mrhs_ctx c, const void* X, int dx, void* T, int dt, size_t r
   MRHS_LAUNCH_CHECK("inv_sqrt");
   const size_t work = rows * 2 * N;
   Prof pr(c, "normalise");
-  if (dx == MRHS_F32 && dt != MRHS_F64 && N % 4 == 0 && aligned16(X) && aligned16(T)) {
-    const size_t n4 = work / 4;
-    MRHS_DISPATCH(dt, SO, (k_scale_convert4<SO><<<grid_for(n4, kBlock), kBlock, 0, c->stream>>>((const float*)X, (SO*)T, n4, N, nrm + 2 * N, scale)));
+  const size_t n4 = work / 4;
+  const int grid = (int)std::min<size_t>((size_t)std::max(c->num_sms, 1) * kScaleCtasPerSm, (n4 + kBlock - 1) / kBlock);
+  // (the persistent form needs a grid of at least N/4 threads)
+  if (dx == MRHS_F32 && dt != MRHS_F64 && N % 4 == 0 && aligned16(X) && aligned16(T) &&
+      (size_t)grid * kBlock >= (size_t)(N / 4)) {
+    MRHS_DISPATCH(dt, SO, (k_scale_convert4<SO><<<grid, kBlock, 0, c->stream>>>((const float*)X, (SO*)T, n4, N, nrm + 2 * N, scale)));
     MRHS_LAUNCH_CHECK("scale_convert4");
     return;
   }
