@@ -301,7 +301,10 @@ int mrhs_coarse_solve_noalloc(mrhs_ctx ctx, const void* bc, void* xc, int nrhs, 
  * n_sweeps calls of one sweep, each v_j <- SAP(b = v_j, x0 = 0)), each v_j
  * normalised, then P (mrhs_build_P) and D_c (mrhs_build_Dc). All test
  * vectors are processed at once. tv0: device interleaved field, nrhs = ntv,
- * storage dtype. */
+ * storage dtype; read only, on the context's stream (with init_mode 0, one
+ * block of all ntv vectors and dtype equal to the context's storage type,
+ * the smoother reads it in place as its right-hand sides), so it must stay
+ * valid and unchanged until the stream has passed the call. */
 int mrhs_setup_init(mrhs_ctx ctx, const void* tv0, int dtype, int init_mode, int n_sweeps, int n_mr);
 
 /* Iterative refinement, Algorithm 2 with block length N_b (default N_b =
